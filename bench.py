@@ -1,0 +1,368 @@
+"""Benchmark: G list elements ranked per second on a random list of n = 2^28.
+
+One step = one lr_rank call over a uniformly random-order single list of
+2^28 elements (unweighted, int32 ranks) already resident in HBM: every kernel
+of the path runs (prep, head selection, chase at every level, base case,
+propagation).  The inputs (1 GiB succ, 2 GiB records, 1 GiB ranks) are far
+larger than L2, so no flush is needed between steps.
+
+Printed as one JSON line (rank 0).  Extra keys:
+  roofline     the level-0 chase kernel against measured HBM bandwidth, with
+               64 algorithmic bytes per element (one 32 B sector gathered and
+               one written back);
+  pipeline     the whole step against the random-sector roofline
+               (measured HBM GB/s / 64 B per element);
+  cpu_baseline the CPU oracle, single thread, on a bounded sample;
+  e2e          the same metric through lr_rank_host (host buffers, copies
+               inside the timed region).
+
+--impl reference times the CPU oracle as the reference arm.  Under torchrun
+(N > 1) every rank ranks its own list (replicas, no collective on the data
+path); value is the total over ranks divided by the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "G list elements ranked/s at n=2^28 (1 GB300) and % of random-sector HBM roofline"
+UNIT = "G elem/s"
+BYTES_PER_ELEM_CHASE = 64          # one 32 B sector read + one 32 B sector write-back
+FALLBACK_HBM_GBS = 6800.0
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rk = int(os.environ.get("RANK", "0"))
+    lrk = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rk, lrk
+
+
+def init_dist(backend):
+    import torch.distributed as dist
+    ws, rk, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def max_over_ranks(value, dist, device="cpu"):
+    """Max of a float over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed_steps(step, steps, warmup, dist=None, sync=None, device="cpu"):
+    """W untimed steps, then exactly K steps between barriers; returns the
+    slowest rank's seconds for the K steps."""
+    for _ in range(warmup):
+        step()
+    if sync:
+        sync()
+    if dist is not None:
+        dist.barrier()
+    if sync:
+        sync()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    if sync:
+        sync()
+    t1 = time.perf_counter()
+    if dist is not None:
+        dist.barrier()
+    return max_over_ranks(t1 - t0, dist, device)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for nm, v in zip(names, r[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("lr_kernels.cu", "lr_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2606_09318_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(n):
+    """DRAM bytes per level-0 chase launch from the committed ncu summary,
+    scaled to n elements, or None if the kernel changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "chase0_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("kernel_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_elem"]) * n
+
+
+def cpu_baseline(seconds_target=12.0):
+    """The oracle as it stands, one thread, on random lists of 2^24."""
+    import numpy as np
+    import gen
+    import oracle
+    oracle.build()
+    n = 1 << 24
+    succ = gen.random_list(n, 2028)
+    t_total, reps = 0.0, 0
+    while t_total < seconds_target and reps < 8:
+        t0 = time.perf_counter()
+        r = oracle.rank(succ)
+        t_total += time.perf_counter() - t0
+        reps += 1
+    assert r.shape[0] == n and np.int64(r.max()) == n - 1
+    return {"value": n * reps / t_total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "random-order list n=2^24 x %d runs (%.1f s), single thread" % (reps, t_total)}
+
+
+def make_random_list(n, seed, device):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    order = torch.randperm(n, device=device, generator=g, dtype=torch.int64)
+    s = torch.empty(n, dtype=torch.int64, device=device)
+    s[order[:-1]] = order[1:]
+    s[order[-1]] = order[-1]
+    out = s.to(torch.int32)
+    del s
+    return out, order
+
+
+def run_ours(args):
+    import torch
+    import paper_2606_09318_gb300 as lr
+    ws, rk, lrk = dist_env()
+    torch.cuda.set_device(lrk)
+    dist = init_dist("nccl")
+    dev = torch.device("cuda", lrk)
+    n = args.n
+    lr.load()
+    succ, order = make_random_list(n, 1000 * 2 + rk, dev)
+    rank = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        lr.rank_ex(succ, out=rank, sync=False, stream=stream)
+
+    # warm-up then timed region (device events + host clock around K steps)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if lr.device_status(stream) != 0:
+        raise RuntimeError("device reported an error during warm-up")
+    lr.profile_enable(True)
+    lr.profile_read(reset=True)
+    launches0 = lr.kernel_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(lrk) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+    launches = lr.kernel_launch_count() - launches0
+    prof = lr.profile_read(reset=True)
+    lr.profile_enable(False)
+    st = lr.device_status(stream)
+    if st != 0:
+        raise RuntimeError("device reported %s" % lr.status_string(st))
+    ms_local = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ms_local, dist, device=dev)
+
+    # correctness of the timed output (properties that determine it exactly)
+    r64 = rank.to(torch.int64)
+    sl = succ.to(torch.int64)
+    idx = torch.arange(n, device=dev)
+    term = sl == idx
+    ok = bool((r64[~term] == r64[sl[~term]] + 1).all()) and int(r64[term].sum()) == 0 \
+        and int(r64[order[0]]) == n - 1
+    del r64, sl, idx, term
+    if not ok:
+        raise RuntimeError("benchmark output failed the rank recurrence check")
+
+    # end-to-end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        hsucc = succ.cpu().pin_memory()
+        hrank = torch.empty(n, dtype=torch.int32).pin_memory()
+        lr.rank_host(hsucc, out=hrank.numpy(), stream=stream)          # warm-up
+        e2e_steps = max(1, min(args.steps, 5))
+
+        def estep():
+            lr.rank_host(hsucc, out=hrank.numpy(), stream=stream)
+
+        t = timed_steps(estep, e2e_steps, 1, dist, torch.cuda.synchronize, dev)
+        if not torch.equal(hrank, rank.cpu()):
+            raise RuntimeError("host-buffer path disagrees with the device path")
+        e2e = {"value": ws * n * e2e_steps / t / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n}
+
+    hbm, src = measured_peaks()
+    chase_ms = prof["ms_chase0"] / max(1, prof["chase0_launches"])
+    achieved = BYTES_PER_ELEM_CHASE * n / (chase_ms * 1e-3) / 1e9
+    value = ws * n / (ms * 1e-3) / 1e9
+    sector_roof = hbm / BYTES_PER_ELEM_CHASE            # G elem/s
+    steps_prof = max(1, prof["calls"])
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic: uniformly random-order single list (torch.randperm, seeded)",
+        "config": {"workload": "single random-order list, n=2^28, unweighted, int32 ranks",
+                   "n": n, "l2_policy": "inputs larger than L2 (1 GiB succ + 2 GiB records)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "k_chase<Rec8> (level-0 ruler chasing)",
+                     "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "peak_source": src,
+                     "traffic": ncu_traffic(n), "algorithmic_bytes": BYTES_PER_ELEM_CHASE * n,
+                     "ms_per_launch": round(chase_ms, 4)},
+        "pipeline": {"random_sector_roofline_gelem_s": round(sector_roof, 2),
+                     "frac": round(value / ws / sector_roof, 4),
+                     "phases_ms_per_step": {k[3:]: round(prof[k] / steps_prof, 4) for k in
+                                            ("ms_prep", "ms_select", "ms_chase0", "ms_chase_rest",
+                                             "ms_base", "ms_finalize")}},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    if rk == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rk == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    ws, rk, _ = dist_env()
+    if rk != 0:
+        return
+    import numpy as np
+    import gen
+    import oracle
+    oracle.build()
+    n = 1 << 22
+    succ = gen.random_list(n, 4242)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.rank(succ)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    assert int(np.int64(r.max())) == n - 1
+    t = sum(times)
+    value = n * len(times) / t / 1e9
+    sample = "random-order list n=2^22 per step (bounded sample of the n=2^28 workload), single thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * t / len(times), 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "single random-order list, unweighted, int32 ranks (oracle sample n=2^22)",
+                   "n": n},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1 << 28)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

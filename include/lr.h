@@ -1,0 +1,233 @@
+/*
+ * lr.h -- C ABI of the GB300 list-ranking library (liblr.so).
+ *
+ * Problem (Section 1.1 of "Engineering Scalable Distributed List Ranking",
+ * Sanders, Schimek, Uhl, Weidmann): a successor array succ[0..n-1] describes
+ * a set of singly linked lists; a terminal element points to itself
+ * (succ[t] == t) and an initial element (head) has no predecessor.  The rank
+ * of element i is the number of links from i to the terminal of its list, or,
+ * in the weighted problem, the sum of the link weights on that path.
+ *
+ * Method: sparse ruling set (Section 2.1, Algorithm 1): pick rulers (every
+ * head is forced to be one), chase each ruler's packet along succ until the
+ * next ruler while recording (ruler, offset) per element, rank the reduced
+ * list of rulers recursively (a single-CTA pointer-doubling base case ends the
+ * recursion), then give every element rank[ruler] - offset.
+ *
+ * Conventions shared by every entry point below:
+ *  - Pointers named succ/weight/rank/offsets are DEVICE pointers owned by the
+ *    caller unless the name ends in _host.  The library never frees them.
+ *  - succ is uint32; n <= LR_MAX_N (2^32 - 2).  Terminals satisfy succ[i]==i.
+ *  - weight == NULL means unweighted (every link weighs 1).  weight[i] is the
+ *    weight of the link i -> succ[i]; a terminal's weight is ignored, so a
+ *    terminal's rank is 0 (the paper's unweighted <=> weight 1 / terminal 0
+ *    equivalence, Section 1.1).
+ *  - Arithmetic is exact two's-complement, wrapping in the rank type; int32
+ *    weights are sign-extended.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream).  Argument errors are returned at once.  Errors
+ *    that depend on the data (out-of-range successor, cycle, two
+ *    predecessors, capacity) are recorded on the device and returned by
+ *    lr_get_device_status(stream) (or at once when lr_opts.sync is set).
+ *    On any error the contents of rank are unspecified.
+ *  - The library owns only its workspace: one grow-only device arena per
+ *    stream, reused across calls, unless the caller passes lr_opts.workspace.
+ *    Calls on one stream must not overlap from several host threads.
+ */
+#ifndef LR_H
+#define LR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t (struct CUstream_st *). */
+typedef struct CUstream_st *lr_stream;
+
+#define LR_MAX_N 4294967294LL /* 2^32 - 2: ids fit uint32 with two sentinels */
+
+typedef enum lr_status {
+    LR_OK = 0,
+    LR_ERR_INVALID_ARGUMENT = 1, /* NULL pointer with n > 0, bad size or dtype   */
+    LR_ERR_OUT_OF_RANGE = 2,     /* some succ[i] >= n (or >= its instance size)  */
+    LR_ERR_CYCLE = 3,            /* an element is not reachable from any head    */
+    LR_ERR_NOT_A_LIST = 4,       /* an element has two or more predecessors      */
+    LR_ERR_OUT_OF_MEMORY = 5,    /* device or pinned allocation failed           */
+    LR_ERR_BUDGET = 6,           /* serving: request larger than the budget      */
+    LR_ERR_TIMEOUT = 7,          /* a bounded wait ran out                       */
+    LR_ERR_CUDA = 8,             /* a CUDA runtime call failed                   */
+    LR_ERR_CAPACITY = 9,         /* more lists than lr_opts.max_lists promised   */
+    LR_ERR_NOT_FOUND = 10,       /* serving: unknown ticket                      */
+    LR_ERR_CANCELLED = 11,       /* serving: server shut down before the run     */
+    LR_ERR_CAPTURE = 12          /* call would sync or allocate during capture   */
+} lr_status;
+
+typedef enum lr_dtype { LR_NONE = 0, LR_I32 = 1, LR_I64 = 2 } lr_dtype;
+
+/*
+ * Tuning knobs of the ruling-set recursion (filled by the autotuner; zero
+ * fields take the built-in defaults).  Rulers per level: ceil(n / f_inv).
+ */
+typedef struct lr_tuning {
+    uint32_t f0_inv;     /* 1/f at level 0 (default 64)                          */
+    uint32_t f_inv;      /* 1/f at levels >= 1 (default 8)                       */
+    uint32_t cutoff;     /* largest level ranked by the single-CTA base case     */
+    uint32_t chase_block;/* threads per CTA of the chase kernel (default 256)    */
+    uint32_t chase_ctas; /* CTAs per SM of the chase kernel (default: occupancy) */
+    uint32_t reserved[3];
+} lr_tuning;
+
+typedef struct lr_opts {
+    lr_dtype wtype;           /* weight type: LR_NONE (unweighted), LR_I32, LR_I64   */
+    lr_dtype rtype;           /* rank type: LR_I32 or LR_I64                          */
+    const lr_tuning *tuning;  /* NULL: defaults / autotuned table                     */
+    void *workspace;          /* optional caller-owned device memory                  */
+    size_t ws_bytes;          /* its size; must be >= lr_workspace_size(...)          */
+    int32_t validate;         /* 1: also detect two predecessors (LR_ERR_NOT_A_LIST) */
+    int32_t sync;             /* 1: wait for the device and return its status         */
+    uint64_t seed;            /* ruler sampling seed (results do not depend on it)    */
+    int64_t max_lists;        /* > 0: promise at most this many lists (heads).  The   */
+                              /* call then never synchronises and can be captured in  */
+                              /* a CUDA graph.  0: count the heads first (one sync).  */
+    int64_t n_total;          /* batch only: sum of instance sizes if known (>0), so  */
+                              /* offsets[k] need not be read back from the device.    */
+} lr_opts;
+
+/* Fill *o with defaults: unweighted, int32 ranks, seed 0x5eed, no sync. */
+void lr_opts_default(lr_opts *o);
+
+/*
+ * Rank one successor array.  weight == NULL: unweighted, rank is int32
+ * (n must be < 2^31).  weight != NULL: weight and rank are int64.
+ */
+lr_status lr_rank(const uint32_t *succ, const void *weight, int64_t n, void *rank,
+                  lr_stream stream);
+
+/* Same with explicit dtypes, tuning, workspace and validation. */
+lr_status lr_rank_ex(const uint32_t *succ, const void *weight, int64_t n, void *rank,
+                     const lr_opts *opts, lr_stream stream);
+
+/*
+ * Rank k independent instances stored back to back.  offsets (device,
+ * int64[k+1], offsets[0] == 0, non-decreasing) delimits instance j as
+ * elements offsets[j] .. offsets[j+1]-1; succ holds LOCAL ids in
+ * [0, offsets[j+1]-offsets[j]).  weight/rank as in lr_rank (int64 when
+ * weighted).  All instances run in one launch sequence over the forest they
+ * form (Section 1.1 allows a set of lists).  Sum of sizes <= LR_MAX_N.
+ */
+lr_status lr_rank_batch(const int64_t *offsets, const uint32_t *succ, const void *weight,
+                        void *rank, int32_t k, lr_stream stream);
+
+lr_status lr_rank_batch_ex(const int64_t *offsets, const uint32_t *succ, const void *weight,
+                           void *rank, int32_t k, const lr_opts *opts, lr_stream stream);
+
+/*
+ * End-to-end form with HOST buffers (pageable or pinned): copies succ and
+ * weight to the device, ranks, copies rank back and waits.  Returns the
+ * final status (argument or device error).
+ */
+lr_status lr_rank_host(const uint32_t *succ_host, const void *weight_host, int64_t n,
+                       void *rank_host, const lr_opts *opts, lr_stream stream);
+
+/*
+ * Bytes of workspace a call with these sizes needs when the caller passes
+ * lr_opts.workspace.  k = 0 for lr_rank_ex.  Uses opts->max_lists as the
+ * bound on the number of lists (0: assumes every element may be a head).
+ * Host-only; needs no GPU.
+ */
+size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts);
+
+/*
+ * Wait for `stream` and return (and clear) the status the device recorded
+ * for the last call issued on it.
+ */
+lr_status lr_get_device_status(lr_stream stream);
+
+/* Human-readable name of a status code (static string). */
+const char *lr_status_string(lr_status s);
+
+/* Library version string (static). */
+const char *lr_version(void);
+
+/*
+ * Profiling.  While enabled, every call records CUDA events around its
+ * phases on its own stream; lr_profile_read waits for them and returns the
+ * accumulated device milliseconds per phase and the number of kernels the
+ * library launched since the last reset.
+ */
+typedef struct lr_profile {
+    double ms_prep;      /* level-0 pass: validate, pack, has-predecessor bitmap */
+    double ms_select;    /* head detection and ruler numbering, all levels      */
+    double ms_chase0;    /* level-0 ruler chasing (the dominant kernel)          */
+    double ms_chase_rest;/* ruler chasing at levels >= 1                         */
+    double ms_base;      /* base case                                            */
+    double ms_finalize;  /* ruler propagation, all levels                        */
+    int64_t calls;       /* ranked calls covered                                 */
+    int64_t chase0_launches;
+    int64_t kernel_launches;
+    int64_t elements;    /* elements ranked (sum of n)                           */
+} lr_profile;
+
+lr_status lr_profile_enable(int32_t on);
+lr_status lr_profile_read(lr_profile *out, int32_t reset);
+
+/* Kernels launched by the library since load (all streams). Host-only. */
+int64_t lr_kernel_launch_count(void);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching: requests of mixed sizes are admitted while their
+ * device footprint fits the memory budget, grouped as they arrive into
+ * batched launches on one of n_streams streams, and completed individually.
+ */
+typedef struct lr_server lr_server;
+
+typedef struct lr_server_config {
+    size_t budget_bytes;     /* device memory for resident requests (default 40e9)  */
+    int32_t n_streams;       /* concurrent batches in flight (default 2)             */
+    int32_t max_batch;       /* most requests per launch (default 256)               */
+    int64_t max_batch_elems; /* most elements per launch (default 2^28)              */
+    int32_t device;          /* CUDA device ordinal (default 0)                      */
+    int32_t plain;           /* 1: launch every request alone (baseline mode)        */
+} lr_server_config;
+
+void lr_server_config_default(lr_server_config *c);
+
+typedef struct lr_request {
+    const uint32_t *succ;    /* successor array (host or device, see on_device)     */
+    const void *weight;      /* weights or NULL                                     */
+    void *rank;              /* output (host or device)                             */
+    int64_t n;
+    lr_dtype wtype, rtype;
+    int32_t on_device;       /* 1: pointers are device memory the caller keeps      */
+                             /* alive until lr_server_wait returns; 0: host memory  */
+                             /* copied into budgeted device buffers by the server   */
+} lr_request;
+
+typedef struct lr_result {
+    lr_status status;
+    double t_submit_ms, t_admit_ms, t_launch_ms, t_done_ms; /* since server start */
+} lr_result;
+
+typedef struct lr_server_stats {
+    int64_t completed;
+    int64_t elements;
+    int64_t batches;
+    double p50_ms, p99_ms, mean_ms;   /* submit -> done                            */
+    double elements_per_s;            /* completed elements / busy wall time        */
+    size_t peak_resident_bytes;
+} lr_server_stats;
+
+lr_status lr_server_create(const lr_server_config *cfg, lr_server **out);
+lr_status lr_server_submit(lr_server *s, const lr_request *req, uint64_t *ticket);
+/* timeout_ms < 0: wait without limit. */
+lr_status lr_server_wait(lr_server *s, uint64_t ticket, int64_t timeout_ms, lr_result *res);
+lr_status lr_server_stats_get(lr_server *s, lr_server_stats *out);
+void lr_server_destroy(lr_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LR_H */

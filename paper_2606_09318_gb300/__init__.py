@@ -1,0 +1,389 @@
+"""Python binding of liblr.so, the GB300 list-ranking library.
+
+Thin ctypes marshalling over the C ABI in include/lr.h: torch tensors supply
+device memory and streams, every step of the ranking runs in the library's
+CUDA kernels.  There is no CPU fallback: if the shared library is missing or
+cannot load, importing the ranking functions raises.
+
+    import paper_2606_09318_gb300 as lr
+    rank = lr.rank(succ)                      # succ: cuda uint32/int32 tensor
+    rank = lr.rank(succ, weight)              # int64 weights -> int64 ranks
+    rank = lr.rank_batch(offsets, succ, w)    # many lists, one launch sequence
+"""
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "LRError", "Tuning", "load", "lib_path", "rank", "rank_ex", "rank_batch", "rank_host",
+    "device_status", "workspace_size", "status_string", "version", "profile_enable",
+    "profile_read", "kernel_launch_count", "Server", "STATUS",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "liblr.so")
+
+STATUS = {
+    0: "LR_OK", 1: "LR_ERR_INVALID_ARGUMENT", 2: "LR_ERR_OUT_OF_RANGE", 3: "LR_ERR_CYCLE",
+    4: "LR_ERR_NOT_A_LIST", 5: "LR_ERR_OUT_OF_MEMORY", 6: "LR_ERR_BUDGET", 7: "LR_ERR_TIMEOUT",
+    8: "LR_ERR_CUDA", 9: "LR_ERR_CAPACITY", 10: "LR_ERR_NOT_FOUND", 11: "LR_ERR_CANCELLED",
+    12: "LR_ERR_CAPTURE",
+}
+LR_NONE, LR_I32, LR_I64 = 0, 1, 2
+
+
+class LRError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = int(code)
+        self.name = STATUS.get(self.code, "LR_ERR_%d" % self.code)
+        super().__init__("%s%s" % (self.name, (": " + what) if what else ""))
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("f0_inv", ctypes.c_uint32), ("f_inv", ctypes.c_uint32), ("cutoff", ctypes.c_uint32),
+                ("chase_block", ctypes.c_uint32), ("chase_ctas", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 3)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("wtype", ctypes.c_int), ("rtype", ctypes.c_int), ("tuning", ctypes.POINTER(Tuning)),
+                ("workspace", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t),
+                ("validate", ctypes.c_int32), ("sync", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("max_lists", ctypes.c_int64), ("n_total", ctypes.c_int64)]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("ms_prep", ctypes.c_double), ("ms_select", ctypes.c_double),
+                ("ms_chase0", ctypes.c_double), ("ms_chase_rest", ctypes.c_double),
+                ("ms_base", ctypes.c_double), ("ms_finalize", ctypes.c_double),
+                ("calls", ctypes.c_int64), ("chase0_launches", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("elements", ctypes.c_int64)]
+
+
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("n_streams", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_batch_elems", ctypes.c_int64),
+                ("device", ctypes.c_int32), ("plain", ctypes.c_int32)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("succ", ctypes.c_void_p), ("weight", ctypes.c_void_p), ("rank", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("wtype", ctypes.c_int), ("rtype", ctypes.c_int),
+                ("on_device", ctypes.c_int32)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("t_submit_ms", ctypes.c_double),
+                ("t_admit_ms", ctypes.c_double), ("t_launch_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("elements", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("elements_per_s", ctypes.c_double), ("peak_resident_bytes", ctypes.c_size_t)]
+
+
+_lock = threading.Lock()
+_lib = None
+_V, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+_SIGS = {
+    "lr_opts_default": (None, [ctypes.POINTER(_Opts)]),
+    "lr_rank": (ctypes.c_int, [_V, _V, _I64, _V, _V]),
+    "lr_rank_ex": (ctypes.c_int, [_V, _V, _I64, _V, ctypes.POINTER(_Opts), _V]),
+    "lr_rank_batch": (ctypes.c_int, [_V, _V, _V, _V, _I32, _V]),
+    "lr_rank_batch_ex": (ctypes.c_int, [_V, _V, _V, _V, _I32, ctypes.POINTER(_Opts), _V]),
+    "lr_rank_host": (ctypes.c_int, [_V, _V, _I64, _V, ctypes.POINTER(_Opts), _V]),
+    "lr_workspace_size": (_SZ, [_I64, _I32, ctypes.POINTER(_Opts)]),
+    "lr_get_device_status": (ctypes.c_int, [_V]),
+    "lr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "lr_version": (ctypes.c_char_p, []),
+    "lr_profile_enable": (ctypes.c_int, [_I32]),
+    "lr_profile_read": (ctypes.c_int, [ctypes.POINTER(_Profile), _I32]),
+    "lr_kernel_launch_count": (_I64, []),
+    "lr_server_config_default": (None, [ctypes.POINTER(_ServerConfig)]),
+    "lr_server_create": (ctypes.c_int, [ctypes.POINTER(_ServerConfig), ctypes.POINTER(_V)]),
+    "lr_server_submit": (ctypes.c_int, [_V, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "lr_server_wait": (ctypes.c_int, [_V, ctypes.c_uint64, _I64, ctypes.POINTER(_Result)]),
+    "lr_server_stats_get": (ctypes.c_int, [_V, ctypes.POINTER(_ServerStats)]),
+    "lr_server_destroy": (None, [_V]),
+}
+
+
+def lib_path():
+    return _LIB_PATH
+
+
+def load():
+    """Load liblr.so (built by build.py / __graft_entry__.build()); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                raise ImportError("liblr.so is not built (%s); run paper_2606_09318_gb300/build.py"
+                                  % _LIB_PATH)
+            lib = ctypes.CDLL(_LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def status_string(code):
+    return load().lr_status_string(int(code)).decode()
+
+
+def version():
+    return load().lr_version().decode()
+
+
+def _check(code, what=""):
+    if code != 0:
+        raise LRError(code, what)
+
+
+# ---------------------------------------------------------------- torch glue
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, name, dtypes):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype not in dtypes:
+        raise TypeError("%s has dtype %s, expected one of %s" % (name, t.dtype, dtypes))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _succ_dtypes():
+    torch = _torch()
+    return tuple(d for d in (getattr(torch, "uint32", None), torch.int32) if d is not None)
+
+
+def _wcode(weight):
+    torch = _torch()
+    if weight is None:
+        return LR_NONE
+    return {torch.int32: LR_I32, torch.int64: LR_I64}[weight.dtype]
+
+
+def _opts(wtype, rtype, validate=False, seed=0x5EED, max_lists=0, tuning=None, sync=False,
+          n_total=0, workspace=None):
+    o = _Opts()
+    load().lr_opts_default(ctypes.byref(o))
+    o.wtype, o.rtype = wtype, rtype
+    o.validate = 1 if validate else 0
+    o.sync = 1 if sync else 0
+    o.seed = int(seed) & (2**64 - 1)
+    o.max_lists = int(max_lists)
+    o.n_total = int(n_total)
+    if tuning is not None:
+        o.tuning = ctypes.pointer(tuning)
+    if workspace is not None:
+        o.workspace = ctypes.c_void_p(workspace.data_ptr())
+        o.ws_bytes = workspace.numel() * workspace.element_size()
+    return o
+
+
+def _rank_dtype(weight, rank_dtype):
+    torch = _torch()
+    if rank_dtype is None:
+        return torch.int32 if weight is None else torch.int64
+    return rank_dtype
+
+
+def rank_ex(succ, weight=None, out=None, rank_dtype=None, validate=False, seed=0x5EED,
+            max_lists=0, tuning=None, sync=True, stream=None, workspace=None):
+    """Rank a successor array held in a CUDA tensor.
+
+    Returns the rank tensor (int32 when unweighted, int64 when weighted,
+    unless rank_dtype says otherwise).  With sync=True the device status is
+    checked and errors raise LRError; with sync=False the call only queues
+    work on the stream (use device_status() later).
+    """
+    torch = _torch()
+    lib = load()
+    rdt = _rank_dtype(weight, rank_dtype)
+    sp = _dev_ptr(succ, "succ", _succ_dtypes())
+    n = succ.numel()
+    wp = None if weight is None else _dev_ptr(weight, "weight", (torch.int32, torch.int64))
+    if weight is not None and weight.numel() != n:
+        raise ValueError("weight and succ differ in length")
+    if out is None:
+        out = torch.empty(n, dtype=rdt, device=succ.device)
+    rp = _dev_ptr(out, "out", (torch.int32, torch.int64))
+    if out.numel() != n:
+        raise ValueError("out has the wrong length")
+    o = _opts(_wcode(weight), LR_I32 if out.dtype == torch.int32 else LR_I64, validate, seed,
+              max_lists, tuning, sync, workspace=workspace)
+    code = lib.lr_rank_ex(sp, wp, n, rp, ctypes.byref(o), _stream_handle(stream))
+    _check(code, "lr_rank_ex")
+    return out
+
+
+def rank(succ, weight=None, out=None, stream=None, **kw):
+    """The lr_rank entry point (waits for the device and checks the status)."""
+    return rank_ex(succ, weight, out=out, stream=stream, **kw)
+
+
+def rank_batch(offsets, succ, weight=None, out=None, rank_dtype=None, validate=False,
+               seed=0x5EED, max_lists=0, n_total=0, tuning=None, sync=True, stream=None,
+               workspace=None):
+    """Rank k instances back to back (offsets: CUDA int64[k+1], local ids)."""
+    torch = _torch()
+    lib = load()
+    op = _dev_ptr(offsets, "offsets", (torch.int64,))
+    k = offsets.numel() - 1
+    rdt = _rank_dtype(weight, rank_dtype)
+    sp = _dev_ptr(succ, "succ", _succ_dtypes())
+    wp = None if weight is None else _dev_ptr(weight, "weight", (torch.int32, torch.int64))
+    if out is None:
+        out = torch.empty(succ.numel(), dtype=rdt, device=succ.device)
+    rp = _dev_ptr(out, "out", (torch.int32, torch.int64))
+    o = _opts(_wcode(weight), LR_I32 if out.dtype == torch.int32 else LR_I64, validate, seed,
+              max_lists, tuning, sync, n_total=n_total or succ.numel(), workspace=workspace)
+    code = lib.lr_rank_batch_ex(op, sp, wp, rp, k, ctypes.byref(o), _stream_handle(stream))
+    _check(code, "lr_rank_batch_ex")
+    return out
+
+
+def rank_host(succ, weight=None, out=None, rank_dtype=None, validate=False, seed=0x5EED,
+              max_lists=0, stream=None):
+    """End-to-end form on host tensors / numpy arrays: copy in, rank, copy out."""
+    import numpy as np
+    torch = _torch()
+    lib = load()
+
+    def host_ptr(a):
+        if isinstance(a, torch.Tensor):
+            assert not a.is_cuda and a.is_contiguous()
+            return ctypes.c_void_p(a.data_ptr()), a.numel()
+        a = np.ascontiguousarray(a)
+        return a.ctypes.data_as(ctypes.c_void_p), a.size
+
+    sp, n = host_ptr(succ)
+    wp = None if weight is None else host_ptr(weight)[0]
+    if weight is None:
+        wt = LR_NONE
+    else:
+        wdt = weight.dtype
+        wt = LR_I32 if wdt in (torch.int32, np.int32, np.dtype(np.int32)) else LR_I64
+    if out is None:
+        rdt = rank_dtype or (np.int32 if weight is None else np.int64)
+        out = np.empty(n, dtype=rdt)
+    rp = host_ptr(out)[0]
+    o = _opts(wt, LR_I32 if out.dtype in (np.int32, torch.int32) else LR_I64, validate, seed, max_lists)
+    code = lib.lr_rank_host(sp, wp, n, rp, ctypes.byref(o), _stream_handle(stream))
+    _check(code, "lr_rank_host")
+    return out
+
+
+def device_status(stream=None):
+    """Wait for the stream; return the status code of its last call (0 = OK)."""
+    return load().lr_get_device_status(_stream_handle(stream))
+
+
+def workspace_size(n_total, k=0, weighted=False, rank64=None, max_lists=0, tuning=None):
+    if rank64 is None:
+        rank64 = weighted
+    o = _Opts()
+    load().lr_opts_default(ctypes.byref(o))
+    o.wtype = LR_I64 if weighted else LR_NONE
+    o.rtype = LR_I64 if rank64 else LR_I32
+    o.max_lists = int(max_lists)
+    if tuning is not None:
+        o.tuning = ctypes.pointer(tuning)
+    return int(load().lr_workspace_size(int(n_total), int(k), ctypes.byref(o)))
+
+
+def profile_enable(on=True):
+    _check(load().lr_profile_enable(1 if on else 0))
+
+
+def profile_read(reset=True):
+    p = _Profile()
+    _check(load().lr_profile_read(ctypes.byref(p), 1 if reset else 0))
+    return {f: getattr(p, f) for f, _ in _Profile._fields_}
+
+
+def kernel_launch_count():
+    return int(load().lr_kernel_launch_count())
+
+
+class Server:
+    """Continuous-batching ranking server (lr_server_* of the C ABI)."""
+
+    def __init__(self, budget_bytes=40_000_000_000, n_streams=2, max_batch=256,
+                 max_batch_elems=1 << 28, device=0, plain=False):
+        lib = load()
+        c = _ServerConfig()
+        lib.lr_server_config_default(ctypes.byref(c))
+        c.budget_bytes, c.n_streams, c.max_batch = int(budget_bytes), int(n_streams), int(max_batch)
+        c.max_batch_elems, c.device, c.plain = int(max_batch_elems), int(device), 1 if plain else 0
+        h = ctypes.c_void_p()
+        _check(lib.lr_server_create(ctypes.byref(c), ctypes.byref(h)), "lr_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, succ, weight=None, out=None, rank_dtype=None):
+        """Submit a request (CUDA tensors are ranked in place; host tensors are
+        copied by the server).  Returns a ticket."""
+        import numpy as np
+        torch = _torch()
+        on_dev = isinstance(succ, torch.Tensor) and succ.is_cuda
+        n = succ.numel() if isinstance(succ, torch.Tensor) else np.asarray(succ).size
+        if out is None:
+            rdt = rank_dtype or (torch.int32 if weight is None else torch.int64)
+            out = torch.empty(n, dtype=rdt, device=succ.device if on_dev else "cpu",
+                              pin_memory=False)
+        r = _Request()
+        r.succ = succ.data_ptr()
+        r.weight = None if weight is None else weight.data_ptr()
+        r.rank = out.data_ptr()
+        r.n = n
+        r.wtype = _wcode(weight)
+        r.rtype = LR_I32 if out.dtype == torch.int32 else LR_I64
+        r.on_device = 1 if on_dev else 0
+        t = ctypes.c_uint64()
+        _check(load().lr_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)), "lr_server_submit")
+        self._keep[t.value] = (succ, weight, out)
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        """Wait for a request; returns (rank tensor, result dict); raises on error."""
+        res = _Result()
+        code = load().lr_server_wait(self._h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(res))
+        keep = self._keep.pop(ticket, (None, None, None)) if code != 7 else self._keep.get(ticket)
+        info = {f: getattr(res, f) for f, _ in _Result._fields_}
+        if code != 0:
+            raise LRError(code, "request %d" % ticket)
+        return keep[2], info
+
+    def stats(self):
+        s = _ServerStats()
+        _check(load().lr_server_stats_get(self._h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in _ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            load().lr_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,662 @@
+// lr_engine.cu -- host engine of liblr.so: argument checks, the static level
+// plan, workspace layout, per-stream contexts, launch sequence, device status
+// and profiling.  Implements the C ABI declared in include/lr.h.
+//
+// Recursion plan (Section 2.1: rank the rulers' list recursively, then
+// propagate; Section 3 runs a few sparse ruling-set rounds before pointer
+// doubling).  The number of levels and every array size are fixed on the host
+// from n and a bound h on the number of lists:
+//   cap_0 = n,  cap_{l+1} = min(cap_l, ceil(cap_l / f_l) + h),
+// until a level fits the single-CTA base case.  The actual sizes are decided
+// on the device (each level's head scan writes the next level's size and
+// mode), so a call never waits for the device unless h has to be counted
+// first, and a call with a known bound can be captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "lr.h"
+#include "lr_engine.h"
+#include "lr_kernels.h"
+
+namespace lr {
+
+// ---------------------------------------------------------------- tuning
+static uint32_t env_u32(const char *spec, const char *key, uint32_t dflt) {
+  if (!spec) return dflt;
+  std::string s(spec), k = std::string(key) + "=";
+  size_t p = 0;
+  while ((p = s.find(k, p)) != std::string::npos) {
+    if (p == 0 || s[p - 1] == ',') return (uint32_t)strtoul(s.c_str() + p + k.size(), nullptr, 10);
+    p += k.size();
+  }
+  return dflt;
+}
+
+Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted) {
+  (void)n;
+  (void)weighted;
+  Tuning u;
+  u.f0_inv = 64;
+  u.f_inv = 8;
+  u.cutoff = 8192;
+  u.block = 256;
+  u.ctas = 0;
+  const char *env = getenv("LR_TUNING");
+  u.f0_inv = env_u32(env, "f0", u.f0_inv);
+  u.f_inv = env_u32(env, "f", u.f_inv);
+  u.cutoff = env_u32(env, "cutoff", u.cutoff);
+  u.block = env_u32(env, "block", u.block);
+  u.ctas = env_u32(env, "ctas", u.ctas);
+  u.xchg = env_u32(env, "xchg", 1);
+  if (t) {
+    if (t->f0_inv) u.f0_inv = t->f0_inv;
+    if (t->f_inv) u.f_inv = t->f_inv;
+    if (t->cutoff) u.cutoff = t->cutoff;
+    if (t->chase_block) u.block = t->chase_block;
+    if (t->chase_ctas) u.ctas = t->chase_ctas;
+  }
+  u.f0_inv = std::max<uint32_t>(2, u.f0_inv);
+  u.f_inv = std::max<uint32_t>(2, u.f_inv);
+  u.cutoff = std::min<uint32_t>(std::max<uint32_t>(u.cutoff, 64), kMaxCutoff);
+  if (u.block != 128 && u.block != 256 && u.block != 512) u.block = 256;
+  return u;
+}
+
+static uint32_t ceil_log2(uint64_t x) {
+  uint32_t b = 0;
+  while ((1ull << b) < x) ++b;
+  return b;
+}
+
+static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+int chase_grid_for(const Tuning &u, bool rec16) {
+  int per = u.ctas ? (int)u.ctas : chase_occupancy(rec16, (int)u.block);
+  return device_sm_count() * std::max(1, per);
+}
+
+// Static plan for n elements and at most h lists.
+Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,
+               uint64_t seed, int chase_grid, bool force_srs) {
+  Plan p;
+  memset(&p, 0, sizeof(p));
+  p.n = n;
+  p.rec16_0 = rec16_0;
+  p.rank_bytes = rank_bytes;
+  p.cutoff = u.cutoff;
+  p.chase_grid = chase_grid;
+  p.chase_block = (int)u.block;
+  p.hcap = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(h, std::max<uint64_t>(n, 1)));
+  p.cap[0] = (uint32_t)n;
+  p.f_inv[0] = u.f0_inv;
+  int L = 0;
+  if (n > u.cutoff || force_srs) {
+    for (;;) {
+      const uint64_t r = (p.cap[L] + p.f_inv[L] - 1) / p.f_inv[L];
+      const uint64_t nc = std::min<uint64_t>(p.cap[L], r + p.hcap);
+      ++L;
+      p.cap[L] = (uint32_t)nc;
+      p.f_inv[L] = u.f_inv;
+      if (nc <= u.cutoff) break;
+      if (L == kMaxLevels) break;
+      if (L == 1 && p.cap[0] <= u.cutoff) break;
+      if (L >= 3 && (uint64_t)p.cap[L] * 4 > (uint64_t)p.cap[L - 1] * 3) break;  // stalled
+    }
+  }
+  p.nlev = L + 1;
+  p.has_pd = p.cap[L] > u.cutoff;
+  p.pd_rounds = p.has_pd ? ceil_log2(p.cap[L]) + 1 : 0;
+  for (int l = 0; l <= L; ++l) p.seed[l] = splitmix64(seed + 0x9E37ull * (uint64_t)(l + 1));
+
+  // fixed part: independent of h
+  size_t o = 0;
+  p.off_desc = o; o = align_up(o + sizeof(LevelDesc) * (kMaxLevels + 1));
+  p.off_zero = o;
+  p.off_err = o; o = align_up(o + 16);
+  p.off_hcount = o; o = align_up(o + 16);
+  p.off_q = o; o = align_up(o + sizeof(uint32_t) * (size_t)chase_grid * kMaxLevels);
+  p.off_bcnt = o; o = align_up(o + sizeof(uint64_t) * kHeadBlocks);
+  p.zero_bytes = o - p.off_zero;
+  p.off_bitmap = o; o = align_up(o + sizeof(uint32_t) * ((n + 31) / 32));
+  p.off_work[0] = o; o = align_up(o + (rec16_0 ? 16 : 8) * (size_t)n);
+  p.fixed_bytes = o;
+  // variable part
+  o = 0;
+  for (int l = 1; l <= L; ++l) {
+    p.off_work[l] = o; o = align_up(o + 16 * (size_t)p.cap[l]);
+    p.off_R[l] = o; o = align_up(o + (size_t)rank_bytes * p.cap[l]);
+  }
+  p.off_hA = o; o = align_up(o + 4 * (size_t)p.hcap);
+  p.off_hB = o; o = align_up(o + 4 * (size_t)p.hcap);
+  p.off_ns = o; o = align_up(o + 4 * (size_t)p.hcap);
+  if (p.has_pd) {
+    p.off_pd[0] = o; o = align_up(o + 4 * (size_t)p.cap[L]);
+    p.off_pd[1] = o; o = align_up(o + 4 * (size_t)p.cap[L]);
+    p.off_pd[2] = o; o = align_up(o + 8 * (size_t)p.cap[L]);
+    p.off_pd[3] = o; o = align_up(o + 8 * (size_t)p.cap[L]);
+  }
+  p.var_bytes = std::max<size_t>(o, 256);
+  return p;
+}
+
+// ---------------------------------------------------------------- contexts
+static std::mutex g_mu;
+static std::map<std::pair<int, uintptr_t>, Ctx *> g_ctx;
+static bool g_setup_done[64];
+
+static lr_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LR_OK;
+  if (e == cudaErrorMemoryAllocation) return LR_ERR_OUT_OF_MEMORY;
+  if (e == cudaErrorStreamCaptureUnsupported || e == cudaErrorStreamCaptureInvalidated)
+    return LR_ERR_CAPTURE;
+  return LR_ERR_CUDA;
+}
+
+Ctx *get_ctx(cudaStream_t stream, lr_status *st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { *st = from_cuda(e); return nullptr; }
+  std::lock_guard<std::mutex> g(g_mu);
+  if (dev >= 0 && dev < 64 && !g_setup_done[dev]) {
+    e = kernels_setup();
+    if (e != cudaSuccess) { *st = from_cuda(e); return nullptr; }
+    g_setup_done[dev] = true;
+  }
+  auto key = std::make_pair(dev, (uintptr_t)stream);
+  auto it = g_ctx.find(key);
+  if (it != g_ctx.end()) { *st = LR_OK; return it->second; }
+  Ctx *c = new Ctx();
+  c->device = dev;
+  e = cudaMallocHost((void **)&c->host_words, 64);
+  if (e != cudaSuccess) { delete c; *st = LR_ERR_OUT_OF_MEMORY; return nullptr; }
+  memset(c->host_words, 0, 64);
+  g_ctx[key] = c;
+  *st = LR_OK;
+  return c;
+}
+
+static bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// Grow-only device buffer.
+lr_status ensure_buffer(void **buf, size_t *cur, size_t want, cudaStream_t s) {
+  if (*cur >= want && *buf) return LR_OK;
+  if (stream_capturing(s)) return LR_ERR_CAPTURE;
+  if (*buf) {
+    cudaStreamSynchronize(s);
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cur = 0;
+  }
+  size_t sz = std::max(want, (size_t)1 << 20);
+  cudaError_t e = cudaMalloc(buf, sz);
+  if (e != cudaSuccess) { cudaGetLastError(); *buf = nullptr; return LR_ERR_OUT_OF_MEMORY; }
+  *cur = sz;
+  return LR_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+static bool g_prof = false;
+struct ProfMark { cudaEvent_t ev; int phase; };  // phase of the interval ending here
+struct ProfCall { std::vector<ProfMark> marks; int64_t n; int64_t launches; };
+static std::vector<ProfCall> g_prof_pending;
+static lr_profile g_prof_acc;
+
+struct Profiler {
+  bool on = false;
+  ProfCall call;
+  cudaStream_t s = nullptr;
+  void begin(cudaStream_t st, int64_t n) {
+    on = g_prof && !stream_capturing(st);
+    s = st;
+    if (!on) return;
+    call.n = n;
+    call.launches = launch_count();
+    mark(-1);
+  }
+  void mark(int phase) {
+    if (!on) return;
+    ProfMark m;
+    m.phase = phase;
+    cudaEventCreate(&m.ev);
+    cudaEventRecord(m.ev, s);
+    call.marks.push_back(m);
+  }
+  void end() {
+    if (!on) return;
+    call.launches = launch_count() - call.launches;
+    std::lock_guard<std::mutex> g(g_mu);
+    g_prof_pending.push_back(call);
+  }
+};
+enum { PH_PREP = 0, PH_SELECT, PH_CHASE0, PH_CHASE, PH_BASE, PH_FINAL };
+
+// ---------------------------------------------------------------- the run
+struct Inputs {
+  const uint32_t *succ;
+  const void *weight;
+  int wtype;          // 0 none, 1 i32, 2 i64
+  void *rank;
+  int rank_bytes;
+  uint64_t n;
+  const int64_t *offsets;  // batched form
+  int32_t k;
+  int validate;
+  uint64_t seed;
+  int64_t max_lists;
+  int sync;
+  void *ws;
+  size_t ws_bytes;
+  const uint32_t *const *sptr;   // per-instance pointer tables (device), or null
+  const void *const *wptr;
+  void *const *rptr;
+};
+
+static lr_status map_device_bits(uint32_t bits) {
+  if (bits & kErrRange) return LR_ERR_OUT_OF_RANGE;
+  if (bits & kErrNotList) return LR_ERR_NOT_A_LIST;
+  if (bits & kErrCycle) return LR_ERR_CYCLE;
+  if (bits & kErrCapacity) return LR_ERR_CAPACITY;
+  if (bits & kErrInternal) return LR_ERR_NOT_A_LIST;
+  return LR_OK;
+}
+
+#define LR_TRY(expr)                                   \
+  do {                                                 \
+    cudaError_t e__ = (expr);                          \
+    if (e__ != cudaSuccess) return from_cuda(e__);     \
+  } while (0)
+
+lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
+  const bool ptrs = in.sptr != nullptr;
+  lr_status st;
+  Ctx *c = get_ctx(s, &st);
+  if (!c) return st;
+  if (in.n == 0) {
+    // nothing to rank; still clear the stream's recorded status
+    c->host_words[0] = 0;
+    c->pending_status = false;
+    return LR_OK;
+  }
+  const bool capturing = stream_capturing(s);
+  const Tuning u = resolve_tuning(tuning, (int64_t)in.n, in.wtype != 0);
+  const bool rec16_0 = in.wtype != 0;
+  const int grid = chase_grid_for(u, rec16_0);
+  const bool need_count = in.max_lists <= 0 && in.ws == nullptr && (in.n > u.cutoff || ptrs);
+  if (need_count && capturing) return LR_ERR_CAPTURE;
+  uint64_t hb = in.max_lists > 0 ? (uint64_t)in.max_lists : in.n;
+  Plan p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs);
+
+  // fixed part (level 0)
+  char *fixed = nullptr;
+  char *var = nullptr;
+  if (in.ws) {
+    if (in.ws_bytes < p.fixed_bytes + p.var_bytes) return LR_ERR_INVALID_ARGUMENT;
+    fixed = (char *)in.ws;
+    var = fixed + p.fixed_bytes;
+  } else {
+    st = ensure_buffer(&c->fixed, &c->fixed_bytes, p.fixed_bytes, s);
+    if (st != LR_OK) return st;
+    fixed = (char *)c->fixed;
+  }
+  LevelDesc *desc = (LevelDesc *)(fixed + p.off_desc);
+  uint32_t *err = (uint32_t *)(fixed + p.off_err);
+  uint32_t *hcount = (uint32_t *)(fixed + p.off_hcount);
+  uint32_t *qctr = (uint32_t *)(fixed + p.off_q);
+  uint64_t *bcnt = (uint64_t *)(fixed + p.off_bcnt);
+  uint32_t *bitmap = (uint32_t *)(fixed + p.off_bitmap);
+  void *work0 = fixed + p.off_work[0];
+
+  Profiler prof;
+  prof.begin(s, (int64_t)in.n);
+  LR_TRY(cudaMemsetAsync(fixed + p.off_zero, 0, p.zero_bytes, s));
+  LR_TRY(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * ((in.n + 31) / 32), s));
+  if (ptrs)
+    LR_TRY(launch_prep0_ptrs(in.sptr, in.wptr, in.wtype, (uint32_t)in.n, work0, bitmap, err,
+                             in.validate, in.offsets, in.k, s));
+  else
+    LR_TRY(launch_prep0(in.succ, in.weight, in.wtype, (uint32_t)in.n, work0, bitmap, err,
+                        in.validate, in.offsets, in.k, s));
+  if (need_count) {
+    // count the heads (one wait), then size the recursion for exactly that many lists
+    LR_TRY(launch_count_heads(bitmap, (uint32_t)in.n, hcount, s));
+    LR_TRY(cudaMemcpyAsync(c->host_words + 1, hcount, 4, cudaMemcpyDeviceToHost, s));
+    LR_TRY(cudaStreamSynchronize(s));
+    hb = std::max<uint64_t>(1, c->host_words[1]);
+    p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs);
+  }
+  if (!in.ws) {
+    st = ensure_buffer(&c->var, &c->var_bytes, p.var_bytes, s);
+    if (st != LR_OK) return st;
+    var = (char *)c->var;
+  }
+  prof.mark(PH_PREP);
+
+  InitParams ip;
+  memset(&ip, 0, sizeof(ip));
+  ip.nlev = p.nlev;
+  ip.n0 = (uint32_t)in.n;
+  ip.mode0 = p.nlev == 1 ? kModeBase : kModeSrs;
+  ip.cutoff = p.cutoff;
+  for (int l = 0; l < p.nlev; ++l) {
+    ip.f_inv[l] = p.f_inv[l];
+    ip.cap[l] = p.cap[l];
+    ip.seed[l] = p.seed[l];
+  }
+  ip.pd_rounds = p.pd_rounds;
+  ip.has_pd = p.has_pd;
+  ip.hcap = p.hcap;
+  LR_TRY(launch_init(desc, ip, s));
+
+  auto work_of = [&](int l) -> void * { return l == 0 ? work0 : (void *)(var + p.off_work[l]); };
+  auto R_of = [&](int l) -> void * { return l == 0 ? in.rank : (void *)(var + p.off_R[l]); };
+  uint32_t *hA = (uint32_t *)(var + p.off_hA);
+  uint32_t *hB = (uint32_t *)(var + p.off_hB);
+  uint32_t *ns = (uint32_t *)(var + p.off_ns);
+  const int L = p.nlev - 1;
+  for (int l = 0; l < L; ++l) {
+    const bool r16 = l > 0 || rec16_0;
+    uint32_t *hin = (l & 1) ? hB : hA;
+    uint32_t *hout = (l & 1) ? hA : hB;
+    if (l > 0) {
+      LR_TRY(launch_base(desc, l, work_of(l), r16, R_of(l), p.rank_bytes, p.cutoff, err, s));
+      prof.mark(PH_BASE);
+    }
+    LR_TRY(launch_heads(desc, l, p.nlev, bitmap, hin, work_of(l), r16, ns, hout, bcnt, err,
+                        p.cutoff, p.hcap, p.has_pd ? 1u : 0u, s));
+    prof.mark(PH_SELECT);
+    LR_TRY(launch_chase(desc, l, work_of(l), r16, work_of(l + 1), ns,
+                        qctr + (size_t)l * p.chase_grid, p.chase_grid, p.chase_block, err,
+                        (int)u.xchg, s));
+    prof.mark(l == 0 ? PH_CHASE0 : PH_CHASE);
+  }
+  LR_TRY(launch_base(desc, L, work_of(L), L > 0 || rec16_0, R_of(L), p.rank_bytes, p.cutoff, err, s));
+  if (p.has_pd) {
+    LR_TRY(launch_pd(desc, L, work_of(L), p.cap[L], p.pd_rounds, (uint32_t *)(var + p.off_pd[0]),
+                     (uint32_t *)(var + p.off_pd[1]), (uint64_t *)(var + p.off_pd[2]),
+                     (uint64_t *)(var + p.off_pd[3]), R_of(L), p.rank_bytes, err, s));
+  }
+  prof.mark(PH_BASE);
+  for (int l = L - 1; l >= 0; --l) {
+    if (l == 0 && ptrs)
+      LR_TRY(launch_finalize_ptrs(desc, work0, rec16_0, R_of(1), in.rptr, p.rank_bytes, p.cap[0],
+                                  in.offsets, in.k, err, s));
+    else
+      LR_TRY(launch_finalize(desc, l, work_of(l), l > 0 || rec16_0, R_of(l + 1), R_of(l),
+                             p.rank_bytes, p.cap[l], err, s));
+  }
+  prof.mark(PH_FINAL);
+  prof.end();
+  LR_TRY(cudaMemcpyAsync(c->host_words, err, 4, cudaMemcpyDeviceToHost, s));
+  c->pending_status = true;
+  if (in.sync) {
+    LR_TRY(cudaStreamSynchronize(s));
+    c->pending_status = false;
+    const uint32_t bits = c->host_words[0];
+    c->host_words[0] = 0;
+    return map_device_bits(bits);
+  }
+  return LR_OK;
+}
+
+lr_status run_ptr_batch(const int64_t *offsets, int32_t k, int64_t n_total,
+                        const uint32_t *const *sptr, const void *const *wptr, void *const *rptr,
+                        int wtype, int rank_bytes, uint64_t seed, cudaStream_t s) {
+  Inputs in;
+  memset(&in, 0, sizeof(in));
+  in.n = (uint64_t)n_total;
+  in.offsets = offsets;
+  in.k = k;
+  in.sptr = sptr;
+  in.wptr = wptr;
+  in.rptr = rptr;
+  in.wtype = wtype;
+  in.rank_bytes = rank_bytes;
+  in.seed = seed;
+  in.sync = 1;
+  return run(in, nullptr, s);
+}
+
+lr_status device_status(cudaStream_t s) {
+  lr_status st;
+  Ctx *c = get_ctx(s, &st);
+  if (!c) return st;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  const uint32_t bits = c->host_words[0];
+  c->host_words[0] = 0;
+  c->pending_status = false;
+  return map_device_bits(bits);
+}
+
+}  // namespace lr
+
+// ================================================================ C ABI
+using namespace lr;
+
+extern "C" {
+
+void lr_opts_default(lr_opts *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->wtype = LR_NONE;
+  o->rtype = LR_I32;
+  o->seed = 0x5eedull;
+}
+
+const char *lr_version(void) { return "lr-gb300 0.1 (sparse ruling set, sm_103a)"; }
+
+const char *lr_status_string(lr_status s) {
+  switch (s) {
+    case LR_OK: return "LR_OK";
+    case LR_ERR_INVALID_ARGUMENT: return "LR_ERR_INVALID_ARGUMENT";
+    case LR_ERR_OUT_OF_RANGE: return "LR_ERR_OUT_OF_RANGE";
+    case LR_ERR_CYCLE: return "LR_ERR_CYCLE";
+    case LR_ERR_NOT_A_LIST: return "LR_ERR_NOT_A_LIST";
+    case LR_ERR_OUT_OF_MEMORY: return "LR_ERR_OUT_OF_MEMORY";
+    case LR_ERR_BUDGET: return "LR_ERR_BUDGET";
+    case LR_ERR_TIMEOUT: return "LR_ERR_TIMEOUT";
+    case LR_ERR_CUDA: return "LR_ERR_CUDA";
+    case LR_ERR_CAPACITY: return "LR_ERR_CAPACITY";
+    case LR_ERR_NOT_FOUND: return "LR_ERR_NOT_FOUND";
+    case LR_ERR_CANCELLED: return "LR_ERR_CANCELLED";
+    case LR_ERR_CAPTURE: return "LR_ERR_CAPTURE";
+  }
+  return "LR_ERR_UNKNOWN";
+}
+
+static lr_status check_types(const void *weight, lr_dtype wtype, lr_dtype rtype, int *wcode, int *rbytes) {
+  if (rtype != LR_I32 && rtype != LR_I64) return LR_ERR_INVALID_ARGUMENT;
+  if (wtype != LR_NONE && wtype != LR_I32 && wtype != LR_I64) return LR_ERR_INVALID_ARGUMENT;
+  if ((wtype == LR_NONE) != (weight == nullptr)) return LR_ERR_INVALID_ARGUMENT;
+  *wcode = (int)wtype;
+  *rbytes = rtype == LR_I32 ? 4 : 8;
+  return LR_OK;
+}
+
+lr_status lr_rank_ex(const uint32_t *succ, const void *weight, int64_t n, void *rank,
+                     const lr_opts *opts, lr_stream stream) {
+  lr_opts d;
+  if (!opts) { lr_opts_default(&d); if (weight) { d.wtype = LR_I64; d.rtype = LR_I64; } opts = &d; }
+  if (n < 0 || n > LR_MAX_N) return LR_ERR_INVALID_ARGUMENT;
+  if (n > 0 && (!succ || !rank)) return LR_ERR_INVALID_ARGUMENT;
+  int wc, rb;
+  lr_status st = check_types(n > 0 ? weight : (opts->wtype ? (const void *)1 : nullptr),
+                             opts->wtype, opts->rtype, &wc, &rb);
+  if (st != LR_OK) return st;
+  Inputs in;
+  memset(&in, 0, sizeof(in));
+  in.succ = succ;
+  in.weight = weight;
+  in.wtype = wc;
+  in.rank = rank;
+  in.rank_bytes = rb;
+  in.n = (uint64_t)n;
+  in.validate = opts->validate;
+  in.seed = opts->seed;
+  in.max_lists = opts->max_lists;
+  in.sync = opts->sync;
+  in.ws = opts->workspace;
+  in.ws_bytes = opts->ws_bytes;
+  return run(in, opts->tuning, (cudaStream_t)stream);
+}
+
+lr_status lr_rank(const uint32_t *succ, const void *weight, int64_t n, void *rank, lr_stream stream) {
+  lr_opts o;
+  lr_opts_default(&o);
+  if (weight) { o.wtype = LR_I64; o.rtype = LR_I64; }
+  else if (n >= ((int64_t)1 << 31)) return LR_ERR_INVALID_ARGUMENT;  // int32 ranks
+  return lr_rank_ex(succ, weight, n, rank, &o, stream);
+}
+
+lr_status lr_rank_batch_ex(const int64_t *offsets, const uint32_t *succ, const void *weight,
+                           void *rank, int32_t k, const lr_opts *opts, lr_stream stream) {
+  lr_opts d;
+  if (!opts) { lr_opts_default(&d); if (weight) { d.wtype = LR_I64; d.rtype = LR_I64; } opts = &d; }
+  if (k < 0 || (k > 0 && !offsets)) return LR_ERR_INVALID_ARGUMENT;
+  if (k == 0) return LR_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int64_t n = opts->n_total;
+  if (n <= 0) {
+    if (stream_capturing(s)) return LR_ERR_CAPTURE;
+    lr_status st;
+    Ctx *c = get_ctx(s, &st);
+    if (!c) return st;
+    int64_t *h = (int64_t *)(c->host_words + 8);
+    cudaError_t e = cudaMemcpyAsync(h, offsets + k, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return from_cuda(e);
+    n = *h;
+  }
+  if (n < 0 || n > LR_MAX_N) return LR_ERR_INVALID_ARGUMENT;
+  if (n > 0 && (!succ || !rank)) return LR_ERR_INVALID_ARGUMENT;
+  int wc, rb;
+  lr_status st = check_types(n > 0 ? weight : (opts->wtype ? (const void *)1 : nullptr),
+                             opts->wtype, opts->rtype, &wc, &rb);
+  if (st != LR_OK) return st;
+  Inputs in;
+  memset(&in, 0, sizeof(in));
+  in.succ = succ;
+  in.weight = weight;
+  in.wtype = wc;
+  in.rank = rank;
+  in.rank_bytes = rb;
+  in.n = (uint64_t)n;
+  in.offsets = offsets;
+  in.k = k;
+  in.validate = opts->validate;
+  in.seed = opts->seed;
+  in.max_lists = opts->max_lists;
+  in.sync = opts->sync;
+  in.ws = opts->workspace;
+  in.ws_bytes = opts->ws_bytes;
+  return run(in, opts->tuning, s);
+}
+
+lr_status lr_rank_batch(const int64_t *offsets, const uint32_t *succ, const void *weight,
+                        void *rank, int32_t k, lr_stream stream) {
+  lr_opts o;
+  lr_opts_default(&o);
+  if (weight) { o.wtype = LR_I64; o.rtype = LR_I64; }
+  return lr_rank_batch_ex(offsets, succ, weight, rank, k, &o, stream);
+}
+
+lr_status lr_rank_host(const uint32_t *succ_host, const void *weight_host, int64_t n,
+                       void *rank_host, const lr_opts *opts, lr_stream stream) {
+  lr_opts d;
+  if (!opts) { lr_opts_default(&d); if (weight_host) { d.wtype = LR_I64; d.rtype = LR_I64; } opts = &d; }
+  if (n < 0 || n > LR_MAX_N) return LR_ERR_INVALID_ARGUMENT;
+  if (n == 0) return LR_OK;
+  if (!succ_host || !rank_host) return LR_ERR_INVALID_ARGUMENT;
+  int wc, rb;
+  lr_status st = check_types(weight_host, opts->wtype, opts->rtype, &wc, &rb);
+  if (st != LR_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (stream_capturing(s)) return LR_ERR_CAPTURE;
+  Ctx *c = get_ctx(s, &st);
+  if (!c) return st;
+  const size_t wb = wc == 0 ? 0 : (wc == 1 ? 4 : 8);
+  const size_t bs = align_up(4 * (size_t)n), bw = align_up(wb * (size_t)n), br = align_up((size_t)rb * n);
+  st = ensure_buffer(&c->hostpath, &c->hostpath_bytes, bs + bw + br, s);
+  if (st != LR_OK) return st;
+  char *b = (char *)c->hostpath;
+  uint32_t *dsucc = (uint32_t *)b;
+  void *dw = wb ? (void *)(b + bs) : nullptr;
+  void *drank = b + bs + bw;
+  LR_TRY(cudaMemcpyAsync(dsucc, succ_host, 4 * (size_t)n, cudaMemcpyHostToDevice, s));
+  if (wb) LR_TRY(cudaMemcpyAsync(dw, weight_host, wb * (size_t)n, cudaMemcpyHostToDevice, s));
+  lr_opts o = *opts;
+  o.sync = 0;
+  st = lr_rank_ex(dsucc, dw, n, drank, &o, stream);
+  if (st != LR_OK) return st;
+  LR_TRY(cudaMemcpyAsync(rank_host, drank, (size_t)rb * n, cudaMemcpyDeviceToHost, s));
+  return device_status(s);
+}
+
+size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts) {
+  (void)k;
+  lr_opts d;
+  if (!opts) { lr_opts_default(&d); opts = &d; }
+  if (n_total <= 0) return 0;
+  const Tuning u = resolve_tuning(opts->tuning, n_total, opts->wtype != LR_NONE);
+  // The chase grid depends on the device; size for a generous upper bound so
+  // the answer needs no GPU: 256 SMs x 16 CTAs.
+  const uint64_t h = opts->max_lists > 0 ? (uint64_t)opts->max_lists : (uint64_t)n_total;
+  Plan p = make_plan((uint64_t)n_total, h, u, opts->wtype != LR_NONE,
+                     opts->rtype == LR_I64 ? 8 : 4, opts->seed, 256 * 16, false);
+  return p.fixed_bytes + p.var_bytes;
+}
+
+lr_status lr_get_device_status(lr_stream stream) { return device_status((cudaStream_t)stream); }
+
+lr_status lr_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> g(g_mu);
+  g_prof = on != 0;
+  return LR_OK;
+}
+
+lr_status lr_profile_read(lr_profile *out, int32_t reset) {
+  std::vector<ProfCall> pend;
+  {
+    std::lock_guard<std::mutex> g(g_mu);
+    pend.swap(g_prof_pending);
+  }
+  for (auto &call : pend) {
+    for (size_t i = 1; i < call.marks.size(); ++i) {
+      float ms = 0.f;
+      cudaEventSynchronize(call.marks[i].ev);
+      cudaEventElapsedTime(&ms, call.marks[i - 1].ev, call.marks[i].ev);
+      switch (call.marks[i].phase) {
+        case PH_PREP: g_prof_acc.ms_prep += ms; break;
+        case PH_SELECT: g_prof_acc.ms_select += ms; break;
+        case PH_CHASE0: g_prof_acc.ms_chase0 += ms; g_prof_acc.chase0_launches += 1; break;
+        case PH_CHASE: g_prof_acc.ms_chase_rest += ms; break;
+        case PH_BASE: g_prof_acc.ms_base += ms; break;
+        case PH_FINAL: g_prof_acc.ms_finalize += ms; break;
+      }
+    }
+    for (auto &m : call.marks) cudaEventDestroy(m.ev);
+    g_prof_acc.calls += 1;
+    g_prof_acc.kernel_launches += call.launches;
+    g_prof_acc.elements += call.n;
+  }
+  if (out) *out = g_prof_acc;
+  if (reset) memset(&g_prof_acc, 0, sizeof(g_prof_acc));
+  return LR_OK;
+}
+
+int64_t lr_kernel_launch_count(void) { return launch_count(); }
+
+}  // extern "C"

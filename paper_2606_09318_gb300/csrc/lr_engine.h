@@ -1,0 +1,64 @@
+// lr_engine.h -- host engine internals shared by lr_engine.cu and the server.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lr.h"
+#include "lr_device.cuh"
+
+namespace lr {
+
+struct Tuning {
+  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg;
+};
+
+struct Plan {
+  uint64_t n;
+  int nlev;                         // levels 0..nlev-1; the last one is base or fallback
+  uint32_t cap[kMaxLevels + 1];
+  uint32_t f_inv[kMaxLevels + 1];
+  uint64_t seed[kMaxLevels + 1];
+  bool has_pd;
+  uint32_t pd_rounds;
+  uint32_t hcap;                    // head-list capacity (bound on lists)
+  uint32_t cutoff;
+  bool rec16_0;
+  int rank_bytes;
+  int chase_grid, chase_block;
+  // fixed part (does not depend on the list bound)
+  size_t off_desc, off_zero, zero_bytes, off_err, off_hcount, off_q, off_bcnt, off_bitmap;
+  size_t fixed_bytes;
+  // variable part
+  size_t off_work[kMaxLevels + 1], off_R[kMaxLevels + 1];
+  size_t off_hA, off_hB, off_ns, off_pd[4];
+  size_t var_bytes;
+};
+
+// One per (device, stream): grow-only workspaces and a pinned status word.
+struct Ctx {
+  int device = 0;
+  void *fixed = nullptr;
+  size_t fixed_bytes = 0;
+  void *var = nullptr;
+  size_t var_bytes = 0;
+  void *hostpath = nullptr;
+  size_t hostpath_bytes = 0;
+  uint32_t *host_words = nullptr;   // [0] device error bits, [1] head count, [8..9] int64 scratch
+  bool pending_status = false;
+};
+
+Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted);
+Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,
+               uint64_t seed, int chase_grid, bool force_srs);
+int chase_grid_for(const Tuning &u, bool rec16);
+Ctx *get_ctx(cudaStream_t stream, lr_status *st);
+lr_status ensure_buffer(void **buf, size_t *cur, size_t want, cudaStream_t s);
+lr_status device_status(cudaStream_t s);
+// Rank k instances given by per-instance device pointers (tables in device
+// memory); waits for the result and returns the status.
+lr_status run_ptr_batch(const int64_t *offsets, int32_t k, int64_t n_total,
+                        const uint32_t *const *sptr, const void *const *wptr, void *const *rptr,
+                        int wtype, int rank_bytes, uint64_t seed, cudaStream_t s);
+
+}  // namespace lr

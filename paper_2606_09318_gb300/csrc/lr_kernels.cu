@@ -1,0 +1,787 @@
+// lr_kernels.cu -- CUDA kernels of the sparse ruling-set list ranker (sm_103a).
+//
+// Pipeline of one call (Section 2.1, Algorithm 1 of "Engineering Scalable
+// Distributed List Ranking", restated for one GPU):
+//   prep0      level-0 pass: range check, has-predecessor bitmap (findInit),
+//              pack succ (and the link weight) into per-element records;
+//   heads      per level: classify the heads (initial elements) into sampled
+//              rulers, extra rulers and resolved singletons, and number the
+//              extra rulers after the sampled ones (pickRulers);
+//   chase      per level: one thread per ruler walks succ to the next ruler,
+//              rewriting each visited record as (ruler id, offset) and
+//              emitting one record of the reduced list (ruler chasing);
+//   base       single-CTA pointer doubling (Wyllie) once a level is small
+//              enough (the base case), or a grid-wide pointer-doubling
+//              fallback for a large last level;
+//   finalize   per level, deepest first: R_l[i] = R_{l+1}[ruler(i)] - offset(i)
+//              (ruler propagation).
+// The chase records the *next* ruler, so ranks come out relative to the
+// terminal directly and the list never has to be reversed (Section 2.1 notes
+// that the distributed algorithm needs a reversal or the post-processing of
+// Section 2.5; walking succ forward from each ruler makes both unnecessary).
+#include <atomic>
+#include <cstdio>
+
+#include "lr_kernels.h"
+
+namespace lr {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return sms > 0 ? sms : 1;
+}
+
+static int stream_grid(uint64_t work_items, int block) {
+  // grid-stride kernels: enough CTAs to fill every SM, no more than needed
+  uint64_t want = (work_items + block - 1) / block;
+  uint64_t full = (uint64_t)device_sm_count() * (2048 / block);
+  if (want < 1) want = 1;
+  return (int)(want < full ? want : full);
+}
+
+// ---------------------------------------------------------------- init
+__global__ void k_init(LevelDesc *desc, InitParams p) {
+  const int l = threadIdx.x;
+  if (l < p.nlev) {
+    LevelDesc x;
+    x.mode = l == 0 ? p.mode0 : (uint32_t)kModeOff;
+    x.n = l == 0 ? p.n0 : 0u;
+    x.f_inv = p.f_inv[l];
+    x.r = l == 0 ? (uint32_t)(((uint64_t)p.n0 + p.f_inv[0] - 1) / p.f_inv[0]) : 0u;
+    x.k = 0;
+    x.h = 0;
+    x.visited = 0;
+    x.cap = p.cap[l];
+    x.seed = p.seed[l];
+    x.rounds = p.pd_rounds;
+    x.pad = 0;
+    desc[l] = x;
+  }
+}
+
+cudaError_t launch_init(LevelDesc *desc, const InitParams &p, cudaStream_t s) {
+  k_init<<<1, 32, 0, s>>>(desc, p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- prep0
+template <int WT>
+__device__ __forceinline__ uint64_t load_weight(const void *w, uint32_t i) {
+  if constexpr (WT == 1) return (uint64_t)(int64_t)__ldcs(reinterpret_cast<const int *>(w) + i);
+  else if constexpr (WT == 2) return (uint64_t)__ldcs(reinterpret_cast<const long long *>(w) + i);
+  else return 1u;
+}
+
+// One pass over the input: check every successor, mark the has-predecessor
+// bit of every successor (the complement gives the heads, Algorithm 1's
+// findInit), and pack {succ, kUnvisited[, link weight]} records.  A terminal's
+// weight is stored as 0, so every deeper computation can treat weights
+// inclusively.
+template <int WT>
+__global__ void __launch_bounds__(256)
+k_prep0(const uint32_t *__restrict__ succ, const void *__restrict__ weight, uint32_t n,
+        void *__restrict__ work, uint32_t *__restrict__ bitmap, uint32_t *__restrict__ err,
+        int validate, int vec, const int64_t *__restrict__ offsets, int32_t k) {
+  const uint32_t ngroups = (uint32_t)(((uint64_t)n + 3u) / 4u);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+    const uint32_t i0 = g * 4u;
+    const uint32_t cnt = min(4u, n - i0);
+    uint32_t s[4];
+    uint64_t w[4];
+    if (vec && cnt == 4u) {
+      uint4 v = __ldcs(reinterpret_cast<const uint4 *>(succ + i0));
+      s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
+      if constexpr (WT == 1) {
+        int4 q = __ldcs(reinterpret_cast<const int4 *>(reinterpret_cast<const int *>(weight) + i0));
+        w[0] = (uint64_t)(int64_t)q.x; w[1] = (uint64_t)(int64_t)q.y;
+        w[2] = (uint64_t)(int64_t)q.z; w[3] = (uint64_t)(int64_t)q.w;
+      } else if constexpr (WT == 2) {
+        const longlong2 *wp = reinterpret_cast<const longlong2 *>(reinterpret_cast<const long long *>(weight) + i0);
+        longlong2 a = __ldcs(wp), b = __ldcs(wp + 1);
+        w[0] = (uint64_t)a.x; w[1] = (uint64_t)a.y; w[2] = (uint64_t)b.x; w[3] = (uint64_t)b.y;
+      } else {
+        w[0] = w[1] = w[2] = w[3] = 1u;
+      }
+    } else {
+      for (uint32_t j = 0; j < 4u; ++j) {
+        s[j] = j < cnt ? __ldcs(succ + i0 + j) : 0u;
+        w[j] = j < cnt ? load_weight<WT>(weight, i0 + j) : 0u;
+      }
+    }
+    if (offsets != nullptr) {
+      // batched input: instance of i0 by binary search, then walk forward
+      int32_t lo = 0, hi = k;
+      while (hi - lo > 1) {
+        int32_t mid = (lo + hi) >> 1;
+        if ((uint64_t)__ldg(offsets + mid) <= i0) lo = mid; else hi = mid;
+      }
+      uint64_t base = (uint64_t)__ldg(offsets + lo), end = (uint64_t)__ldg(offsets + lo + 1);
+      for (uint32_t j = 0; j < cnt; ++j) {
+        const uint32_t i = i0 + j;
+        while (i >= end && lo + 1 < k) { ++lo; base = end; end = (uint64_t)__ldg(offsets + lo + 1); }
+        const uint64_t g = base + s[j];
+        if (i < base || i >= end || (uint64_t)s[j] >= end - base || g >= n) {
+          record_error(err, kErrRange);   // successor outside its instance (or a bad table)
+          s[j] = i;
+        } else {
+          s[j] = (uint32_t)g;
+        }
+      }
+    } else {
+      for (uint32_t j = 0; j < cnt; ++j)
+        if (s[j] >= n) { record_error(err, kErrRange); s[j] = i0 + j; }
+    }
+    for (uint32_t j = 0; j < cnt; ++j) {
+      const uint32_t i = i0 + j;
+      if (s[j] != i) {
+        const uint32_t bit = 1u << (s[j] & 31u);
+        if (validate) {
+          if (atomicOr(bitmap + (s[j] >> 5), bit) & bit) record_error(err, kErrNotList);
+        } else {
+          atomicOr(bitmap + (s[j] >> 5), bit);
+        }
+      } else {
+        w[j] = 0u;   // a terminal has no outgoing link
+      }
+    }
+    if constexpr (WT == 0) {
+      uint2 *out = reinterpret_cast<uint2 *>(work) + i0;
+      if (cnt == 4u) {
+        uint4 *o4 = reinterpret_cast<uint4 *>(out);
+        __stcs(o4, make_uint4(s[0], kUnvisited, s[1], kUnvisited));
+        __stcs(o4 + 1, make_uint4(s[2], kUnvisited, s[3], kUnvisited));
+      } else {
+        for (uint32_t j = 0; j < cnt; ++j) out[j] = make_uint2(s[j], kUnvisited);
+      }
+    } else {
+      uint4 *out = reinterpret_cast<uint4 *>(work) + i0;
+      for (uint32_t j = 0; j < cnt; ++j)
+        __stcs(out + j, make_uint4(s[j], kUnvisited, (uint32_t)w[j], (uint32_t)(w[j] >> 32)));
+    }
+  }
+}
+
+cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, uint32_t n,
+                         void *work, uint32_t *bitmap, uint32_t *err, int validate,
+                         const int64_t *offsets, int32_t k, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int block = 256;
+  const int grid = stream_grid(((uint64_t)n + 3) / 4, block);
+  int vec = ((uintptr_t)succ & 15u) == 0;
+  if (wtype == 1) vec = vec && ((uintptr_t)weight & 15u) == 0;
+  if (wtype == 2) vec = vec && ((uintptr_t)weight & 15u) == 0;
+  switch (wtype) {
+    case 0: k_prep0<0><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k); break;
+    case 1: k_prep0<1><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k); break;
+    default: k_prep0<2><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k); break;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Batched input given as one device pointer per instance (the serving path
+// ranks requests where they already live, without gathering them first).
+template <int WT>
+__global__ void __launch_bounds__(256)
+k_prep0_ptrs(const uint32_t *const *__restrict__ sptr, const void *const *__restrict__ wptr,
+             uint32_t n, void *__restrict__ work, uint32_t *__restrict__ bitmap,
+             uint32_t *__restrict__ err, int validate, const int64_t *__restrict__ offsets, int32_t k) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int32_t lo = 0, hi = k;
+    while (hi - lo > 1) {
+      int32_t mid = (lo + hi) >> 1;
+      if ((uint64_t)__ldg(offsets + mid) <= i) lo = mid; else hi = mid;
+    }
+    const uint64_t base = (uint64_t)__ldg(offsets + lo), len = (uint64_t)__ldg(offsets + lo + 1) - base;
+    const uint64_t loc = i - base;
+    uint32_t s = __ldcs(sptr[lo] + loc);
+    uint64_t w = 1u;
+    if constexpr (WT == 1) w = (uint64_t)(int64_t)__ldcs(reinterpret_cast<const int *>(wptr[lo]) + loc);
+    if constexpr (WT == 2) w = (uint64_t)__ldcs(reinterpret_cast<const long long *>(wptr[lo]) + loc);
+    if ((uint64_t)s >= len || base + s >= n) { record_error(err, kErrRange); s = i; }
+    else s = (uint32_t)(base + s);
+    if (s != i) {
+      const uint32_t bit = 1u << (s & 31u);
+      if (validate) {
+        if (atomicOr(bitmap + (s >> 5), bit) & bit) record_error(err, kErrNotList);
+      } else {
+        atomicOr(bitmap + (s >> 5), bit);
+      }
+    } else {
+      w = 0u;
+    }
+    if constexpr (WT == 0) reinterpret_cast<uint2 *>(work)[i] = make_uint2(s, kUnvisited);
+    else __stcs(reinterpret_cast<uint4 *>(work) + i, make_uint4(s, kUnvisited, (uint32_t)w, (uint32_t)(w >> 32)));
+  }
+}
+
+cudaError_t launch_prep0_ptrs(const uint32_t *const *sptr, const void *const *wptr, int wtype,
+                              uint32_t n, void *work, uint32_t *bitmap, uint32_t *err, int validate,
+                              const int64_t *offsets, int32_t k, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int block = 256;
+  const int grid = stream_grid(n, block);
+  switch (wtype) {
+    case 0: k_prep0_ptrs<0><<<grid, block, 0, s>>>(sptr, wptr, n, work, bitmap, err, validate, offsets, k); break;
+    case 1: k_prep0_ptrs<1><<<grid, block, 0, s>>>(sptr, wptr, n, work, bitmap, err, validate, offsets, k); break;
+    default: k_prep0_ptrs<2><<<grid, block, 0, s>>>(sptr, wptr, n, work, bitmap, err, validate, offsets, k); break;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Number of heads (zero bits of the has-predecessor bitmap below n).
+__global__ void k_count_heads(const uint32_t *__restrict__ bitmap, uint32_t n, uint32_t *out) {
+  const uint32_t words = (uint32_t)(((uint64_t)n + 31u) / 32u);
+  uint32_t c = 0;
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < words; w += gridDim.x * blockDim.x) {
+    uint32_t bits = ~__ldcg(bitmap + w);
+    if (w == words - 1u && (n & 31u)) bits &= (1u << (n & 31u)) - 1u;
+    c += __popc(bits);
+  }
+  for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xFFFFFFFFu, c, d);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+cudaError_t launch_count_heads(const uint32_t *bitmap, uint32_t n, uint32_t *out, cudaStream_t s) {
+  const int block = 256;
+  const int grid = stream_grid(((uint64_t)n + 31u) / 32u, block);
+  k_count_heads<<<grid, block, 0, s>>>(bitmap, n, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- heads
+enum : int { kCatSampled = 0, kCatNew = 1, kCatSingle = 2 };
+
+// Classify head x of a level: a sampled ruler keeps id pi(x); a head that is
+// also a terminal is a one-element list whose rank is its own weight
+// (resolved here, never chased); any other head becomes an extra ruler.
+template <class Rec>
+__device__ __forceinline__ int classify_head(uint32_t x, const Perm &P, uint32_t r,
+                                             const Rec *work, uint32_t *pid, uint64_t *wself) {
+  const uint32_t p = P.fwd(x);
+  *pid = p;
+  if (p < r) return kCatSampled;
+  Rec v = ld_rec(work + x);
+  if (rec_succ(v) == x) { *wself = rec_weight(v, x); return kCatSingle; }
+  return kCatNew;
+}
+
+// Visit this thread's heads in a fixed order (deterministic numbering).
+template <bool LEVEL0, class F>
+__device__ __forceinline__ void for_each_head(const LevelDesc &d, const uint32_t *bitmap,
+                                              const uint32_t *hlist, F &&f) {
+  if constexpr (LEVEL0) {
+    const uint32_t words = (uint32_t)(((uint64_t)d.n + 31u) / 32u);
+    const uint32_t per = (words + gridDim.x - 1) / gridDim.x;
+    const uint32_t w0 = blockIdx.x * per, w1 = min(words, w0 + per);
+    for (uint32_t w = w0 + threadIdx.x; w < w1; w += blockDim.x) {
+      uint32_t bits = ~__ldcg(bitmap + w);
+      if (w == words - 1u && (d.n & 31u)) bits &= (1u << (d.n & 31u)) - 1u;
+      while (bits) {
+        const uint32_t b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        f(w * 32u + b);
+      }
+    }
+  } else {
+    const uint32_t cnt = d.h;
+    const uint32_t per = (cnt + gridDim.x - 1) / gridDim.x;
+    const uint32_t e0 = blockIdx.x * per, e1 = min(cnt, e0 + per);
+    for (uint32_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) f(__ldcg(hlist + e));
+  }
+}
+
+template <class Rec, bool LEVEL0>
+__global__ void __launch_bounds__(kHeadThreads)
+k_heads_count(const LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ bitmap,
+              const uint32_t *__restrict__ hlist, const Rec *__restrict__ work,
+              uint64_t *__restrict__ blockcnt) {
+  __shared__ uint64_t sm[33];
+  const LevelDesc d = desc[lev];
+  if (d.mode != kModeSrs) return;
+  Perm P;
+  P.init(d.n, d.seed);
+  uint32_t nS = 0, nN = 0;
+  for_each_head<LEVEL0>(d, bitmap, hlist, [&](uint32_t x) {
+    uint32_t p;
+    uint64_t w;
+    const int c = classify_head(x, P, d.r, work, &p, &w);
+    nS += c == kCatSampled;
+    nN += c == kCatNew;
+  });
+  uint64_t total;
+  block_exclusive_scan(((uint64_t)(nS + nN) << 32) | nN, sm, &total);
+  if (threadIdx.x == 0) blockcnt[blockIdx.x] = total;
+}
+
+// Exclusive scan of the per-CTA counts; sizes of the next level; its mode.
+__global__ void __launch_bounds__(kHeadBlocks)
+k_heads_scan(LevelDesc *desc, int lev, int nlev, uint64_t *blockcnt, uint32_t *err,
+             uint32_t cutoff, uint32_t hcap, uint32_t has_pd) {
+  __shared__ uint64_t sm[33];
+  if (desc[lev].mode != kModeSrs) return;
+  uint64_t total;
+  const uint64_t v = blockcnt[threadIdx.x];
+  const uint64_t ex = block_exclusive_scan(v, sm, &total);
+  blockcnt[threadIdx.x] = ex;
+  if (threadIdx.x == 0) {
+    LevelDesc &d = desc[lev];
+    LevelDesc &e = desc[lev + 1];
+    const uint32_t kNew = (uint32_t)total;
+    const uint32_t hNext = (uint32_t)(total >> 32);
+    const uint64_t n1 = (uint64_t)d.r + kNew;
+    d.k = kNew;
+    bool bad = hNext > hcap || n1 > e.cap;
+    uint32_t mode = kModeSrs;
+    if (n1 <= cutoff) mode = kModeBase;
+    else if (lev + 1 >= nlev - 1) { if (has_pd) mode = kModePd; else bad = true; }
+    if (bad) {
+      record_error(err, kErrCapacity);
+      d.mode = kModeOff;      // nothing more runs at this level or below
+      return;
+    }
+    e.n = (uint32_t)n1;
+    e.r = (uint32_t)((n1 + e.f_inv - 1) / e.f_inv);
+    e.h = hNext;
+    e.mode = mode;
+  }
+}
+
+template <class Rec, bool LEVEL0>
+__global__ void __launch_bounds__(kHeadThreads)
+k_heads_write(LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ bitmap,
+              const uint32_t *__restrict__ hlist, Rec *__restrict__ work,
+              uint32_t *__restrict__ ns, uint32_t *__restrict__ hnext,
+              const uint64_t *__restrict__ blockoff) {
+  __shared__ uint64_t sm[33];
+  const LevelDesc d = desc[lev];
+  if (d.mode != kModeSrs) return;
+  Perm P;
+  P.init(d.n, d.seed);
+  uint32_t nS = 0, nN = 0;
+  for_each_head<LEVEL0>(d, bitmap, hlist, [&](uint32_t x) {
+    uint32_t p;
+    uint64_t w;
+    const int c = classify_head(x, P, d.r, work, &p, &w);
+    nS += c == kCatSampled;
+    nN += c == kCatNew;
+  });
+  const uint64_t mine = block_exclusive_scan(((uint64_t)(nS + nN) << 32) | nN, sm, nullptr);
+  const uint64_t base = blockoff[blockIdx.x] + mine;
+  uint32_t posN = (uint32_t)base, posH = (uint32_t)(base >> 32), nZ = 0;
+  for_each_head<LEVEL0>(d, bitmap, hlist, [&](uint32_t x) {
+    uint32_t p;
+    uint64_t w;
+    const int c = classify_head(x, P, d.r, work, &p, &w);
+    if (c == kCatSampled) {
+      hnext[posH++] = p;
+    } else if (c == kCatNew) {
+      ns[posN] = x;
+      hnext[posH++] = d.r + posN;
+      ++posN;
+    } else {
+      st_rec(work + x, kZeroCid, (uint64_t)0 - w);   // R(x) = 0 - (-w) = w
+      ++nZ;
+    }
+  });
+  for (int dd = 16; dd > 0; dd >>= 1) nZ += __shfl_down_sync(0xFFFFFFFFu, nZ, dd);
+  if ((threadIdx.x & 31) == 0 && nZ) atomicAdd(&desc[lev].visited, nZ);
+}
+
+cudaError_t launch_heads(LevelDesc *desc, int lev, int nlev, const uint32_t *bitmap,
+                         const uint32_t *hlist, void *work, bool rec16, uint32_t *ns,
+                         uint32_t *hnext, uint64_t *blockcnt, uint32_t *err, uint32_t cutoff,
+                         uint32_t hcap, uint32_t has_pd, cudaStream_t s) {
+  const bool l0 = lev == 0;
+#define LR_HEADS_COUNT(REC, L0)                                                                   \
+  k_heads_count<REC, L0><<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, lev, bitmap, hlist,           \
+                                                              reinterpret_cast<const REC *>(work), blockcnt)
+#define LR_HEADS_WRITE(REC, L0)                                                                   \
+  k_heads_write<REC, L0><<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, lev, bitmap, hlist,           \
+                                                              reinterpret_cast<REC *>(work), ns, hnext, blockcnt)
+  if (rec16) { if (l0) LR_HEADS_COUNT(Rec16, true); else LR_HEADS_COUNT(Rec16, false); }
+  else { if (l0) LR_HEADS_COUNT(Rec8, true); else LR_HEADS_COUNT(Rec8, false); }
+  k_heads_scan<<<1, kHeadBlocks, 0, s>>>(desc, lev, nlev, blockcnt, err, cutoff, hcap, has_pd);
+  if (rec16) { if (l0) LR_HEADS_WRITE(Rec16, true); else LR_HEADS_WRITE(Rec16, false); }
+  else { if (l0) LR_HEADS_WRITE(Rec8, true); else LR_HEADS_WRITE(Rec8, false); }
+#undef LR_HEADS_COUNT
+#undef LR_HEADS_WRITE
+  count_launch(3);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- chase
+// Persistent CTAs; CTA b owns a contiguous slice of ruler ids and its threads
+// pull ids one at a time from a per-CTA counter (the next id is requested
+// while the current chain runs, hiding the atomic's latency).  Each thread
+// walks succ from its ruler until it meets the next ruler (pi(y) < r) or a
+// terminal, rewriting every visited record as (ruler id, offset).
+// Visit one record: return its old contents and rewrite it as (cid, off)
+// unless another chase got there first.  XCHG: one atomic exchange at L2;
+// otherwise the store is issued only after the load has returned (it depends
+// on the loaded tag), so it always hits the sector the load just brought in.
+template <bool XCHG, class Rec>
+__device__ __forceinline__ Rec visit(Rec *p, uint32_t cid, uint64_t off) {
+  if constexpr (XCHG) {
+    return xchg_rec(p, cid, off);
+  } else {
+    Rec v = ld_rec(p);
+    if (rec_tag(v) == kUnvisited) st_rec(p, cid, off);
+    return v;
+  }
+}
+
+template <class Rec, bool XCHG>
+__global__ void __launch_bounds__(512)
+k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__restrict__ next,
+        const uint32_t *__restrict__ ns, uint32_t *__restrict__ qctr, uint32_t *__restrict__ err) {
+  const LevelDesc d = desc[lev];
+  if (d.mode != kModeSrs) return;
+  const uint32_t n = d.n, r = d.r;
+  const uint64_t R = (uint64_t)r + d.k;
+  Perm P;
+  P.init(n, d.seed);
+  const uint32_t lo = (uint32_t)(R * blockIdx.x / gridDim.x);
+  const uint32_t hi = (uint32_t)(R * (blockIdx.x + 1) / gridDim.x);
+  uint32_t *q = qctr + blockIdx.x;
+  uint32_t visited = 0, bad = 0;
+  uint64_t c64 = (uint64_t)lo + atomicAdd(q, 1u);
+  while (c64 < hi) {
+    const uint64_t cnext = (uint64_t)lo + atomicAdd(q, 1u);
+    const uint32_t c = (uint32_t)c64;
+    const uint32_t rho = c < r ? P.inv(c) : __ldcg(ns + (c - r));
+    Rec v = visit<XCHG>(work + rho, c, 0);
+    uint64_t o = rec_weight(v, rho);
+    uint32_t steps = 1, nxt = c;
+    bad |= rec_tag(v) != kUnvisited;
+    uint32_t y = rec_succ(v);
+    if (y != rho && rec_tag(v) == kUnvisited) {
+      for (;;) {
+        if (y >= n) { bad |= 4u; break; }   // never produced by prep or a chase
+        const uint32_t p = P.fwd(y);
+        if (p < r) {                 // reached the next ruler
+          nxt = p;
+          if (p == c) bad |= 2u;     // came back to itself: a cycle
+          break;
+        }
+        v = visit<XCHG>(work + y, c, o);
+        ++steps;
+        if (rec_tag(v) != kUnvisited) { bad |= 1u; break; }   // second predecessor
+        o += rec_weight(v, y);
+        const uint32_t s = rec_succ(v);
+        if (s == y) break;           // terminal: the reduced element is terminal too
+        if (steps > n) { bad |= 2u; break; }
+        y = s;
+      }
+    }
+    __stcg(reinterpret_cast<uint4 *>(next + c),
+           make_uint4(nxt, kUnvisited, (uint32_t)o, (uint32_t)(o >> 32)));
+    visited += steps;
+    c64 = cnext;
+  }
+  if (bad & 1u) record_error(err, kErrNotList);
+  if (bad & 2u) record_error(err, kErrCycle);
+  if (bad & 4u) record_error(err, kErrInternal);
+  for (int dd = 16; dd > 0; dd >>= 1) visited += __shfl_down_sync(0xFFFFFFFFu, visited, dd);
+  if ((threadIdx.x & 31) == 0 && visited) atomicAdd(&desc[lev].visited, visited);
+}
+
+cudaError_t launch_chase(LevelDesc *desc, int lev, void *work, bool rec16, void *next_work,
+                         const uint32_t *ns, uint32_t *qctr, int grid, int block, uint32_t *err,
+                         int xchg, cudaStream_t s) {
+  Rec16 *nx = reinterpret_cast<Rec16 *>(next_work);
+  if (rec16)
+    k_chase<Rec16, false><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<Rec16 *>(work), nx, ns, qctr, err);
+  else if (xchg)
+    k_chase<Rec8, true><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<Rec8 *>(work), nx, ns, qctr, err);
+  else
+    k_chase<Rec8, false><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<Rec8 *>(work), nx, ns, qctr, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+int chase_occupancy(bool rec16, int block) {
+  int nb = 0;
+  if (rec16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chase<Rec16, false>, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chase<Rec8, false>, block, 0);
+  return nb > 0 ? nb : 1;
+}
+
+// ---------------------------------------------------------------- finalize
+template <class RT>
+__device__ __forceinline__ RT propagate(uint32_t c, uint64_t o, uint32_t nn, const RT *rnext,
+                                        uint32_t &bad) {
+  RT base = 0;
+  if (c < nn) base = __ldcg(rnext + c);
+  else if (c != kZeroCid) bad |= c == kUnvisited ? kErrCycle : kErrInternal;
+  return (RT)(base - (RT)o);
+}
+
+// Ruler propagation: every element gets its ruler's rank minus its offset.
+template <class Rec, class RT>
+__global__ void __launch_bounds__(256)
+k_finalize(const LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ work,
+           const RT *__restrict__ rnext, RT *__restrict__ rout, uint32_t *__restrict__ err, int vec) {
+  const LevelDesc d = desc[lev];
+  if (d.mode != kModeSrs) return;
+  const uint32_t n = d.n, nn = desc[lev + 1].n;
+  uint32_t bad = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && d.visited != n) bad |= kErrCycle;
+  const uint32_t ngroups = (uint32_t)(((uint64_t)n + 3u) / 4u);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
+    const uint32_t i0 = g * 4u;
+    const uint32_t cnt = min(4u, n - i0);
+    RT out[4];
+    if constexpr (sizeof(Rec) == 8) {
+      if (cnt == 4u) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(work + i0);
+        uint4 a = __ldcs(p), b = __ldcs(p + 1);
+        out[0] = propagate<RT>(a.y, a.x, nn, rnext, bad);
+        out[1] = propagate<RT>(a.w, a.z, nn, rnext, bad);
+        out[2] = propagate<RT>(b.y, b.x, nn, rnext, bad);
+        out[3] = propagate<RT>(b.w, b.z, nn, rnext, bad);
+      } else {
+        for (uint32_t j = 0; j < cnt; ++j) {
+          Rec v = ld_rec(work + i0 + j);
+          out[j] = propagate<RT>(done_cid(v), done_off(v), nn, rnext, bad);
+        }
+      }
+    } else {
+      for (uint32_t j = 0; j < cnt; ++j) {
+        uint4 a = __ldcs(reinterpret_cast<const uint4 *>(work + i0 + j));
+        out[j] = propagate<RT>(a.y, ((uint64_t)a.w << 32) | a.z, nn, rnext, bad);
+      }
+    }
+    if (vec && cnt == 4u) {
+      if constexpr (sizeof(RT) == 4) {
+        __stcs(reinterpret_cast<uint4 *>(rout + i0), make_uint4(out[0], out[1], out[2], out[3]));
+      } else {
+        ulonglong2 *q = reinterpret_cast<ulonglong2 *>(rout + i0);
+        __stcs(q, make_ulonglong2(out[0], out[1]));
+        __stcs(q + 1, make_ulonglong2(out[2], out[3]));
+      }
+    } else {
+      for (uint32_t j = 0; j < cnt; ++j) rout[i0 + j] = out[j];
+    }
+  }
+  if (bad) record_error(err, bad);
+}
+
+// Level-0 propagation into per-instance output buffers.
+template <class Rec, class RT>
+__global__ void __launch_bounds__(256)
+k_finalize_ptrs(const LevelDesc *__restrict__ desc, const Rec *__restrict__ work,
+                const RT *__restrict__ rnext, RT *const *__restrict__ rptr,
+                const int64_t *__restrict__ offsets, int32_t k, uint32_t *__restrict__ err) {
+  const LevelDesc d = desc[0];
+  if (d.mode != kModeSrs) return;
+  const uint32_t n = d.n, nn = desc[1].n;
+  uint32_t bad = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && d.visited != n) bad |= kErrCycle;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    Rec v = ld_rec(work + i);
+    const RT val = propagate<RT>(done_cid(v), done_off(v), nn, rnext, bad);
+    int32_t lo = 0, hi = k;
+    while (hi - lo > 1) {
+      int32_t mid = (lo + hi) >> 1;
+      if ((uint64_t)__ldg(offsets + mid) <= i) lo = mid; else hi = mid;
+    }
+    rptr[lo][i - (uint64_t)__ldg(offsets + lo)] = val;
+  }
+  if (bad) record_error(err, bad);
+}
+
+cudaError_t launch_finalize_ptrs(LevelDesc *desc, const void *work, bool rec16, const void *rnext,
+                                 void *const *rptr, int rank_bytes, uint32_t cap,
+                                 const int64_t *offsets, int32_t k, uint32_t *err, cudaStream_t s) {
+  const int block = 256;
+  const int grid = stream_grid(cap, block);
+#define LR_FINP(REC, RT)                                                                          \
+  k_finalize_ptrs<REC, RT><<<grid, block, 0, s>>>(desc, reinterpret_cast<const REC *>(work),      \
+                                                  reinterpret_cast<const RT *>(rnext),            \
+                                                  reinterpret_cast<RT *const *>(rptr), offsets, k, err)
+  if (rec16) { if (rank_bytes == 4) LR_FINP(Rec16, uint32_t); else LR_FINP(Rec16, unsigned long long); }
+  else { if (rank_bytes == 4) LR_FINP(Rec8, uint32_t); else LR_FINP(Rec8, unsigned long long); }
+#undef LR_FINP
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec16,
+                            const void *rnext, void *rout, int rank_bytes, uint32_t cap,
+                            uint32_t *err, cudaStream_t s) {
+  const int block = 256;
+  const int grid = stream_grid(((uint64_t)cap + 3) / 4, block);
+  const int vec = ((uintptr_t)rout & 15u) == 0;
+#define LR_FIN(REC, RT)                                                                     \
+  k_finalize<REC, RT><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<const REC *>(work), \
+                                             reinterpret_cast<const RT *>(rnext),            \
+                                             reinterpret_cast<RT *>(rout), err, vec)
+  if (rec16) { if (rank_bytes == 4) LR_FIN(Rec16, uint32_t); else LR_FIN(Rec16, unsigned long long); }
+  else { if (rank_bytes == 4) LR_FIN(Rec8, uint32_t); else LR_FIN(Rec8, unsigned long long); }
+#undef LR_FIN
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- base case
+// Pointer doubling (Wyllie) inside one CTA: nxt/val live in shared memory;
+// every round each element adds its successor's value and jumps to its
+// successor's successor, reading the old values before anyone writes.
+// Values are inclusive (a terminal starts with its own weight), so after
+// ceil(log2 n) rounds val[i] is the rank of i at this level.
+template <class Rec, class RT>
+__global__ void __launch_bounds__(kBaseThreads)
+k_base(LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ work, RT *__restrict__ rout,
+       uint32_t *__restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  LevelDesc &d = desc[lev];
+  if (d.mode != kModeBase) return;
+  const uint32_t n = d.n;
+  uint32_t *nxt = reinterpret_cast<uint32_t *>(smem_raw);
+  RT *val = reinterpret_cast<RT *>(smem_raw + ((kMaxCutoff * 4 + 15) & ~15));
+  constexpr int PER = (kMaxCutoff + kBaseThreads - 1) / kBaseThreads;
+  for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+    Rec v = ld_rec(work + j);
+    const uint32_t s = rec_succ(v);
+    nxt[j] = (s == j || s >= n) ? kEnd : s;
+    val[j] = (RT)rec_weight(v, j);
+    if (s >= n) record_error(err, kErrInternal);
+  }
+  __syncthreads();
+  uint32_t rounds = 0;
+  while ((1ull << rounds) < n) ++rounds;
+  for (uint32_t it = 0; it < rounds; ++it) {
+    uint32_t tn[PER];
+    RT tv[PER];
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      const uint32_t j = threadIdx.x + e * kBaseThreads;
+      if (j < n) {
+        const uint32_t a = nxt[j];
+        if (a != kEnd) { tv[e] = val[j] + val[a]; tn[e] = nxt[a]; }
+        else { tv[e] = val[j]; tn[e] = kEnd; }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < PER; ++e) {
+      const uint32_t j = threadIdx.x + e * kBaseThreads;
+      if (j < n) { nxt[j] = tn[e]; val[j] = tv[e]; }
+    }
+    __syncthreads();
+  }
+  uint32_t bad = 0;
+  for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
+    if (nxt[j] != kEnd) bad = 1;
+    rout[j] = val[j];
+  }
+  if (bad) record_error(err, kErrCycle);
+  if (threadIdx.x == 0) d.visited = n;
+}
+
+static size_t base_smem(int rank_bytes) {
+  return ((kMaxCutoff * 4 + 15) & ~15) + (size_t)kMaxCutoff * rank_bytes;
+}
+
+cudaError_t launch_base(LevelDesc *desc, int lev, const void *work, bool rec16, void *rout,
+                        int rank_bytes, uint32_t cutoff, uint32_t *err, cudaStream_t s) {
+  (void)cutoff;
+  const size_t sm = base_smem(rank_bytes);
+#define LR_BASE(REC, RT)                                                                         \
+  k_base<REC, RT><<<1, kBaseThreads, sm, s>>>(desc, lev, reinterpret_cast<const REC *>(work), \
+                                              reinterpret_cast<RT *>(rout), err)
+  if (rec16) { if (rank_bytes == 4) LR_BASE(Rec16, uint32_t); else LR_BASE(Rec16, unsigned long long); }
+  else { if (rank_bytes == 4) LR_BASE(Rec8, uint32_t); else LR_BASE(Rec8, unsigned long long); }
+#undef LR_BASE
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- grid-wide pointer doubling
+// Fallback base case for a last level larger than one CTA can hold (many
+// lists whose heads keep the levels from shrinking).  Same rounds as the
+// single-CTA version, one kernel per round, ping-pong buffers.
+__global__ void k_pd_init(const LevelDesc *__restrict__ desc, int lev, const Rec16 *__restrict__ work,
+                          uint32_t *__restrict__ nxt, uint64_t *__restrict__ val) {
+  const LevelDesc d = desc[lev];
+  if (d.mode != kModePd) return;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) {
+    Rec16 v = ld_rec(work + j);
+    nxt[j] = (v.succ == j || v.succ >= d.n) ? kEnd : v.succ;
+    val[j] = v.w;
+  }
+}
+
+__global__ void k_pd_round(const LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ nin,
+                           const uint64_t *__restrict__ vin, uint32_t *__restrict__ nout,
+                           uint64_t *__restrict__ vout) {
+  const LevelDesc d = desc[lev];
+  if (d.mode != kModePd) return;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) {
+    const uint32_t a = nin[j];
+    if (a != kEnd) { vout[j] = vin[j] + vin[a]; nout[j] = nin[a]; }
+    else { vout[j] = vin[j]; nout[j] = kEnd; }
+  }
+}
+
+template <class RT>
+__global__ void k_pd_out(LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ nxt,
+                         const uint64_t *__restrict__ val, RT *__restrict__ rout, uint32_t *__restrict__ err) {
+  const LevelDesc d = desc[lev];
+  if (d.mode != kModePd) return;
+  uint32_t bad = 0;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) {
+    bad |= nxt[j] != kEnd;
+    rout[j] = (RT)val[j];
+  }
+  if (bad) record_error(err, kErrCycle);
+  if (blockIdx.x == 0 && threadIdx.x == 0) desc[lev].visited = d.n;
+}
+
+cudaError_t launch_pd(LevelDesc *desc, int lev, const void *work, uint32_t cap, uint32_t rounds,
+                      uint32_t *nxt0, uint32_t *nxt1, uint64_t *val0, uint64_t *val1, void *rout,
+                      int rank_bytes, uint32_t *err, cudaStream_t s) {
+  const int block = 256;
+  const int grid = stream_grid(cap, block);
+  k_pd_init<<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<const Rec16 *>(work), nxt0, val0);
+  uint32_t *na = nxt0, *nb = nxt1;
+  uint64_t *va = val0, *vb = val1;
+  for (uint32_t it = 0; it < rounds; ++it) {
+    k_pd_round<<<grid, block, 0, s>>>(desc, lev, na, va, nb, vb);
+    uint32_t *tn = na; na = nb; nb = tn;
+    uint64_t *tv = va; va = vb; vb = tv;
+  }
+  if (rank_bytes == 4)
+    k_pd_out<uint32_t><<<grid, block, 0, s>>>(desc, lev, na, va, reinterpret_cast<uint32_t *>(rout), err);
+  else
+    k_pd_out<unsigned long long><<<grid, block, 0, s>>>(desc, lev, na, va,
+                                                        reinterpret_cast<unsigned long long *>(rout), err);
+  count_launch(2 + (int)rounds);
+  return cudaGetLastError();
+}
+
+cudaError_t kernels_setup() {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(k_base<Rec8, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base_smem(4));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_base<Rec8, unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base_smem(8));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_base<Rec16, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base_smem(4));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_base<Rec16, unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base_smem(8));
+}
+
+}  // namespace lr

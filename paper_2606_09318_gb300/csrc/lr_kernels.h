@@ -1,0 +1,74 @@
+// lr_kernels.h -- host-side launchers of the list-ranking kernels (C++ linkage,
+// internal to liblr.so).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lr_device.cuh"
+
+namespace lr {
+
+struct InitParams {
+  int32_t nlev;                       // levels in the plan (0..nlev-1)
+  uint32_t n0;                        // elements at level 0
+  uint32_t mode0;                     // kModeSrs or kModeBase
+  uint32_t cutoff;                    // base-case bound
+  uint32_t f_inv[kMaxLevels + 1];
+  uint32_t cap[kMaxLevels + 1];
+  uint64_t seed[kMaxLevels + 1];
+  uint32_t pd_rounds;                 // rounds of the pointer-doubling fallback
+  uint32_t has_pd;                    // the last level may fall back to pointer doubling
+  uint32_t hcap;                      // capacity of the head lists
+};
+
+// Kernel launch counter (all streams).
+void count_launch(int k = 1);
+int64_t launch_count();
+
+int device_sm_count();
+
+cudaError_t launch_init(LevelDesc *desc, const InitParams &p, cudaStream_t s);
+
+// Level-0 pass.  wtype 0/1/2 (none/i32/i64).  offsets != nullptr: batched
+// input with local successor ids (k instances).
+cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, uint32_t n,
+                         void *work, uint32_t *bitmap, uint32_t *err, int validate,
+                         const int64_t *offsets, int32_t k, cudaStream_t s);
+
+cudaError_t launch_prep0_ptrs(const uint32_t *const *sptr, const void *const *wptr, int wtype,
+                              uint32_t n, void *work, uint32_t *bitmap, uint32_t *err, int validate,
+                              const int64_t *offsets, int32_t k, cudaStream_t s);
+
+cudaError_t launch_finalize_ptrs(LevelDesc *desc, const void *work, bool rec16, const void *rnext,
+                                 void *const *rptr, int rank_bytes, uint32_t cap,
+                                 const int64_t *offsets, int32_t k, uint32_t *err, cudaStream_t s);
+
+cudaError_t launch_count_heads(const uint32_t *bitmap, uint32_t n, uint32_t *out, cudaStream_t s);
+
+// Head selection of level `lev` (reads the bitmap at level 0, the head list
+// otherwise), then the exclusive scan and the writes.
+cudaError_t launch_heads(LevelDesc *desc, int lev, int nlev, const uint32_t *bitmap,
+                         const uint32_t *hlist, void *work, bool rec16, uint32_t *ns,
+                         uint32_t *hnext, uint64_t *blockcnt, uint32_t *err, uint32_t cutoff,
+                         uint32_t hcap, uint32_t has_pd, cudaStream_t s);
+
+cudaError_t launch_chase(LevelDesc *desc, int lev, void *work, bool rec16, void *next_work,
+                         const uint32_t *ns, uint32_t *qctr, int grid, int block, uint32_t *err,
+                         int xchg, cudaStream_t s);
+
+cudaError_t launch_base(LevelDesc *desc, int lev, const void *work, bool rec16, void *rout,
+                        int rank_bytes, uint32_t cutoff, uint32_t *err, cudaStream_t s);
+
+cudaError_t launch_pd(LevelDesc *desc, int lev, const void *work, uint32_t cap, uint32_t rounds,
+                      uint32_t *nxt0, uint32_t *nxt1, uint64_t *val0, uint64_t *val1, void *rout,
+                      int rank_bytes, uint32_t *err, cudaStream_t s);
+
+cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec16,
+                            const void *rnext, void *rout, int rank_bytes, uint32_t cap,
+                            uint32_t *err, cudaStream_t s);
+
+int chase_occupancy(bool rec16, int block);
+cudaError_t kernels_setup();
+
+}  // namespace lr

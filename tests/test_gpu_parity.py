@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer results, so the bar is bit-exact equality on every element.  Sizes
+span several tiles and ragged tails; at the full headline size the result is
+checked by properties that determine it completely (tail rank 0 and the
+recurrence rank[i] = w[i] + rank[succ[i]] on a single valid list).
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - collected on CPU machines too
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2606_09318_gb300 as lr  # noqa: E402
+
+
+def dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def check_equal(succ, weight=None, rank_dtype=np.int32, **kw):
+    want = oracle.rank(succ, weight, rank_dtype)
+    tdt = torch.int32 if rank_dtype == np.int32 else torch.int64
+    got = lr.rank(dev(succ), None if weight is None else dev(weight), rank_dtype=tdt, **kw)
+    np.testing.assert_array_equal(host(got), want)
+    return got
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 32, 33, 1023, 1024, 1025, 8191, 8192, 8193,
+                               12289, 65537, 1 << 20, (1 << 20) + 7])
+def test_random_list_unweighted(n):
+    check_equal(gen.random_list(n, 100 + n))
+
+
+@pytest.mark.parametrize("kind", ["random", "locality", "identity"])
+@pytest.mark.parametrize("n", [(1 << 22) + 3, 1 << 24])
+def test_orders(kind, n):
+    check_equal(gen.list_of_order_kind(kind, n, 7))
+
+
+@pytest.mark.parametrize("wt,rt", [(np.int32, np.int64), (np.int64, np.int64),
+                                   (np.int32, np.int32), (np.int64, np.int32)])
+@pytest.mark.parametrize("n", [5, 4097, (1 << 20) + 1])
+def test_weighted(wt, rt, n):
+    succ = gen.random_list(n, 3 * n)
+    if wt == np.int32:
+        w = gen.weights_i32(n, 11)
+    else:
+        w = gen.weights_i64(n, 12, -(1 << 40), 1 << 40)
+    check_equal(succ, w, rt)
+
+
+def test_wraparound_extremes():
+    n = 100_000
+    succ = gen.random_list(n, 5)
+    check_equal(succ, np.full(n, np.iinfo(np.int32).max, dtype=np.int32), np.int32)
+    check_equal(succ, np.full(n, np.iinfo(np.int32).min, dtype=np.int32), np.int64)
+    check_equal(succ, np.full(n, np.iinfo(np.int64).max, dtype=np.int64), np.int64)
+
+
+def test_forest():
+    succ, _ = gen.forest(1 << 22, 31, n_long=16, long_len=1 << 16, mean_short=64)
+    check_equal(succ)
+
+
+def test_forest_short_lists_and_singletons():
+    succ, _ = gen.forest(1 << 20, 32, n_long=2, long_len=1 << 12, mean_short=2)
+    check_equal(succ)
+    check_equal(np.arange(300_000, dtype=np.uint32))          # all singletons
+
+
+def test_euler_tour_depths():
+    V = 1 << 18
+    parent = gen.random_recursive_tree(V, 77)
+    succ, w = gen.euler_tour(parent)
+    r = host(check_equal(succ, w, np.int32)).astype(np.int64)
+    depth = np.zeros(V, dtype=np.int64)
+    for v in range(1, V):
+        depth[v] = depth[parent[v]] + 1
+    v = np.arange(1, V)
+    np.testing.assert_array_equal(2 - r[2 * (v - 1)], depth[v])
+
+
+def test_result_independent_of_seed_and_tuning():
+    n = (1 << 21) + 5
+    succ = gen.random_list(n, 9)
+    want = oracle.rank(succ)
+    s = dev(succ)
+    for seed in (1, 2, 12345):
+        np.testing.assert_array_equal(host(lr.rank(s, seed=seed)), want)
+    for f0, f, cut in ((16, 4, 1024), (128, 16, 12288), (2, 2, 64), (32, 8, 4096)):
+        t = lr.Tuning(f0_inv=f0, f_inv=f, cutoff=cut)
+        np.testing.assert_array_equal(host(lr.rank(s, tuning=t)), want)
+    for blk, ctas in ((128, 4), (512, 2), (256, 1)):
+        t = lr.Tuning(chase_block=blk, chase_ctas=ctas)
+        np.testing.assert_array_equal(host(lr.rank(s, tuning=t)), want)
+
+
+def test_max_lists_path_matches_counted_path():
+    succ, nl = gen.forest(1 << 20, 8, n_long=4, long_len=1 << 14, mean_short=64)
+    s = dev(succ)
+    a = host(lr.rank(s))
+    b = host(lr.rank(s, max_lists=nl))
+    np.testing.assert_array_equal(a, b)
+    with pytest.raises(lr.LRError) as e:
+        lr.rank(s, max_lists=max(1, nl // 4))
+    assert e.value.name == "LR_ERR_CAPACITY"
+
+
+def test_empty():
+    out = lr.rank(torch.empty(0, dtype=torch.int32, device="cuda"))
+    assert out.numel() == 0
+
+
+def test_batch_matches_oracle_and_single_calls():
+    offsets, succ, w = gen.batch_instances(64, 5, lo_exp=0.0, hi_exp=15.0)
+    want = oracle.rank_batch(offsets, succ, w, np.int64)
+    got = host(lr.rank_batch(dev(offsets), dev(succ), dev(w)))
+    np.testing.assert_array_equal(got, want)
+    got2 = host(lr.rank_batch(dev(offsets), dev(succ), dev(w), max_lists=64))
+    np.testing.assert_array_equal(got2, want)
+    for j in (0, 17, 63):
+        a, b = offsets[j], offsets[j + 1]
+        one = host(lr.rank(dev(succ[a:b]), dev(w[a:b])))
+        np.testing.assert_array_equal(one, want[a:b])
+
+
+def test_batch_unweighted_with_empty_instances():
+    lens = np.array([0, 5, 0, 1, 300, 0, 70000, 2], dtype=np.int64)
+    offsets = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    succ = np.concatenate([gen.random_list(int(m), 40 + i) for i, m in enumerate(lens)]).astype(np.uint32)
+    want = oracle.rank_batch(offsets, succ, None, np.int32)
+    got = host(lr.rank_batch(dev(offsets), dev(succ), rank_dtype=torch.int32))
+    np.testing.assert_array_equal(got, want)
+
+
+def test_host_buffers_end_to_end():
+    n = (1 << 20) + 3
+    succ = gen.random_list(n, 44)
+    np.testing.assert_array_equal(lr.rank_host(succ), oracle.rank(succ))
+    w = gen.weights_i32(n, 45)
+    np.testing.assert_array_equal(lr.rank_host(succ, w), oracle.rank(succ, w, np.int64))
+
+
+@pytest.mark.parametrize("n", [1 << 28])
+def test_full_size_properties(n):
+    """Headline size: the recurrence and tail rank 0 pin the result exactly."""
+    succ = torch.randperm(n, device="cuda", generator=torch.Generator("cuda").manual_seed(2028),
+                          dtype=torch.int64)
+    order = succ
+    s = torch.empty(n, dtype=torch.int64, device="cuda")
+    s[order[:-1]] = order[1:]
+    s[order[-1]] = order[-1]
+    s32 = s.to(torch.int32)
+    del s
+    r = lr.rank(s32).to(torch.int64)
+    idx = torch.arange(n, device="cuda", dtype=torch.int64)
+    sl = s32.to(torch.int64)
+    term = sl == idx
+    assert int(term.sum()) == 1
+    assert int(r[term].item()) == 0
+    nt = ~term
+    assert bool((r[nt] == r[sl[nt]] + 1).all())
+    assert int(r[order[0]].item()) == n - 1
+    # sampled elements against the closed form: the element at list position p has rank n-1-p
+    pos = torch.empty(n, dtype=torch.int64, device="cuda")
+    pos[order] = torch.arange(n, device="cuda")
+    pick = torch.randint(0, n, (4096,), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    assert bool((r[pick] == n - 1 - pos[pick]).all())
