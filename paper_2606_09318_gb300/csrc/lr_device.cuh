@@ -50,8 +50,10 @@ struct LevelDesc {
   uint32_t cap;      // static: capacity of this level's arrays
   uint64_t seed;     // static: permutation seed
   uint32_t rounds;   // static: pointer-doubling rounds of the fallback base
-  uint32_t pad;
+  uint32_t hsrc;     // where this level's heads come from: kHeadsBitmap or kHeadsList
 };
+
+enum : uint32_t { kHeadsBitmap = 0, kHeadsList = 1 };
 
 // ---------------------------------------------------------------- permutation
 // A keyed bijection of [0, 2^b) built from invertible steps (multiply by an
@@ -167,6 +169,21 @@ __device__ __forceinline__ Rec16 xchg_rec(Rec16 *p, uint32_t cid, uint64_t off) 
   if (v.tag == kUnvisited) st_rec(p, cid, off);
   return v;
 }
+
+// The raw successor array read as a record (level 0 of the log path): no tag,
+// unit link weight, 0 at a terminal.
+struct Succ4 {
+  uint32_t s;
+};
+__device__ __forceinline__ Succ4 ld_rec(const Succ4 *p) {
+  return Succ4{__ldcg(reinterpret_cast<const uint32_t *>(p))};
+}
+__device__ __forceinline__ uint64_t rec_weight(const Succ4 &r, uint32_t self) {
+  return r.s == self ? 0u : 1u;
+}
+__device__ __forceinline__ uint32_t rec_succ(const Succ4 &r) { return r.s; }
+__device__ __forceinline__ uint32_t rec_tag(const Succ4 &) { return kUnvisited; }
+__device__ __forceinline__ void st_rec(Succ4 *, uint32_t, uint64_t) {}
 
 // Link weight carried by a record (level-0 unweighted: 1, or 0 at a terminal).
 __device__ __forceinline__ uint64_t rec_weight(const Rec8 &r, uint32_t self) {

@@ -57,6 +57,7 @@ Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted) {
   u.block = env_u32(env, "block", u.block);
   u.ctas = env_u32(env, "ctas", u.ctas);
   u.xchg = env_u32(env, "xchg", 1);
+  u.logmode = env_u32(env, "log", 0);
   if (t) {
     if (t->f0_inv) u.f0_inv = t->f0_inv;
     if (t->f_inv) u.f_inv = t->f_inv;
@@ -79,18 +80,19 @@ static uint32_t ceil_log2(uint64_t x) {
 
 static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
-int chase_grid_for(const Tuning &u, bool rec16) {
-  int per = u.ctas ? (int)u.ctas : chase_occupancy(rec16, (int)u.block);
+int chase_grid_for(const Tuning &u, bool rec16, bool log0) {
+  int per = u.ctas ? (int)u.ctas : (log0 ? chase_log_occupancy((int)u.block) : chase_occupancy(rec16, (int)u.block));
   return device_sm_count() * std::max(1, per);
 }
 
 // Static plan for n elements and at most h lists.
 Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,
-               uint64_t seed, int chase_grid, bool force_srs) {
+               uint64_t seed, int chase_grid, bool force_srs, bool log0) {
   Plan p;
   memset(&p, 0, sizeof(p));
   p.n = n;
   p.rec16_0 = rec16_0;
+  p.log0 = log0;
   p.rank_bytes = rank_bytes;
   p.cutoff = u.cutoff;
   p.chase_grid = chase_grid;
@@ -123,17 +125,40 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
   p.off_zero = o;
   p.off_err = o; o = align_up(o + 16);
   p.off_hcount = o; o = align_up(o + 16);
+  p.off_acc = o; o = align_up(o + 16);
+  p.off_ovf = o; o = align_up(o + 16);
+  p.off_bctr = o; o = align_up(o + sizeof(uint32_t) * 256);
   p.off_q = o; o = align_up(o + sizeof(uint32_t) * (size_t)chase_grid * kMaxLevels);
   p.off_bcnt = o; o = align_up(o + sizeof(uint64_t) * kHeadBlocks);
   p.zero_bytes = o - p.off_zero;
   p.off_bitmap = o; o = align_up(o + sizeof(uint32_t) * ((n + 31) / 32));
-  p.off_work[0] = o; o = align_up(o + (rec16_0 ? 16 : 8) * (size_t)n);
+  if (!log0) { p.off_work[0] = o; o = align_up(o + (rec16_0 ? 16 : 8) * (size_t)n); }
   p.fixed_bytes = o;
   // variable part
   o = 0;
   for (int l = 1; l <= L; ++l) {
     p.off_work[l] = o; o = align_up(o + 16 * (size_t)p.cap[l]);
     p.off_R[l] = o; o = align_up(o + (size_t)rank_bytes * p.cap[l]);
+  }
+  if (log0) {
+    // log entries: every element once plus one mark per ruler, in 32-entry
+    // chunks; each thread may leave one chunk partly filled.  6 % slack per
+    // CTA region plus an overflow pool of the same size.
+    const uint64_t rulers = (n + p.f_inv[0] - 1) / p.f_inv[0] + p.hcap;
+    const uint64_t need = (n + rulers + 31) / 32;
+    const uint64_t threads = (uint64_t)chase_grid * u.block;
+    const uint64_t main = need + need * 6 / 100 + threads + chase_grid;
+    p.per_cta = (uint32_t)((main + chase_grid - 1) / chase_grid);
+    const uint64_t total = (uint64_t)p.per_cta * chase_grid + need * 6 / 100 + 4096;
+    p.total_chunks = (uint32_t)std::min<uint64_t>(total, 0xFFFFFFF0ull);
+    uint32_t lg = 0;
+    while ((1ull << lg) < n) ++lg;
+    p.shift = lg > 8 ? lg - 8 : 0;
+    p.off_log = o; o = align_up(o + (size_t)p.total_chunks * 32 * 4);
+    p.off_hdr = o; o = align_up(o + (size_t)p.total_chunks * 8);
+    p.off_pairs = o; o = align_up(o + (size_t)n * 8);
+    p.part_ctas = std::max(1, std::min(chase_grid, 152 * 8));
+    p.off_hist = o; o = align_up(o + (size_t)p.part_ctas * 256 * 4);
   }
   p.off_hA = o; o = align_up(o + 4 * (size_t)p.hcap);
   p.off_hB = o; o = align_up(o + 4 * (size_t)p.hcap);
@@ -293,11 +318,13 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   const bool capturing = stream_capturing(s);
   const Tuning u = resolve_tuning(tuning, (int64_t)in.n, in.wtype != 0);
   const bool rec16_0 = in.wtype != 0;
-  const int grid = chase_grid_for(u, rec16_0);
+  const bool log0 = u.logmode && !ptrs && in.offsets == nullptr && in.wtype == 0 &&
+                    in.rank_bytes == 4 && in.n > u.cutoff && in.n < (1ull << 31);
+  const int grid = chase_grid_for(u, rec16_0, log0);
   const bool need_count = in.max_lists <= 0 && in.ws == nullptr && (in.n > u.cutoff || ptrs);
   if (need_count && capturing) return LR_ERR_CAPTURE;
   uint64_t hb = in.max_lists > 0 ? (uint64_t)in.max_lists : in.n;
-  Plan p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs);
+  Plan p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0);
 
   // fixed part (level 0)
   char *fixed = nullptr;
@@ -321,21 +348,30 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
 
   Profiler prof;
   prof.begin(s, (int64_t)in.n);
+  unsigned long long *acc = (unsigned long long *)(fixed + p.off_acc);
   LR_TRY(cudaMemsetAsync(fixed + p.off_zero, 0, p.zero_bytes, s));
   LR_TRY(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * ((in.n + 31) / 32), s));
-  if (ptrs)
+  if (log0)
+    LR_TRY(launch_sum0(in.succ, (uint32_t)in.n, acc, err, s));
+  else if (ptrs)
     LR_TRY(launch_prep0_ptrs(in.sptr, in.wptr, in.wtype, (uint32_t)in.n, work0, bitmap, err,
                              in.validate, in.offsets, in.k, s));
   else
     LR_TRY(launch_prep0(in.succ, in.weight, in.wtype, (uint32_t)in.n, work0, bitmap, err,
                         in.validate, in.offsets, in.k, s));
   if (need_count) {
-    // count the heads (one wait), then size the recursion for exactly that many lists
-    LR_TRY(launch_count_heads(bitmap, (uint32_t)in.n, hcount, s));
-    LR_TRY(cudaMemcpyAsync(c->host_words + 1, hcount, 4, cudaMemcpyDeviceToHost, s));
+    // count the lists (one wait), then size the recursion for exactly that many:
+    // the log path counts terminals in its reduction, the record path counts
+    // zero bits of the has-predecessor bitmap
+    if (log0) {
+      LR_TRY(cudaMemcpyAsync(c->host_words + 1, acc, 4, cudaMemcpyDeviceToHost, s));
+    } else {
+      LR_TRY(launch_count_heads(bitmap, (uint32_t)in.n, hcount, s));
+      LR_TRY(cudaMemcpyAsync(c->host_words + 1, hcount, 4, cudaMemcpyDeviceToHost, s));
+    }
     LR_TRY(cudaStreamSynchronize(s));
     hb = std::max<uint64_t>(1, c->host_words[1]);
-    p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs);
+    p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0);
   }
   if (!in.ws) {
     st = ensure_buffer(&c->var, &c->var_bytes, p.var_bytes, s);
@@ -359,6 +395,11 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   ip.has_pd = p.has_pd;
   ip.hcap = p.hcap;
   LR_TRY(launch_init(desc, ip, s));
+  uint32_t *hA0 = (uint32_t *)(var + p.off_hA);
+  if (log0) {
+    LR_TRY(cudaMemsetAsync(var + p.off_hdr, 0xFF, (size_t)p.total_chunks * 8, s));
+    LR_TRY(launch_heads0_log(desc, acc, hA0, in.succ, (uint32_t)in.n, bitmap, err, in.validate, s));
+  }
 
   auto work_of = [&](int l) -> void * { return l == 0 ? work0 : (void *)(var + p.off_work[l]); };
   auto R_of = [&](int l) -> void * { return l == 0 ? in.rank : (void *)(var + p.off_R[l]); };
@@ -374,12 +415,18 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
       LR_TRY(launch_base(desc, l, work_of(l), r16, R_of(l), p.rank_bytes, p.cutoff, err, s));
       prof.mark(PH_BASE);
     }
-    LR_TRY(launch_heads(desc, l, p.nlev, bitmap, hin, work_of(l), r16, ns, hout, bcnt, err,
-                        p.cutoff, p.hcap, p.has_pd ? 1u : 0u, s));
+    const int kind = (l == 0 && log0) ? kRecKindSucc : (r16 ? kRecKind16 : kRecKind8);
+    LR_TRY(launch_heads(desc, l, p.nlev, bitmap, hin, (l == 0 && log0) ? (void *)in.succ : work_of(l),
+                        kind, ns, hout, bcnt, err, p.cutoff, p.hcap, p.has_pd ? 1u : 0u, s));
     prof.mark(PH_SELECT);
-    LR_TRY(launch_chase(desc, l, work_of(l), r16, work_of(l + 1), ns,
-                        qctr + (size_t)l * p.chase_grid, p.chase_grid, p.chase_block, err,
-                        (int)u.xchg, s));
+    if (l == 0 && log0)
+      LR_TRY(launch_chase_log(desc, in.succ, work_of(1), ns, qctr, p.chase_grid, p.chase_block, err,
+                              (uint32_t *)(var + p.off_log), (uint2 *)(var + p.off_hdr), p.per_cta,
+                              p.total_chunks, (uint32_t *)(fixed + p.off_ovf), s));
+    else
+      LR_TRY(launch_chase(desc, l, work_of(l), r16, work_of(l + 1), ns,
+                          qctr + (size_t)l * p.chase_grid, p.chase_grid, p.chase_block, err,
+                          (int)u.xchg, s));
     prof.mark(l == 0 ? PH_CHASE0 : PH_CHASE);
   }
   LR_TRY(launch_base(desc, L, work_of(L), L > 0 || rec16_0, R_of(L), p.rank_bytes, p.cutoff, err, s));
@@ -390,7 +437,12 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   }
   prof.mark(PH_BASE);
   for (int l = L - 1; l >= 0; --l) {
-    if (l == 0 && ptrs)
+    if (l == 0 && log0)
+      LR_TRY(launch_finalize_log(desc, (const uint32_t *)(var + p.off_log), (const uint2 *)(var + p.off_hdr),
+                                 p.total_chunks, R_of(1), (uint2 *)(var + p.off_pairs),
+                                 (uint32_t *)(var + p.off_hist), p.part_ctas, p.shift,
+                                 (uint32_t *)in.rank, (uint32_t)in.n, err, s));
+    else if (l == 0 && ptrs)
       LR_TRY(launch_finalize_ptrs(desc, work0, rec16_0, R_of(1), in.rptr, p.rank_bytes, p.cap[0],
                                   in.offsets, in.k, err, s));
     else
@@ -606,7 +658,6 @@ lr_status lr_rank_host(const uint32_t *succ_host, const void *weight_host, int64
 }
 
 size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts) {
-  (void)k;
   lr_opts d;
   if (!opts) { lr_opts_default(&d); opts = &d; }
   if (n_total <= 0) return 0;
@@ -614,8 +665,10 @@ size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts) {
   // The chase grid depends on the device; size for a generous upper bound so
   // the answer needs no GPU: 256 SMs x 16 CTAs.
   const uint64_t h = opts->max_lists > 0 ? (uint64_t)opts->max_lists : (uint64_t)n_total;
+  const bool log0 = u.logmode && k == 0 && opts->wtype == LR_NONE && opts->rtype == LR_I32 &&
+                    (uint64_t)n_total > u.cutoff && n_total < ((int64_t)1 << 31);
   Plan p = make_plan((uint64_t)n_total, h, u, opts->wtype != LR_NONE,
-                     opts->rtype == LR_I64 ? 8 : 4, opts->seed, 256 * 16, false);
+                     opts->rtype == LR_I64 ? 8 : 4, opts->seed, 256 * 16, false, log0);
   return p.fixed_bytes + p.var_bytes;
 }
 

@@ -10,7 +10,7 @@
 namespace lr {
 
 struct Tuning {
-  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg;
+  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, logmode;
 };
 
 struct Plan {
@@ -24,14 +24,19 @@ struct Plan {
   uint32_t hcap;                    // head-list capacity (bound on lists)
   uint32_t cutoff;
   bool rec16_0;
+  bool log0;                        // level 0 on the log path (lr_log.cu)
   int rank_bytes;
   int chase_grid, chase_block;
   // fixed part (does not depend on the list bound)
-  size_t off_desc, off_zero, zero_bytes, off_err, off_hcount, off_q, off_bcnt, off_bitmap;
+  size_t off_desc, off_zero, zero_bytes, off_err, off_hcount, off_acc, off_ovf, off_bctr, off_q,
+      off_bcnt, off_bitmap;
   size_t fixed_bytes;
   // variable part
   size_t off_work[kMaxLevels + 1], off_R[kMaxLevels + 1];
   size_t off_hA, off_hB, off_ns, off_pd[4];
+  size_t off_log, off_hdr, off_pairs, off_hist;   // log path
+  uint32_t per_cta, total_chunks, shift;
+  int part_ctas;
   size_t var_bytes;
 };
 
@@ -50,8 +55,8 @@ struct Ctx {
 
 Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted);
 Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,
-               uint64_t seed, int chase_grid, bool force_srs);
-int chase_grid_for(const Tuning &u, bool rec16);
+               uint64_t seed, int chase_grid, bool force_srs, bool log0);
+int chase_grid_for(const Tuning &u, bool rec16, bool log0);
 Ctx *get_ctx(cudaStream_t stream, lr_status *st);
 lr_status ensure_buffer(void **buf, size_t *cur, size_t want, cudaStream_t s);
 lr_status device_status(cudaStream_t s);

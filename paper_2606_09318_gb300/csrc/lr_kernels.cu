@@ -37,7 +37,7 @@ int device_sm_count() {
   return sms > 0 ? sms : 1;
 }
 
-static int stream_grid(uint64_t work_items, int block) {
+int stream_grid(uint64_t work_items, int block) {
   // grid-stride kernels: enough CTAs to fill every SM, no more than needed
   uint64_t want = (work_items + block - 1) / block;
   uint64_t full = (uint64_t)device_sm_count() * (2048 / block);
@@ -60,7 +60,7 @@ __global__ void k_init(LevelDesc *desc, InitParams p) {
     x.cap = p.cap[l];
     x.seed = p.seed[l];
     x.rounds = p.pd_rounds;
-    x.pad = 0;
+    x.hsrc = l == 0 ? (uint32_t)kHeadsBitmap : (uint32_t)kHeadsList;
     desc[l] = x;
   }
 }
@@ -266,22 +266,24 @@ enum : int { kCatSampled = 0, kCatNew = 1, kCatSingle = 2 };
 // Classify head x of a level: a sampled ruler keeps id pi(x); a head that is
 // also a terminal is a one-element list whose rank is its own weight
 // (resolved here, never chased); any other head becomes an extra ruler.
-template <class Rec>
+template <class Rec, bool RESOLVE>
 __device__ __forceinline__ int classify_head(uint32_t x, const Perm &P, uint32_t r,
                                              const Rec *work, uint32_t *pid, uint64_t *wself) {
   const uint32_t p = P.fwd(x);
   *pid = p;
   if (p < r) return kCatSampled;
-  Rec v = ld_rec(work + x);
-  if (rec_succ(v) == x) { *wself = rec_weight(v, x); return kCatSingle; }
+  if constexpr (RESOLVE) {
+    Rec v = ld_rec(work + x);
+    if (rec_succ(v) == x) { *wself = rec_weight(v, x); return kCatSingle; }
+  }
   return kCatNew;
 }
 
 // Visit this thread's heads in a fixed order (deterministic numbering).
-template <bool LEVEL0, class F>
+template <class F>
 __device__ __forceinline__ void for_each_head(const LevelDesc &d, const uint32_t *bitmap,
                                               const uint32_t *hlist, F &&f) {
-  if constexpr (LEVEL0) {
+  if (d.hsrc == kHeadsBitmap) {
     const uint32_t words = (uint32_t)(((uint64_t)d.n + 31u) / 32u);
     const uint32_t per = (words + gridDim.x - 1) / gridDim.x;
     const uint32_t w0 = blockIdx.x * per, w1 = min(words, w0 + per);
@@ -302,7 +304,7 @@ __device__ __forceinline__ void for_each_head(const LevelDesc &d, const uint32_t
   }
 }
 
-template <class Rec, bool LEVEL0>
+template <class Rec, bool RESOLVE>
 __global__ void __launch_bounds__(kHeadThreads)
 k_heads_count(const LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ bitmap,
               const uint32_t *__restrict__ hlist, const Rec *__restrict__ work,
@@ -313,10 +315,10 @@ k_heads_count(const LevelDesc *__restrict__ desc, int lev, const uint32_t *__res
   Perm P;
   P.init(d.n, d.seed);
   uint32_t nS = 0, nN = 0;
-  for_each_head<LEVEL0>(d, bitmap, hlist, [&](uint32_t x) {
+  for_each_head(d, bitmap, hlist, [&](uint32_t x) {
     uint32_t p;
     uint64_t w;
-    const int c = classify_head(x, P, d.r, work, &p, &w);
+    const int c = classify_head<Rec, RESOLVE>(x, P, d.r, work, &p, &w);
     nS += c == kCatSampled;
     nN += c == kCatNew;
   });
@@ -358,7 +360,7 @@ k_heads_scan(LevelDesc *desc, int lev, int nlev, uint64_t *blockcnt, uint32_t *e
   }
 }
 
-template <class Rec, bool LEVEL0>
+template <class Rec, bool RESOLVE>
 __global__ void __launch_bounds__(kHeadThreads)
 k_heads_write(LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ bitmap,
               const uint32_t *__restrict__ hlist, Rec *__restrict__ work,
@@ -370,20 +372,20 @@ k_heads_write(LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict_
   Perm P;
   P.init(d.n, d.seed);
   uint32_t nS = 0, nN = 0;
-  for_each_head<LEVEL0>(d, bitmap, hlist, [&](uint32_t x) {
+  for_each_head(d, bitmap, hlist, [&](uint32_t x) {
     uint32_t p;
     uint64_t w;
-    const int c = classify_head(x, P, d.r, work, &p, &w);
+    const int c = classify_head<Rec, RESOLVE>(x, P, d.r, work, &p, &w);
     nS += c == kCatSampled;
     nN += c == kCatNew;
   });
   const uint64_t mine = block_exclusive_scan(((uint64_t)(nS + nN) << 32) | nN, sm, nullptr);
   const uint64_t base = blockoff[blockIdx.x] + mine;
   uint32_t posN = (uint32_t)base, posH = (uint32_t)(base >> 32), nZ = 0;
-  for_each_head<LEVEL0>(d, bitmap, hlist, [&](uint32_t x) {
+  for_each_head(d, bitmap, hlist, [&](uint32_t x) {
     uint32_t p;
     uint64_t w;
-    const int c = classify_head(x, P, d.r, work, &p, &w);
+    const int c = classify_head<Rec, RESOLVE>(x, P, d.r, work, &p, &w);
     if (c == kCatSampled) {
       hnext[posH++] = p;
     } else if (c == kCatNew) {
@@ -400,23 +402,35 @@ k_heads_write(LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict_
 }
 
 cudaError_t launch_heads(LevelDesc *desc, int lev, int nlev, const uint32_t *bitmap,
-                         const uint32_t *hlist, void *work, bool rec16, uint32_t *ns,
+                         const uint32_t *hlist, void *work, int rec_kind, uint32_t *ns,
                          uint32_t *hnext, uint64_t *blockcnt, uint32_t *err, uint32_t cutoff,
                          uint32_t hcap, uint32_t has_pd, cudaStream_t s) {
-  const bool l0 = lev == 0;
-#define LR_HEADS_COUNT(REC, L0)                                                                   \
-  k_heads_count<REC, L0><<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, lev, bitmap, hlist,           \
-                                                              reinterpret_cast<const REC *>(work), blockcnt)
-#define LR_HEADS_WRITE(REC, L0)                                                                   \
-  k_heads_write<REC, L0><<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, lev, bitmap, hlist,           \
-                                                              reinterpret_cast<REC *>(work), ns, hnext, blockcnt)
-  if (rec16) { if (l0) LR_HEADS_COUNT(Rec16, true); else LR_HEADS_COUNT(Rec16, false); }
-  else { if (l0) LR_HEADS_COUNT(Rec8, true); else LR_HEADS_COUNT(Rec8, false); }
+#define LR_HEADS(KERNEL, REC, RES)                                                                \
+  KERNEL<REC, RES><<<kHeadBlocks, kHeadThreads, 0, s>>>
+  switch (rec_kind) {
+    case kRecKind8:
+      LR_HEADS(k_heads_count, Rec8, true)(desc, lev, bitmap, hlist, reinterpret_cast<const Rec8 *>(work), blockcnt);
+      break;
+    case kRecKind16:
+      LR_HEADS(k_heads_count, Rec16, true)(desc, lev, bitmap, hlist, reinterpret_cast<const Rec16 *>(work), blockcnt);
+      break;
+    default:
+      LR_HEADS(k_heads_count, Succ4, false)(desc, lev, bitmap, hlist, reinterpret_cast<const Succ4 *>(work), blockcnt);
+      break;
+  }
   k_heads_scan<<<1, kHeadBlocks, 0, s>>>(desc, lev, nlev, blockcnt, err, cutoff, hcap, has_pd);
-  if (rec16) { if (l0) LR_HEADS_WRITE(Rec16, true); else LR_HEADS_WRITE(Rec16, false); }
-  else { if (l0) LR_HEADS_WRITE(Rec8, true); else LR_HEADS_WRITE(Rec8, false); }
-#undef LR_HEADS_COUNT
-#undef LR_HEADS_WRITE
+  switch (rec_kind) {
+    case kRecKind8:
+      LR_HEADS(k_heads_write, Rec8, true)(desc, lev, bitmap, hlist, reinterpret_cast<Rec8 *>(work), ns, hnext, blockcnt);
+      break;
+    case kRecKind16:
+      LR_HEADS(k_heads_write, Rec16, true)(desc, lev, bitmap, hlist, reinterpret_cast<Rec16 *>(work), ns, hnext, blockcnt);
+      break;
+    default:
+      LR_HEADS(k_heads_write, Succ4, false)(desc, lev, bitmap, hlist, reinterpret_cast<Succ4 *>(work), ns, hnext, blockcnt);
+      break;
+  }
+#undef LR_HEADS
   count_launch(3);
   return cudaGetLastError();
 }

@@ -9,6 +9,8 @@
 
 namespace lr {
 
+enum : int { kRecKind8 = 0, kRecKind16 = 1, kRecKindSucc = 2 };
+
 struct InitParams {
   int32_t nlev;                       // levels in the plan (0..nlev-1)
   uint32_t n0;                        // elements at level 0
@@ -27,6 +29,7 @@ void count_launch(int k = 1);
 int64_t launch_count();
 
 int device_sm_count();
+int stream_grid(uint64_t work_items, int block);
 
 cudaError_t launch_init(LevelDesc *desc, const InitParams &p, cudaStream_t s);
 
@@ -49,7 +52,7 @@ cudaError_t launch_count_heads(const uint32_t *bitmap, uint32_t n, uint32_t *out
 // Head selection of level `lev` (reads the bitmap at level 0, the head list
 // otherwise), then the exclusive scan and the writes.
 cudaError_t launch_heads(LevelDesc *desc, int lev, int nlev, const uint32_t *bitmap,
-                         const uint32_t *hlist, void *work, bool rec16, uint32_t *ns,
+                         const uint32_t *hlist, void *work, int rec_kind, uint32_t *ns,
                          uint32_t *hnext, uint64_t *blockcnt, uint32_t *err, uint32_t cutoff,
                          uint32_t hcap, uint32_t has_pd, cudaStream_t s);
 
@@ -67,6 +70,22 @@ cudaError_t launch_pd(LevelDesc *desc, int lev, const void *work, uint32_t cap, 
 cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec16,
                             const void *rnext, void *rout, int rank_bytes, uint32_t cap,
                             uint32_t *err, cudaStream_t s);
+
+// Log path (unweighted level 0, see lr_log.cu).
+cudaError_t launch_sum0(const uint32_t *succ, uint32_t n, unsigned long long *acc, uint32_t *err,
+                        cudaStream_t s);
+cudaError_t launch_heads0_log(LevelDesc *desc, const unsigned long long *acc, uint32_t *hlist0,
+                              const uint32_t *succ, uint32_t n, uint32_t *bitmap, uint32_t *err,
+                              int validate, cudaStream_t s);
+cudaError_t launch_chase_log(LevelDesc *desc, const uint32_t *succ, void *next_work, const uint32_t *ns,
+                             uint32_t *qctr, int grid, int block, uint32_t *err, uint32_t *log,
+                             uint2 *hdr, uint32_t per_cta, uint32_t total_chunks, uint32_t *ovf,
+                             cudaStream_t s);
+cudaError_t launch_finalize_log(LevelDesc *desc, const uint32_t *log, const uint2 *hdr,
+                                uint32_t total_chunks, const void *r1, uint2 *pairs, uint32_t *hist,
+                                int part_ctas, uint32_t shift, uint32_t *rank, uint32_t n, uint32_t *err,
+                                cudaStream_t s);
+int chase_log_occupancy(int block);
 
 int chase_occupancy(bool rec16, int block);
 cudaError_t kernels_setup();

@@ -180,3 +180,15 @@ def test_full_size_properties(n):
     pos[order] = torch.arange(n, device="cuda")
     pick = torch.randint(0, n, (4096,), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
     assert bool((r[pick] == n - 1 - pos[pick]).all())
+
+
+@pytest.mark.parametrize("path", ["log=0", "log=1", "log=1,f0=16,f=4", "xchg=0,log=0"])
+def test_level0_paths(path, monkeypatch):
+    """Both level-0 variants (log-based and in-place records) and their knobs."""
+    monkeypatch.setenv("LR_TUNING", path)
+    for n, seed in ((100_003, 1), ((1 << 20) + 9, 2)):
+        check_equal(gen.random_list(n, seed))
+        check_equal(gen.locality_list(n, seed))
+    succ, _ = gen.forest(1 << 20, 3, n_long=4, long_len=1 << 14, mean_short=64)
+    check_equal(succ)
+    check_equal(gen.random_list(300_000, 4), rank_dtype=np.int64)
