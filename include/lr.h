@@ -146,6 +146,31 @@ size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts);
  */
 lr_status lr_get_device_status(lr_stream stream);
 
+/*
+ * Rank without allocating.  The paper has no counterpart: this is a service
+ * for callers that cannot call cudaMalloc when they need a ranking (a process
+ * whose allocator already holds all free device memory, a latency-critical
+ * loop that must not risk an allocation's implicit synchronisation, a plug-in
+ * in a host that forbids allocations after start-up).
+ *  - succ: device uint32[n]; rank: device int32[n] (unweighted ranks).
+ *    Caller-owned; n <= LR_NOALLOC_MAX_N, larger n returns
+ *    LR_ERR_INVALID_ARGUMENT.
+ *  - Workspace is a fixed 64 MiB scratch array compiled into liblr.so; every
+ *    GPU that loads the library holds it until the process exits.  The
+ *    first call on a device looks up the array's device address (with that
+ *    device current).  No cudaMalloc, cudaFree or other allocating call is
+ *    made.  Inputs with so many lists that the recursion does not fit the
+ *    scratch return LR_ERR_CAPACITY.
+ *  - All calls share the scratch, which keeps the last call's contents
+ *    (everything that must start at zero is cleared by each call).  Calls
+ *    that overlap on the GPU race, and the host side is not thread-safe:
+ *    serialise calls.
+ *  - The call waits for the device and returns the final status (argument
+ *    or data error), like lr_opts.sync = 1.
+ */
+#define LR_NOALLOC_MAX_N (1LL << 22)
+lr_status lr_rank_noalloc(const uint32_t *succ, int64_t n, int32_t *rank, lr_stream stream);
+
 /* Human-readable name of a status code (static string). */
 const char *lr_status_string(lr_status s);
 

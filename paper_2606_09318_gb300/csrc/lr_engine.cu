@@ -186,16 +186,26 @@ static lr_status from_cuda(cudaError_t e) {
   return LR_ERR_CUDA;
 }
 
+lr_status setup_device_once() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return from_cuda(e);
+  std::lock_guard<std::mutex> g(g_mu);
+  if (dev >= 0 && dev < 64 && !g_setup_done[dev]) {
+    e = kernels_setup();
+    if (e != cudaSuccess) return from_cuda(e);
+    g_setup_done[dev] = true;
+  }
+  return LR_OK;
+}
+
 Ctx *get_ctx(cudaStream_t stream, lr_status *st) {
+  *st = setup_device_once();
+  if (*st != LR_OK) return nullptr;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) { *st = from_cuda(e); return nullptr; }
   std::lock_guard<std::mutex> g(g_mu);
-  if (dev >= 0 && dev < 64 && !g_setup_done[dev]) {
-    e = kernels_setup();
-    if (e != cudaSuccess) { *st = from_cuda(e); return nullptr; }
-    g_setup_done[dev] = true;
-  }
   auto key = std::make_pair(dev, (uintptr_t)stream);
   auto it = g_ctx.find(key);
   if (it != g_ctx.end()) { *st = LR_OK; return it->second; }
@@ -287,6 +297,8 @@ struct Inputs {
   const uint32_t *const *sptr;   // per-instance pointer tables (device), or null
   const void *const *wptr;
   void *const *rptr;
+  Ctx *ctx;                      // use this context instead of the per-stream one
+  int count_in_ws;               // caller workspace, but still count the lists first
 };
 
 static lr_status map_device_bits(uint32_t bits) {
@@ -306,8 +318,8 @@ static lr_status map_device_bits(uint32_t bits) {
 
 lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   const bool ptrs = in.sptr != nullptr;
-  lr_status st;
-  Ctx *c = get_ctx(s, &st);
+  lr_status st = LR_OK;
+  Ctx *c = in.ctx ? in.ctx : get_ctx(s, &st);
   if (!c) return st;
   if (in.n == 0) {
     // nothing to rank; still clear the stream's recorded status
@@ -321,7 +333,8 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   const bool log0 = u.logmode && !ptrs && in.offsets == nullptr && in.wtype == 0 &&
                     in.rank_bytes == 4 && in.n > u.cutoff && in.n < (1ull << 31);
   const int grid = chase_grid_for(u, rec16_0, log0);
-  const bool need_count = in.max_lists <= 0 && in.ws == nullptr && (in.n > u.cutoff || ptrs);
+  const bool need_count = in.max_lists <= 0 && (in.ws == nullptr || in.count_in_ws) &&
+                          (in.n > u.cutoff || ptrs);
   if (need_count && capturing) return LR_ERR_CAPTURE;
   uint64_t hb = in.max_lists > 0 ? (uint64_t)in.max_lists : in.n;
   Plan p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0);
@@ -330,7 +343,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   char *fixed = nullptr;
   char *var = nullptr;
   if (in.ws) {
-    if (in.ws_bytes < p.fixed_bytes + p.var_bytes) return LR_ERR_INVALID_ARGUMENT;
+    if (in.ws_bytes < p.fixed_bytes + (need_count ? 0 : p.var_bytes)) return LR_ERR_INVALID_ARGUMENT;
     fixed = (char *)in.ws;
     var = fixed + p.fixed_bytes;
   } else {
@@ -347,7 +360,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   void *work0 = fixed + p.off_work[0];
 
   Profiler prof;
-  prof.begin(s, (int64_t)in.n);
+  if (!in.ctx) prof.begin(s, (int64_t)in.n);
   unsigned long long *acc = (unsigned long long *)(fixed + p.off_acc);
   LR_TRY(cudaMemsetAsync(fixed + p.off_zero, 0, p.zero_bytes, s));
   LR_TRY(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * ((in.n + 31) / 32), s));
@@ -377,6 +390,9 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     st = ensure_buffer(&c->var, &c->var_bytes, p.var_bytes, s);
     if (st != LR_OK) return st;
     var = (char *)c->var;
+  } else if (in.ws_bytes < p.fixed_bytes + p.var_bytes) {
+    LR_TRY(cudaStreamSynchronize(s));     // nothing else may still write the caller's memory
+    return LR_ERR_CAPACITY;               // the lists need more workspace than was given
   }
   prof.mark(PH_PREP);
 
@@ -461,6 +477,23 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     return map_device_bits(bits);
   }
   return LR_OK;
+}
+
+lr_status run_fixed_scratch(const uint32_t *succ, int64_t n, int32_t *rank, void *scratch,
+                            size_t scratch_bytes, Ctx *ctx, cudaStream_t s) {
+  Inputs in;
+  memset(&in, 0, sizeof(in));
+  in.succ = succ;
+  in.rank = rank;
+  in.rank_bytes = 4;
+  in.n = (uint64_t)n;
+  in.seed = 0x5eedull;
+  in.sync = 1;
+  in.ws = scratch;
+  in.ws_bytes = scratch_bytes;
+  in.ctx = ctx;
+  in.count_in_ws = 1;
+  return run(in, nullptr, s);
 }
 
 lr_status run_ptr_batch(const int64_t *offsets, int32_t k, int64_t n_total,

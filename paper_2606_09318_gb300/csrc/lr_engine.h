@@ -60,6 +60,12 @@ int chase_grid_for(const Tuning &u, bool rec16, bool log0);
 Ctx *get_ctx(cudaStream_t stream, lr_status *st);
 lr_status ensure_buffer(void **buf, size_t *cur, size_t want, cudaStream_t s);
 lr_status device_status(cudaStream_t s);
+// Unweighted int32 ranking inside caller-provided scratch with a caller-provided
+// host context (no allocation); counts the lists first and waits for the result.
+lr_status run_fixed_scratch(const uint32_t *succ, int64_t n, int32_t *rank, void *scratch,
+                            size_t scratch_bytes, Ctx *ctx, cudaStream_t s);
+// Kernel attributes (shared-memory limits) for the current device, once.
+lr_status setup_device_once();
 // Rank k instances given by per-instance device pointers (tables in device
 // memory); waits for the result and returns the status.
 lr_status run_ptr_batch(const int64_t *offsets, int32_t k, int64_t n_total,
