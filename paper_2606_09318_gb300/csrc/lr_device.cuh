@@ -157,6 +157,15 @@ __device__ __forceinline__ Rec16 ld_rec(const Rec16 *p) {
 __device__ __forceinline__ void st_rec(Rec16 *p, uint32_t cid, uint64_t off) {
   __stcg(reinterpret_cast<uint4 *>(p), make_uint4(0u, cid, (uint32_t)off, (uint32_t)(off >> 32)));
 }
+// One 32-byte store: a whole sector in a single request.  On GB300 two
+// 16-byte stores to one sector cost two DRAM accesses; this costs one.
+__device__ __forceinline__ void st_sector(void *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d,
+                                          uint32_t e, uint32_t f, uint32_t g, uint32_t h) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+               :: "l"(p), "r"(a), "r"(b), "r"(c), "r"(d), "r"(e), "r"(f), "r"(g), "r"(h)
+               : "memory");
+}
+
 // Swap in (ruler id, offset) and return the old record in one L2 atomic
 // (8-byte records only).
 __device__ __forceinline__ Rec8 xchg_rec(Rec8 *p, uint32_t cid, uint64_t off) {

@@ -156,9 +156,13 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
     p.shift = lg > 8 ? lg - 8 : 0;
     p.off_log = o; o = align_up(o + (size_t)p.total_chunks * 32 * 4);
     p.off_hdr = o; o = align_up(o + (size_t)p.total_chunks * 8);
+    uint32_t sB, na, kb, nw;
+    log_part_geometry((uint32_t)n, &sB, &na, &kb, &nw);
     p.off_pairs = o; o = align_up(o + (size_t)n * 8);
+    p.off_pairsB = o; o = align_up(o + (sB ? (size_t)n * 8 : 0));
     p.part_ctas = std::max(1, std::min(chase_grid, 152 * 8));
     p.off_hist = o; o = align_up(o + (size_t)p.part_ctas * 256 * 4);
+    p.off_histB = o; o = align_up(o + (size_t)std::max<uint32_t>(1, na * kb) * 256 * 4);
   }
   p.off_hA = o; o = align_up(o + 4 * (size_t)p.hcap);
   p.off_hB = o; o = align_up(o + 4 * (size_t)p.hcap);
@@ -193,6 +197,7 @@ lr_status setup_device_once() {
   std::lock_guard<std::mutex> g(g_mu);
   if (dev >= 0 && dev < 64 && !g_setup_done[dev]) {
     e = kernels_setup();
+    if (e == cudaSuccess) e = log_setup();
     if (e != cudaSuccess) return from_cuda(e);
     g_setup_done[dev] = true;
   }
@@ -331,7 +336,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   const Tuning u = resolve_tuning(tuning, (int64_t)in.n, in.wtype != 0);
   const bool rec16_0 = in.wtype != 0;
   const bool log0 = u.logmode && !ptrs && in.offsets == nullptr && in.wtype == 0 &&
-                    in.rank_bytes == 4 && in.n > u.cutoff && in.n < (1ull << 31);
+                    in.rank_bytes == 4 && in.n > u.cutoff && in.n <= (1ull << 30);
   const int grid = chase_grid_for(u, rec16_0, log0);
   const bool need_count = in.max_lists <= 0 && (in.ws == nullptr || in.count_in_ws) &&
                           (in.n > u.cutoff || ptrs);
@@ -359,6 +364,9 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   uint32_t *bitmap = (uint32_t *)(fixed + p.off_bitmap);
   void *work0 = fixed + p.off_work[0];
 
+  // Single instance, no validation: heads from the streaming sums (one list)
+  // with the bitmap as the fallback, instead of atomics for every element.
+  const bool sums0 = !log0 && !ptrs && in.offsets == nullptr && !in.validate && in.n > u.cutoff;
   Profiler prof;
   if (!in.ctx) prof.begin(s, (int64_t)in.n);
   unsigned long long *acc = (unsigned long long *)(fixed + p.off_acc);
@@ -371,12 +379,12 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
                              in.validate, in.offsets, in.k, s));
   else
     LR_TRY(launch_prep0(in.succ, in.weight, in.wtype, (uint32_t)in.n, work0, bitmap, err,
-                        in.validate, in.offsets, in.k, s));
+                        in.validate, in.offsets, in.k, sums0 ? acc : nullptr, s));
   if (need_count) {
     // count the lists (one wait), then size the recursion for exactly that many:
-    // the log path counts terminals in its reduction, the record path counts
-    // zero bits of the has-predecessor bitmap
-    if (log0) {
+    // a single-instance pass counts terminals in its reduction, the batched
+    // passes count zero bits of the has-predecessor bitmap
+    if (log0 || sums0) {
       LR_TRY(cudaMemcpyAsync(c->host_words + 1, acc, 4, cudaMemcpyDeviceToHost, s));
     } else {
       LR_TRY(launch_count_heads(bitmap, (uint32_t)in.n, hcount, s));
@@ -412,10 +420,9 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   ip.hcap = p.hcap;
   LR_TRY(launch_init(desc, ip, s));
   uint32_t *hA0 = (uint32_t *)(var + p.off_hA);
-  if (log0) {
-    LR_TRY(cudaMemsetAsync(var + p.off_hdr, 0xFF, (size_t)p.total_chunks * 8, s));
+  if (log0) LR_TRY(cudaMemsetAsync(var + p.off_hdr, 0xFF, (size_t)p.total_chunks * 8, s));
+  if (log0 || sums0)
     LR_TRY(launch_heads0_log(desc, acc, hA0, in.succ, (uint32_t)in.n, bitmap, err, in.validate, s));
-  }
 
   auto work_of = [&](int l) -> void * { return l == 0 ? work0 : (void *)(var + p.off_work[l]); };
   auto R_of = [&](int l) -> void * { return l == 0 ? in.rank : (void *)(var + p.off_R[l]); };
@@ -456,8 +463,9 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     if (l == 0 && log0)
       LR_TRY(launch_finalize_log(desc, (const uint32_t *)(var + p.off_log), (const uint2 *)(var + p.off_hdr),
                                  p.total_chunks, R_of(1), (uint2 *)(var + p.off_pairs),
-                                 (uint32_t *)(var + p.off_hist), p.part_ctas, p.shift,
-                                 (uint32_t *)in.rank, (uint32_t)in.n, err, s));
+                                 (uint2 *)(var + p.off_pairsB), (uint32_t *)(var + p.off_hist),
+                                 (uint32_t *)(var + p.off_histB), p.part_ctas, (uint32_t *)in.rank,
+                                 (uint32_t)in.n, err, s));
     else if (l == 0 && ptrs)
       LR_TRY(launch_finalize_ptrs(desc, work0, rec16_0, R_of(1), in.rptr, p.rank_bytes, p.cap[0],
                                   in.offsets, in.k, err, s));
@@ -699,7 +707,7 @@ size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts) {
   // the answer needs no GPU: 256 SMs x 16 CTAs.
   const uint64_t h = opts->max_lists > 0 ? (uint64_t)opts->max_lists : (uint64_t)n_total;
   const bool log0 = u.logmode && k == 0 && opts->wtype == LR_NONE && opts->rtype == LR_I32 &&
-                    (uint64_t)n_total > u.cutoff && n_total < ((int64_t)1 << 31);
+                    (uint64_t)n_total > u.cutoff && n_total <= ((int64_t)1 << 30);
   Plan p = make_plan((uint64_t)n_total, h, u, opts->wtype != LR_NONE,
                      opts->rtype == LR_I64 ? 8 : 4, opts->seed, 256 * 16, false, log0);
   return p.fixed_bytes + p.var_bytes;

@@ -34,7 +34,7 @@ struct Plan {
   // variable part
   size_t off_work[kMaxLevels + 1], off_R[kMaxLevels + 1];
   size_t off_hA, off_hB, off_ns, off_pd[4];
-  size_t off_log, off_hdr, off_pairs, off_hist;   // log path
+  size_t off_log, off_hdr, off_pairs, off_pairsB, off_hist, off_histB;   // log path
   uint32_t per_cta, total_chunks, shift;
   int part_ctas;
   size_t var_bytes;

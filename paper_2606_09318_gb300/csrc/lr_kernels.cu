@@ -84,11 +84,15 @@ __device__ __forceinline__ uint64_t load_weight(const void *w, uint32_t i) {
 // findInit), and pack {succ, kUnvisited[, link weight]} records.  A terminal's
 // weight is stored as 0, so every deeper computation can treat weights
 // inclusively.
+// sums != nullptr: instead of the bitmap, accumulate the number of terminals
+// and the sum of the other successors (single-list head, see k_heads_single).
 template <int WT>
 __global__ void __launch_bounds__(256)
 k_prep0(const uint32_t *__restrict__ succ, const void *__restrict__ weight, uint32_t n,
         void *__restrict__ work, uint32_t *__restrict__ bitmap, uint32_t *__restrict__ err,
-        int validate, int vec, const int64_t *__restrict__ offsets, int32_t k) {
+        int validate, int vec, const int64_t *__restrict__ offsets, int32_t k,
+        unsigned long long *__restrict__ sums) {
+  unsigned long long sT = 0, sS = 0;
   const uint32_t ngroups = (uint32_t)(((uint64_t)n + 3u) / 4u);
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
@@ -142,36 +146,56 @@ k_prep0(const uint32_t *__restrict__ succ, const void *__restrict__ weight, uint
     for (uint32_t j = 0; j < cnt; ++j) {
       const uint32_t i = i0 + j;
       if (s[j] != i) {
-        const uint32_t bit = 1u << (s[j] & 31u);
-        if (validate) {
-          if (atomicOr(bitmap + (s[j] >> 5), bit) & bit) record_error(err, kErrNotList);
+        if (sums) {
+          sS += s[j];
         } else {
-          atomicOr(bitmap + (s[j] >> 5), bit);
+          const uint32_t bit = 1u << (s[j] & 31u);
+          if (validate) {
+            if (atomicOr(bitmap + (s[j] >> 5), bit) & bit) record_error(err, kErrNotList);
+          } else {
+            atomicOr(bitmap + (s[j] >> 5), bit);
+          }
         }
       } else {
         w[j] = 0u;   // a terminal has no outgoing link
+        sT += 1;
       }
     }
     if constexpr (WT == 0) {
       uint2 *out = reinterpret_cast<uint2 *>(work) + i0;
       if (cnt == 4u) {
-        uint4 *o4 = reinterpret_cast<uint4 *>(out);
-        __stcs(o4, make_uint4(s[0], kUnvisited, s[1], kUnvisited));
-        __stcs(o4 + 1, make_uint4(s[2], kUnvisited, s[3], kUnvisited));
+        st_sector(out, s[0], kUnvisited, s[1], kUnvisited, s[2], kUnvisited, s[3], kUnvisited);
       } else {
         for (uint32_t j = 0; j < cnt; ++j) out[j] = make_uint2(s[j], kUnvisited);
       }
     } else {
       uint4 *out = reinterpret_cast<uint4 *>(work) + i0;
-      for (uint32_t j = 0; j < cnt; ++j)
-        __stcs(out + j, make_uint4(s[j], kUnvisited, (uint32_t)w[j], (uint32_t)(w[j] >> 32)));
+      if (cnt == 4u) {
+        st_sector(out, s[0], kUnvisited, (uint32_t)w[0], (uint32_t)(w[0] >> 32),
+                  s[1], kUnvisited, (uint32_t)w[1], (uint32_t)(w[1] >> 32));
+        st_sector(out + 2, s[2], kUnvisited, (uint32_t)w[2], (uint32_t)(w[2] >> 32),
+                  s[3], kUnvisited, (uint32_t)w[3], (uint32_t)(w[3] >> 32));
+      } else {
+        for (uint32_t j = 0; j < cnt; ++j)
+          __stcs(out + j, make_uint4(s[j], kUnvisited, (uint32_t)w[j], (uint32_t)(w[j] >> 32)));
+      }
+    }
+  }
+  if (sums) {
+    for (int d = 16; d > 0; d >>= 1) {
+      sS += __shfl_down_sync(0xFFFFFFFFu, sS, d);
+      sT += __shfl_down_sync(0xFFFFFFFFu, sT, d);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (sT) atomicAdd(sums + 0, sT);
+      if (sS) atomicAdd(sums + 1, sS);
     }
   }
 }
 
 cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, uint32_t n,
                          void *work, uint32_t *bitmap, uint32_t *err, int validate,
-                         const int64_t *offsets, int32_t k, cudaStream_t s) {
+                         const int64_t *offsets, int32_t k, unsigned long long *sums, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int block = 256;
   const int grid = stream_grid(((uint64_t)n + 3) / 4, block);
@@ -179,9 +203,9 @@ cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, ui
   if (wtype == 1) vec = vec && ((uintptr_t)weight & 15u) == 0;
   if (wtype == 2) vec = vec && ((uintptr_t)weight & 15u) == 0;
   switch (wtype) {
-    case 0: k_prep0<0><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k); break;
-    case 1: k_prep0<1><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k); break;
-    default: k_prep0<2><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k); break;
+    case 0: k_prep0<0><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k, sums); break;
+    case 1: k_prep0<1><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k, sums); break;
+    default: k_prep0<2><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k, sums); break;
   }
   count_launch();
   return cudaGetLastError();

@@ -37,7 +37,7 @@ cudaError_t launch_init(LevelDesc *desc, const InitParams &p, cudaStream_t s);
 // input with local successor ids (k instances).
 cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, uint32_t n,
                          void *work, uint32_t *bitmap, uint32_t *err, int validate,
-                         const int64_t *offsets, int32_t k, cudaStream_t s);
+                         const int64_t *offsets, int32_t k, unsigned long long *sums, cudaStream_t s);
 
 cudaError_t launch_prep0_ptrs(const uint32_t *const *sptr, const void *const *wptr, int wtype,
                               uint32_t n, void *work, uint32_t *bitmap, uint32_t *err, int validate,
@@ -82,9 +82,11 @@ cudaError_t launch_chase_log(LevelDesc *desc, const uint32_t *succ, void *next_w
                              uint2 *hdr, uint32_t per_cta, uint32_t total_chunks, uint32_t *ovf,
                              cudaStream_t s);
 cudaError_t launch_finalize_log(LevelDesc *desc, const uint32_t *log, const uint2 *hdr,
-                                uint32_t total_chunks, const void *r1, uint2 *pairs, uint32_t *hist,
-                                int part_ctas, uint32_t shift, uint32_t *rank, uint32_t n, uint32_t *err,
-                                cudaStream_t s);
+                                uint32_t total_chunks, const void *r1, uint2 *pairsA, uint2 *pairsB,
+                                uint32_t *histA, uint32_t *histB, int ga, uint32_t *rank, uint32_t n,
+                                uint32_t *err, cudaStream_t s);
+void log_part_geometry(uint32_t n, uint32_t *sB, uint32_t *na, uint32_t *kb, uint32_t *nw);
+cudaError_t log_setup();
 int chase_log_occupancy(int block);
 
 int chase_occupancy(bool rec16, int block);

@@ -125,17 +125,18 @@ struct LogCfg {
   uint32_t *ovf;          // overflow pool cursor
 };
 
-// Entries are buffered four at a time (a register shift buffer) and stored
-// as one 16-byte vector.
+// Entries are buffered eight at a time (a register shift buffer) and stored
+// as one 32-byte sector with a single 256-bit store: on GB300 a sector
+// written in smaller pieces costs one DRAM access per piece.
 struct LogWriter {
   uint32_t chunk, slot, nb;
-  uint32_t b0, b1, b2, b3;
+  uint32_t b0, b1, b2, b3, b4, b5, b6, b7;
   uint32_t gc, go;   // (ruler, offset) of the buffered group's first entry
   bool ok;
 
   __device__ void init() {
     slot = kChunk; nb = 0; ok = true; chunk = 0; gc = kLogEnd; go = 0;
-    b0 = b1 = b2 = b3 = kLogEnd;
+    b0 = b1 = b2 = b3 = b4 = b5 = b6 = b7 = kLogEnd;
   }
   __device__ bool alloc(const LogCfg &L, uint32_t *s_used) {
     const uint32_t i = atomicAdd(s_used, 1u);
@@ -152,25 +153,28 @@ struct LogWriter {
   __device__ void flush(const LogCfg &L, uint32_t *s_used) {
     nb = 0;
     if (!ok || (slot == kChunk && !alloc(L, s_used))) return;
-    __stcg(reinterpret_cast<uint4 *>(L.log + (size_t)chunk * kChunk + slot), make_uint4(b0, b1, b2, b3));
-    slot += 4;
+    st_sector(L.log + (size_t)chunk * kChunk + slot, b0, b1, b2, b3, b4, b5, b6, b7);
+    slot += 8;
+  }
+  __device__ __forceinline__ void shift_in(uint32_t v) {
+    b0 = b1; b1 = b2; b2 = b3; b3 = b4; b4 = b5; b5 = b6; b6 = b7; b7 = v;
   }
   // v: the entry; (c, o): its ruler and offset when v is an element
   __device__ __forceinline__ void put(const LogCfg &L, uint32_t *s_used, uint32_t v, uint32_t c,
                                       uint32_t o) {
     if (nb == 0) { gc = c; go = o; }
-    b0 = b1; b1 = b2; b2 = b3; b3 = v;
-    if (++nb == 4) flush(L, s_used);
+    shift_in(v);
+    if (++nb == 8) flush(L, s_used);
   }
   __device__ void finish(const LogCfg &L, uint32_t *s_used) {
     if (nb > 0) {
-      while (nb < 4) { b0 = b1; b1 = b2; b2 = b3; b3 = kLogEnd; ++nb; }
+      while (nb < 8) { shift_in(kLogEnd); ++nb; }
       flush(L, s_used);
     }
     if (ok && slot < kChunk) {
-      for (; slot < kChunk; slot += 4)
-        __stcg(reinterpret_cast<uint4 *>(L.log + (size_t)chunk * kChunk + slot),
-               make_uint4(kLogEnd, kLogEnd, kLogEnd, kLogEnd));
+      for (; slot < kChunk; slot += 8)
+        st_sector(L.log + (size_t)chunk * kChunk + slot, kLogEnd, kLogEnd, kLogEnd, kLogEnd,
+                  kLogEnd, kLogEnd, kLogEnd, kLogEnd);
     }
   }
 };
@@ -263,127 +267,348 @@ int chase_log_occupancy(int block) {
 }
 
 // ---------------------------------------------------------------- propagation
-// Radix partition of the log by index range, without global atomics:
-//   H: every CTA decodes its contiguous share of chunks and counts entries
-//      per bucket (256 buckets of 2^shift indices);
-//   S: one CTA turns the per-CTA counts into write offsets, bucket by bucket
-//      (a bucket's region is fixed: exactly its index range for a valid list);
-//   W: every CTA decodes the same chunks again, computes rank = R_1[ruler] -
-//      offset and appends (y, rank) at its own cursor inside each bucket.
-// Decoding a chunk takes one warp: the last mark at or before a lane gives
-// the lane's ruler and offset (ballot + shuffle).
+// Ruler propagation for the log path.  Every element y appears once in the
+// log with its ruler c and offset o; its rank is R_1[c] - o and must land at
+// rank[y].  Writing 4-byte ranks at random y costs a DRAM access each on
+// GB300, so the pairs (y, rank) are first sorted by y into windows of
+// 2^kLgWin elements (a two-level radix partition whose writes are whole
+// 32-byte sectors), then each window is assembled in shared memory and
+// written out as whole lines.
+//   level A: decode the log, partition by A-bucket (y >> (kLgWin + sB));
+//   level B: partition each A-bucket by window (only when there are more
+//            windows than one level can hold);
+//   scatter: one CTA per window.
+// Each pass is count / offsets / write, with no global atomics: the region
+// of every bucket is fixed (exactly its index range, for a valid list) and
+// the per-CTA offsets inside it come from a column scan of the counts.
+constexpr int kLgWin = 14;                 // 16384 ranks = 64 KiB of shared memory
+constexpr int kMaxBuckets = 256;
+constexpr int kPartTile = 4096;            // items staged per partition tile
+constexpr int kPartThreads = 256;
+
+struct PartSmem {
+  uint2 carry[kMaxBuckets * 4];            // < 4 leftover pairs per bucket
+  uint32_t ccnt[kMaxBuckets];
+  uint32_t gpos[kMaxBuckets];              // next global slot of each bucket
+  uint32_t tcnt[kMaxBuckets];
+  uint32_t toff[kMaxBuckets];
+  uint32_t tcur[kMaxBuckets];
+  uint32_t nt;
+  uint2 tmp[kPartTile];
+  uint2 sorted[kPartTile];
+  uint16_t tb[kPartTile];
+};
+
+// Decode one warp-chunk of the log: the last mark at or before a lane gives
+// the lane's ruler and offset (ballot + shuffle).  Calls f(y, c, o) for the
+// element entries.  Must be called by a whole warp.
 template <class F>
-__device__ __forceinline__ void decode_chunks(const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
-                                              uint32_t c0, uint32_t c1, uint32_t n, F &&f) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (uint32_t id = c0 + warp; id < c1; id += nwarps) {
-    const uint2 h = __ldg(hdr + id);
-    if (h.y == kLogEnd) continue;                      // chunk never allocated (warp-uniform)
-    const uint32_t e = __ldg(log + (size_t)id * kChunk + lane);
-    const bool mark = e != kLogEnd && (e & kMark);
-    const uint32_t mm = __ballot_sync(0xFFFFFFFFu, mark);
-    const uint32_t below = mm & ((2u << lane) - 1u);
-    const int m = below ? 31 - __clz(below) : 0;
-    const uint32_t em = __shfl_sync(0xFFFFFFFFu, e, m);
-    const uint32_t c = below ? (em & ~kMark) : h.x;
-    const uint32_t o = below ? (uint32_t)(lane - m - 1) : h.y + (uint32_t)lane;
-    if (e != kLogEnd && !(e & kMark) && e < n) f(e, c, o);
-  }
+__device__ __forceinline__ void decode_chunk(const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
+                                             uint32_t id, uint32_t n, F &&f) {
+  const int lane = threadIdx.x & 31;
+  const uint2 h = __ldg(hdr + id);
+  if (h.y == kLogEnd) return;                      // chunk never allocated (warp-uniform)
+  const uint32_t e = __ldg(log + (size_t)id * kChunk + lane);
+  const bool mark = e != kLogEnd && (e & kMark);
+  const uint32_t mm = __ballot_sync(0xFFFFFFFFu, mark);
+  const uint32_t below = mm & ((2u << lane) - 1u);
+  const int m = below ? 31 - __clz(below) : 0;
+  const uint32_t em = __shfl_sync(0xFFFFFFFFu, e, m);
+  const uint32_t c = below ? (em & ~kMark) : h.x;
+  const uint32_t o = below ? (uint32_t)(lane - m - 1) : h.y + (uint32_t)lane;
+  if (e != kLogEnd && !(e & kMark) && e < n) f(e, c, o);
 }
 
-__global__ void __launch_bounds__(256)
-k_part_hist(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log,
-            const uint2 *__restrict__ hdr, uint32_t total_chunks, uint32_t *__restrict__ hist,
-            uint32_t shift) {
-  __shared__ uint32_t sh[kBuckets];
-  const LevelDesc d = desc[0];
-  if (d.mode != kModeSrs) return;
-  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) sh[b] = 0;
+// Staged tile -> per-bucket runs -> whole-sector stores.  The caller has put
+// nt items into tmp/tb; gpos/ccnt/carry persist across tiles.
+// lim: size of `out`; positions past it (only possible for an invalid list,
+// which the count scan reports) are dropped.
+__device__ void part_emit_tile(PartSmem &S, int nb, uint2 *__restrict__ out, uint32_t lim, uint32_t &bad) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const uint32_t nt = S.nt;
+  for (uint32_t k = tid; k < nt; k += blockDim.x) atomicAdd(&S.tcnt[S.tb[k]], 1u);
+  __syncthreads();
+  if (warp == 0) {                                 // exclusive scan of <= 256 counts
+    uint32_t run = 0;
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+      const int b = b0 + lane;
+      const uint32_t v = b < nb ? S.tcnt[b] : 0u;
+      uint32_t x = v;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+        if (lane >= d) x += y;
+      }
+      if (b < nb) S.toff[b] = run + x - v;
+      run += __shfl_sync(0xFFFFFFFFu, x, 31);
+    }
+  }
+  __syncthreads();
+  for (uint32_t k = tid; k < nt; k += blockDim.x) {
+    const uint32_t b = S.tb[k];
+    S.sorted[S.toff[b] + atomicAdd(&S.tcur[b], 1u)] = S.tmp[k];
+  }
+  __syncthreads();
+  for (int b = warp; b < nb; b += nwarps) {
+    const uint32_t c = S.ccnt[b], m = c + S.tcnt[b], g = S.gpos[b], t0 = S.toff[b];
+    auto seq = [&](uint32_t k) -> uint2 { return k < c ? S.carry[b * 4 + k] : S.sorted[t0 + k - c]; };
+    const uint32_t h = min(m, (4u - (g & 3u)) & 3u);   // pairs up to the next sector boundary
+    if ((uint32_t)lane < h && g + lane < lim) out[g + lane] = seq(lane);
+    const uint32_t nfull = (m - h) / 4u;
+    for (uint32_t q = lane; q < nfull; q += 32) {
+      const uint32_t k = h + 4u * q;
+      const uint2 a = seq(k), bb = seq(k + 1), cc = seq(k + 2), dd = seq(k + 3);
+      if ((uint64_t)g + k + 3 < lim) st_sector(out + g + k, a.x, a.y, bb.x, bb.y, cc.x, cc.y, dd.x, dd.y);
+      else bad |= kErrNotList;
+    }
+    const uint32_t used = h + 4u * nfull, rest = m - used;
+    uint2 keep = make_uint2(0u, 0u);
+    if ((uint32_t)lane < rest) keep = seq(used + lane);
+    __syncwarp();
+    if ((uint32_t)lane < rest) S.carry[b * 4 + lane] = keep;
+    if (lane == 0) {
+      S.gpos[b] = g + used;
+      S.ccnt[b] = rest;
+      S.tcnt[b] = 0;
+      S.tcur[b] = 0;
+    }
+  }
+  if (tid == 0) S.nt = 0;
+  __syncthreads();
+}
+
+__device__ void part_flush(PartSmem &S, int nb, uint2 *__restrict__ out, uint32_t lim) {
+  const int tid = threadIdx.x;
+  for (int b = tid; b < nb; b += blockDim.x)
+    for (uint32_t k = 0; k < S.ccnt[b]; ++k)
+      if ((uint64_t)S.gpos[b] + k < lim) out[S.gpos[b] + k] = S.carry[b * 4 + k];
+}
+
+__device__ void part_init(PartSmem &S, int nb, const uint32_t *__restrict__ offs) {
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    S.ccnt[b] = 0; S.tcnt[b] = 0; S.tcur[b] = 0;
+    S.gpos[b] = offs[b];
+  }
+  if (threadIdx.x == 0) S.nt = 0;
+  __syncthreads();
+}
+
+struct PartGeom {
+  uint32_t n;
+  uint32_t sB;          // level-B bits (windows per A-bucket = 2^sB)
+  uint32_t na;          // A-buckets
+  uint32_t kb;          // level-B CTAs per A-bucket
+  uint32_t nw;          // windows
+};
+
+__device__ __forceinline__ uint32_t bucket_a(uint32_t y, const PartGeom &G) { return y >> (kLgWin + G.sB); }
+__device__ __forceinline__ uint32_t bucket_b(uint32_t y, const PartGeom &G) {
+  return (y >> kLgWin) & ((1u << G.sB) - 1u);
+}
+
+// ---- level A
+__global__ void __launch_bounds__(kPartThreads)
+k_la_hist(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
+          uint32_t total_chunks, uint32_t *__restrict__ hist, PartGeom G) {
+  __shared__ uint32_t sh[kMaxBuckets];
+  if (desc[0].mode != kModeSrs) return;
+  for (int b = threadIdx.x; b < kMaxBuckets; b += blockDim.x) sh[b] = 0;
   __syncthreads();
   const uint32_t c0 = (uint32_t)((uint64_t)total_chunks * blockIdx.x / gridDim.x);
   const uint32_t c1 = (uint32_t)((uint64_t)total_chunks * (blockIdx.x + 1) / gridDim.x);
-  decode_chunks(log, hdr, c0, c1, d.n, [&](uint32_t y, uint32_t, uint32_t) { atomicAdd(&sh[y >> shift], 1u); });
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (uint32_t id = c0 + warp; id < c1; id += nwarps)
+    decode_chunk(log, hdr, id, G.n, [&](uint32_t y, uint32_t, uint32_t) { atomicAdd(&sh[bucket_a(y, G)], 1u); });
   __syncthreads();
-  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) hist[(size_t)blockIdx.x * kBuckets + b] = sh[b];
+  for (int b = threadIdx.x; b < (int)G.na; b += blockDim.x) hist[(size_t)blockIdx.x * G.na + b] = sh[b];
 }
 
-__global__ void __launch_bounds__(kBuckets)
-k_part_scan(const LevelDesc *__restrict__ desc, uint32_t *__restrict__ hist, int nctas, uint32_t shift,
-            uint32_t *__restrict__ err) {
-  const LevelDesc d = desc[0];
-  if (d.mode != kModeSrs) return;
-  const uint32_t b = threadIdx.x;
-  const uint64_t b0 = (uint64_t)b << shift;
-  uint64_t run = b0;
-  for (int k = 0; k < nctas; ++k) {
-    const uint32_t v = hist[(size_t)k * kBuckets + b];
-    hist[(size_t)k * kBuckets + b] = (uint32_t)run;
-    run += v;
+// Column scan: counts[cta][bucket] -> start slot of each CTA's run inside the
+// bucket; bucket b's region starts at base(b).  shift: log2 of a bucket's
+// index span.  groups > 1: CTAs come in groups (level B: one group per
+// A-bucket, buckets are that group's windows).
+__global__ void k_part_scan(const LevelDesc *__restrict__ desc, uint32_t *__restrict__ hist, int nctas_per_group,
+                            int nbuckets, uint32_t shift, uint32_t n, uint32_t *__restrict__ err) {
+  if (desc[0].mode != kModeSrs) return;
+  const int group = blockIdx.x;
+  for (int b = threadIdx.x; b < nbuckets; b += blockDim.x) {
+    const uint64_t bucket = (uint64_t)group * nbuckets + b;
+    const uint64_t base = bucket << shift;
+    uint64_t run = base;
+    for (int k = 0; k < nctas_per_group; ++k) {
+      uint32_t *h = hist + ((size_t)group * nctas_per_group + k) * nbuckets + b;
+      const uint32_t v = *h;
+      *h = (uint32_t)run;
+      run += v;
+    }
+    const uint64_t end = base + (1ull << shift);
+    if (base < n && run > (end < n ? end : (uint64_t)n)) record_error(err, kErrNotList);
   }
-  const uint64_t b1 = b0 + (1ull << shift);
-  if (run > (b1 < d.n ? b1 : (uint64_t)d.n) && b0 < d.n) record_error(err, kErrNotList);
 }
 
-__global__ void __launch_bounds__(256)
-k_part_write(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log,
-             const uint2 *__restrict__ hdr, uint32_t total_chunks, const uint32_t *__restrict__ hist,
-             const uint32_t *__restrict__ r1, uint2 *__restrict__ pairs, uint32_t shift,
-             uint32_t *__restrict__ err) {
-  __shared__ uint32_t cur[kBuckets];
+__global__ void __launch_bounds__(kPartThreads)
+k_la_write(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
+           uint32_t total_chunks, const uint32_t *__restrict__ offs, const uint32_t *__restrict__ r1,
+           uint2 *__restrict__ out, PartGeom G, uint32_t *__restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_part[];
+  PartSmem &S = *reinterpret_cast<PartSmem *>(smem_part);
   const LevelDesc d = desc[0];
   if (d.mode != kModeSrs) return;
-  const uint32_t n = d.n, nn = desc[1].n;
-  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) cur[b] = hist[(size_t)blockIdx.x * kBuckets + b];
-  __syncthreads();
+  const uint32_t nn = desc[1].n;
+  part_init(S, G.na, offs + (size_t)blockIdx.x * G.na);
   const uint32_t c0 = (uint32_t)((uint64_t)total_chunks * blockIdx.x / gridDim.x);
   const uint32_t c1 = (uint32_t)((uint64_t)total_chunks * (blockIdx.x + 1) / gridDim.x);
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  constexpr uint32_t kChunksPerTile = kPartTile / kChunk;
   uint32_t bad = 0;
-  decode_chunks(log, hdr, c0, c1, n, [&](uint32_t y, uint32_t c, uint32_t o) {
-    uint32_t val = 0;
-    if (c < nn) val = __ldcg(r1 + c) - o;
-    else bad |= kErrInternal;
-    const uint32_t b = y >> shift;
-    const uint32_t pos = atomicAdd(&cur[b], 1u);
-    const uint64_t b1 = ((uint64_t)b + 1) << shift;
-    if (pos < (b1 < n ? b1 : (uint64_t)n)) pairs[pos] = make_uint2(y, val);
-    else bad |= kErrNotList;                  // more entries than indices: a revisit
-  });
+  for (uint32_t t0 = c0; t0 < c1; t0 += kChunksPerTile) {
+    const uint32_t t1 = min(c1, t0 + kChunksPerTile);
+    for (uint32_t id = t0 + warp; id < t1; id += nwarps)
+      decode_chunk(log, hdr, id, G.n, [&](uint32_t y, uint32_t c, uint32_t o) {
+        uint32_t val = 0;
+        if (c < nn) val = __ldcg(r1 + c) - o;
+        else bad |= kErrInternal;
+        const uint32_t k = atomicAdd(&S.nt, 1u);
+        S.tmp[k] = make_uint2(y, val);
+        S.tb[k] = (uint16_t)bucket_a(y, G);
+      });
+    __syncthreads();
+    part_emit_tile(S, G.na, out, G.n, bad);
+  }
+  part_flush(S, G.na, out, G.n);
   if (bad) record_error(err, bad);
 }
 
-// Scatter: the partitioned pairs are ordered by index range, so at any time
-// the grid writes into one or two windows of rank[] that stay in L2.
+// ---- level B: CTA (a, i) handles part i of A-bucket a's region
+__device__ __forceinline__ void lb_range(const PartGeom &G, uint32_t &p0, uint32_t &p1) {
+  const uint32_t a = blockIdx.x / G.kb, i = blockIdx.x % G.kb;
+  const uint64_t s0 = (uint64_t)a << (kLgWin + G.sB);
+  const uint64_t e0 = s0 + (1ull << (kLgWin + G.sB));
+  const uint64_t s = s0 < G.n ? s0 : G.n, e = e0 < G.n ? e0 : G.n;
+  p0 = (uint32_t)(s + (e - s) * i / G.kb);
+  p1 = (uint32_t)(s + (e - s) * (i + 1) / G.kb);
+}
+
+__global__ void __launch_bounds__(kPartThreads)
+k_lb_hist(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, uint32_t *__restrict__ hist, PartGeom G) {
+  __shared__ uint32_t sh[kMaxBuckets];
+  if (desc[0].mode != kModeSrs) return;
+  const uint32_t nbk = 1u << G.sB;
+  for (int b = threadIdx.x; b < (int)nbk; b += blockDim.x) sh[b] = 0;
+  __syncthreads();
+  uint32_t p0, p1;
+  lb_range(G, p0, p1);
+  for (uint32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const uint32_t y = __ldcs(&in[p].x);
+    if (y < G.n) atomicAdd(&sh[bucket_b(y, G)], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < (int)nbk; b += blockDim.x) hist[(size_t)blockIdx.x * nbk + b] = sh[b];
+}
+
+__global__ void __launch_bounds__(kPartThreads)
+k_lb_write(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, const uint32_t *__restrict__ offs,
+           uint2 *__restrict__ out, PartGeom G, uint32_t *__restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_part[];
+  PartSmem &S = *reinterpret_cast<PartSmem *>(smem_part);
+  if (desc[0].mode != kModeSrs) return;
+  const uint32_t nbk = 1u << G.sB;
+  part_init(S, nbk, offs + (size_t)blockIdx.x * nbk);
+  uint32_t p0, p1;
+  lb_range(G, p0, p1);
+  uint32_t bad = 0;
+  for (uint32_t t0 = p0; t0 < p1; t0 += kPartTile) {
+    const uint32_t t1 = min(p1, t0 + kPartTile);
+    for (uint32_t p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
+      const uint2 v = __ldcs(in + p);
+      if (v.x < G.n) {
+        const uint32_t k = atomicAdd(&S.nt, 1u);
+        S.tmp[k] = v;
+        S.tb[k] = (uint16_t)bucket_b(v.x, G);
+      } else {
+        bad |= kErrInternal;
+      }
+    }
+    __syncthreads();
+    part_emit_tile(S, nbk, out, G.n, bad);
+  }
+  part_flush(S, nbk, out, G.n);
+  if (bad) record_error(err, bad);
+}
+
+// ---- scatter: one CTA per window of 2^kLgWin ranks assembled in shared memory
 __global__ void __launch_bounds__(256)
-k_scatter_log(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ pairs,
-              uint32_t *__restrict__ rank, uint32_t *__restrict__ err) {
+k_win_scatter(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, uint32_t *__restrict__ rank,
+              uint32_t *__restrict__ err) {
+  extern __shared__ __align__(16) uint32_t win[];
   const LevelDesc d = desc[0];
   if (d.mode != kModeSrs) return;
   const uint32_t n = d.n;
+  const uint64_t w0 = (uint64_t)blockIdx.x << kLgWin;
+  if (w0 >= n) return;
+  const uint32_t len = (uint32_t)min((uint64_t)1 << kLgWin, (uint64_t)n - w0);
   uint32_t bad = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0 && d.visited != n) bad |= d.visited > n ? kErrNotList : kErrCycle;
-  const uint32_t npairs2 = n / 2u;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < npairs2; i += gridDim.x * blockDim.x) {
-    const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(pairs) + i);
-    if (v.x < n) rank[v.x] = v.y; else bad |= kErrInternal;
-    if (v.z < n) rank[v.z] = v.w; else bad |= kErrInternal;
+  for (uint32_t p = threadIdx.x; p < len; p += blockDim.x) {
+    const uint2 v = __ldcs(in + w0 + p);
+    const uint64_t loc = (uint64_t)v.x - w0;
+    if (loc < len) win[loc] = v.y; else bad |= kErrInternal;
   }
-  if ((n & 1u) && blockIdx.x == 0 && threadIdx.x == 0) {
-    const uint2 v = pairs[n - 1];
-    if (v.x < n) rank[v.x] = v.y; else bad |= kErrInternal;
+  __syncthreads();
+  uint32_t *dst = rank + w0;
+  if ((len & 3u) == 0 && ((uintptr_t)dst & 15u) == 0) {
+    for (uint32_t q = threadIdx.x; q < len / 4; q += blockDim.x)
+      __stcs(reinterpret_cast<uint4 *>(dst) + q, reinterpret_cast<const uint4 *>(win)[q]);
+  } else {
+    for (uint32_t q = threadIdx.x; q < len; q += blockDim.x) dst[q] = win[q];
   }
   if (bad) record_error(err, bad);
 }
 
+// Host side: geometry and launch sequence.
+void log_part_geometry(uint32_t n, uint32_t *sB, uint32_t *na, uint32_t *kb, uint32_t *nw) {
+  const uint32_t w = (uint32_t)(((uint64_t)n + (1u << kLgWin) - 1) >> kLgWin);
+  uint32_t lg = 0;
+  while ((1ull << lg) < w) ++lg;
+  *sB = lg > 8 ? lg - 8 : 0;
+  *na = (w + (1u << *sB) - 1) >> *sB;
+  *kb = *sB ? std::max<uint32_t>(1, 1024 / *na) : 0;
+  *nw = w;
+}
+
+static size_t part_smem() { return sizeof(PartSmem); }
+
+cudaError_t log_setup() {
+  cudaError_t e = cudaFuncSetAttribute(k_la_write, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_lb_write, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_win_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4u << kLgWin));
+}
+
 cudaError_t launch_finalize_log(LevelDesc *desc, const uint32_t *log, const uint2 *hdr,
-                                uint32_t total_chunks, const void *r1, uint2 *pairs, uint32_t *hist,
-                                int part_ctas, uint32_t shift, uint32_t *rank, uint32_t n, uint32_t *err,
-                                cudaStream_t s) {
-  k_part_hist<<<part_ctas, 256, 0, s>>>(desc, log, hdr, total_chunks, hist, shift);
-  k_part_scan<<<1, kBuckets, 0, s>>>(desc, hist, part_ctas, shift, err);
-  k_part_write<<<part_ctas, 256, 0, s>>>(desc, log, hdr, total_chunks, hist,
-                                         reinterpret_cast<const uint32_t *>(r1), pairs, shift, err);
-  k_scatter_log<<<stream_grid(n / 2 + 1, 256), 256, 0, s>>>(desc, pairs, rank, err);
-  count_launch(4);
+                                uint32_t total_chunks, const void *r1, uint2 *pairsA, uint2 *pairsB,
+                                uint32_t *histA, uint32_t *histB, int ga, uint32_t *rank, uint32_t n,
+                                uint32_t *err, cudaStream_t s) {
+  PartGeom G;
+  G.n = n;
+  log_part_geometry(n, &G.sB, &G.na, &G.kb, &G.nw);
+  const uint32_t shiftA = kLgWin + G.sB;
+  k_la_hist<<<ga, kPartThreads, 0, s>>>(desc, log, hdr, total_chunks, histA, G);
+  k_part_scan<<<1, 256, 0, s>>>(desc, histA, ga, (int)G.na, shiftA, n, err);
+  k_la_write<<<ga, kPartThreads, part_smem(), s>>>(desc, log, hdr, total_chunks, histA,
+                                                   reinterpret_cast<const uint32_t *>(r1), pairsA, G, err);
+  const uint2 *final_pairs = pairsA;
+  int launches = 4;
+  if (G.sB > 0) {
+    const int gb = (int)(G.na * G.kb);
+    k_lb_hist<<<gb, kPartThreads, 0, s>>>(desc, pairsA, histB, G);
+    k_part_scan<<<G.na, 256, 0, s>>>(desc, histB, (int)G.kb, 1 << G.sB, kLgWin, n, err);
+    k_lb_write<<<gb, kPartThreads, part_smem(), s>>>(desc, pairsA, histB, pairsB, G, err);
+    final_pairs = pairsB;
+    launches += 3;
+  }
+  k_win_scatter<<<G.nw, 256, 4u << kLgWin, s>>>(desc, final_pairs, rank, err);
+  count_launch(launches);
   return cudaGetLastError();
 }
 
