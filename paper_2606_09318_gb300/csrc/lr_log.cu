@@ -283,96 +283,157 @@ int chase_log_occupancy(int block) {
 // the per-CTA offsets inside it come from a column scan of the counts.
 constexpr int kLgWin = 14;                 // 16384 ranks = 64 KiB of shared memory
 constexpr int kMaxBuckets = 256;
-constexpr int kPartTile = 4096;            // items staged per partition tile
 constexpr int kPartThreads = 256;
+constexpr int kIpt = 8;                    // items a thread holds per partition tile
+constexpr int kPartTile = kPartThreads * kIpt;
+constexpr int kDecodeIlp = 4;              // chunks a warp decodes with their loads in flight
 
 struct PartSmem {
   uint2 carry[kMaxBuckets * 4];            // < 4 leftover pairs per bucket
   uint32_t ccnt[kMaxBuckets];
   uint32_t gpos[kMaxBuckets];              // next global slot of each bucket
   uint32_t tcnt[kMaxBuckets];
-  uint32_t toff[kMaxBuckets];
+  uint32_t toff[kMaxBuckets + 1];          // + total
   uint32_t tcur[kMaxBuckets];
-  uint32_t nt;
-  uint2 tmp[kPartTile];
+  uint32_t fstart[kMaxBuckets + 1];        // first whole sector of each bucket in this tile
   uint2 sorted[kPartTile];
-  uint16_t tb[kPartTile];
 };
 
-// Decode one warp-chunk of the log: the last mark at or before a lane gives
-// the lane's ruler and offset (ballot + shuffle).  Calls f(y, c, o) for the
-// element entries.  Must be called by a whole warp.
-template <class F>
-__device__ __forceinline__ void decode_chunk(const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
-                                             uint32_t id, uint32_t n, F &&f) {
+// Decode kDecodeIlp chunks of the log per warp: all header and entry loads
+// are issued before any is used.  In a chunk, the last mark at or before a
+// lane gives the lane's ruler and offset (ballot + shuffle).  Each lane gets
+// at most one element per chunk: out[j] = (y, ruler), off[j] = offset, or
+// y = kLogEnd.  Must be called by whole warps.
+__device__ __forceinline__ void decode_ilp(const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
+                                           uint32_t base, uint32_t c1, uint32_t n, uint2 (&out)[kDecodeIlp],
+                                           uint32_t (&off)[kDecodeIlp]) {
   const int lane = threadIdx.x & 31;
-  const uint2 h = __ldg(hdr + id);
-  if (h.y == kLogEnd) return;                      // chunk never allocated (warp-uniform)
-  const uint32_t e = __ldg(log + (size_t)id * kChunk + lane);
-  const bool mark = e != kLogEnd && (e & kMark);
-  const uint32_t mm = __ballot_sync(0xFFFFFFFFu, mark);
-  const uint32_t below = mm & ((2u << lane) - 1u);
-  const int m = below ? 31 - __clz(below) : 0;
-  const uint32_t em = __shfl_sync(0xFFFFFFFFu, e, m);
-  const uint32_t c = below ? (em & ~kMark) : h.x;
-  const uint32_t o = below ? (uint32_t)(lane - m - 1) : h.y + (uint32_t)lane;
-  if (e != kLogEnd && !(e & kMark) && e < n) f(e, c, o);
+  uint2 h[kDecodeIlp];
+  uint32_t e[kDecodeIlp];
+#pragma unroll
+  for (int j = 0; j < kDecodeIlp; ++j) {
+    const uint32_t id = base + j;
+    h[j] = id < c1 ? __ldg(hdr + id) : make_uint2(kLogEnd, kLogEnd);
+    e[j] = id < c1 ? __ldg(log + (size_t)id * kChunk + lane) : kLogEnd;
+  }
+#pragma unroll
+  for (int j = 0; j < kDecodeIlp; ++j) {
+    out[j] = make_uint2(kLogEnd, 0u);
+    off[j] = 0;
+    if (h[j].y == kLogEnd) continue;               // chunk never allocated (warp-uniform)
+    const bool mark = e[j] != kLogEnd && (e[j] & kMark);
+    const uint32_t mm = __ballot_sync(0xFFFFFFFFu, mark);
+    const uint32_t below = mm & ((2u << lane) - 1u);
+    const int m = below ? 31 - __clz(below) : 0;
+    const uint32_t em = __shfl_sync(0xFFFFFFFFu, e[j], m);
+    const uint32_t c = below ? (em & ~kMark) : h[j].x;
+    const uint32_t o = below ? (uint32_t)(lane - m - 1) : h[j].y + (uint32_t)lane;
+    if (e[j] != kLogEnd && !(e[j] & kMark) && e[j] < n) { out[j] = make_uint2(e[j], c); off[j] = o; }
+  }
 }
 
-// Staged tile -> per-bucket runs -> whole-sector stores.  The caller has put
-// nt items into tmp/tb; gpos/ccnt/carry persist across tiles.
+// Whole-range decode (histogram pass): f(y) for every element.
+template <class F>
+__device__ __forceinline__ void decode_chunks(const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
+                                              uint32_t c0, uint32_t c1, uint32_t n, F &&f) {
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (uint32_t base = c0 + (uint32_t)warp * kDecodeIlp; base < c1; base += (uint32_t)nwarps * kDecodeIlp) {
+    uint2 it[kDecodeIlp];
+    uint32_t off[kDecodeIlp];
+    decode_ilp(log, hdr, base, c1, n, it, off);
+#pragma unroll
+    for (int j = 0; j < kDecodeIlp; ++j)
+      if (it[j].x != kLogEnd) f(it[j].x);
+  }
+}
+
+// Exclusive scan of nb (<= 256) shared-memory counts by warp 0; returns the
+// total through out[nb].
+__device__ __forceinline__ void warp0_scan(const uint32_t *in, uint32_t *out, int nb) {
+  const int lane = threadIdx.x & 31;
+  if ((threadIdx.x >> 5) != 0) return;
+  uint32_t run = 0;
+  for (int b0 = 0; b0 < nb; b0 += 32) {
+    const int b = b0 + lane;
+    const uint32_t v = b < nb ? in[b] : 0u;
+    uint32_t x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (b < nb) out[b] = run + x - v;
+    run += __shfl_sync(0xFFFFFFFFu, x, 31);
+  }
+  if (lane == 0) out[nb] = run;
+}
+
+// One tile of register-held items (item[i] valid when item[i].x != kLogEnd,
+// bk[i] its bucket) -> sorted by bucket in shared memory -> whole-sector
+// stores.  gpos/ccnt/carry persist across tiles: each bucket's output
+// continues its carry, so every store but a bucket's first (unaligned) head
+// and its final tail covers a whole 32-byte sector, one thread per sector.
 // lim: size of `out`; positions past it (only possible for an invalid list,
 // which the count scan reports) are dropped.
-__device__ void part_emit_tile(PartSmem &S, int nb, uint2 *__restrict__ out, uint32_t lim, uint32_t &bad) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  const uint32_t nt = S.nt;
-  for (uint32_t k = tid; k < nt; k += blockDim.x) atomicAdd(&S.tcnt[S.tb[k]], 1u);
+__device__ void part_emit_tile(PartSmem &S, int nb, const uint2 (&item)[kIpt], const uint32_t (&bk)[kIpt],
+                               uint2 *__restrict__ out, uint32_t lim, uint32_t &bad) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i)
+    if (item[i].x != kLogEnd) atomicAdd(&S.tcnt[bk[i]], 1u);
   __syncthreads();
-  if (warp == 0) {                                 // exclusive scan of <= 256 counts
-    uint32_t run = 0;
-    for (int b0 = 0; b0 < nb; b0 += 32) {
-      const int b = b0 + lane;
-      const uint32_t v = b < nb ? S.tcnt[b] : 0u;
-      uint32_t x = v;
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-        if (lane >= d) x += y;
-      }
-      if (b < nb) S.toff[b] = run + x - v;
-      run += __shfl_sync(0xFFFFFFFFu, x, 31);
-    }
+  warp0_scan(S.tcnt, S.toff, nb);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i)
+    if (item[i].x != kLogEnd) S.sorted[S.toff[bk[i]] + atomicAdd(&S.tcur[bk[i]], 1u)] = item[i];
+  __syncthreads();                                   // placement done before tcur is reused
+  // per bucket: pairs up to the next sector boundary (h), whole sectors (f)
+  for (int b = tid; b < nb; b += blockDim.x) {
+    const uint32_t m = S.ccnt[b] + S.tcnt[b], g = S.gpos[b];
+    const uint32_t h = min(m, (4u - (g & 3u)) & 3u);
+    S.tcur[b] = (m - h) / 4u;                        // reuse: whole sectors of bucket b
   }
   __syncthreads();
-  for (uint32_t k = tid; k < nt; k += blockDim.x) {
-    const uint32_t b = S.tb[k];
-    S.sorted[S.toff[b] + atomicAdd(&S.tcur[b], 1u)] = S.tmp[k];
-  }
+  warp0_scan(S.tcur, S.fstart, nb);
   __syncthreads();
-  for (int b = warp; b < nb; b += nwarps) {
-    const uint32_t c = S.ccnt[b], m = c + S.tcnt[b], g = S.gpos[b], t0 = S.toff[b];
-    auto seq = [&](uint32_t k) -> uint2 { return k < c ? S.carry[b * 4 + k] : S.sorted[t0 + k - c]; };
-    const uint32_t h = min(m, (4u - (g & 3u)) & 3u);   // pairs up to the next sector boundary
-    if ((uint32_t)lane < h && g + lane < lim) out[g + lane] = seq(lane);
-    const uint32_t nfull = (m - h) / 4u;
-    for (uint32_t q = lane; q < nfull; q += 32) {
-      const uint32_t k = h + 4u * q;
-      const uint2 a = seq(k), bb = seq(k + 1), cc = seq(k + 2), dd = seq(k + 3);
-      if ((uint64_t)g + k + 3 < lim) st_sector(out + g + k, a.x, a.y, bb.x, bb.y, cc.x, cc.y, dd.x, dd.y);
-      else bad |= kErrNotList;
+  auto seq = [&](int b, uint32_t k) -> uint2 {
+    const uint32_t c = S.ccnt[b];
+    return k < c ? S.carry[b * 4 + k] : S.sorted[S.toff[b] + k - c];
+  };
+  const uint32_t nsec = S.fstart[nb];
+  for (uint32_t sct = tid; sct < nsec; sct += blockDim.x) {
+    int lo = 0, hi = nb;                              // bucket: last b with fstart[b] <= sct
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (S.fstart[mid] <= sct) lo = mid; else hi = mid;
     }
-    const uint32_t used = h + 4u * nfull, rest = m - used;
-    uint2 keep = make_uint2(0u, 0u);
-    if ((uint32_t)lane < rest) keep = seq(used + lane);
-    __syncwarp();
-    if ((uint32_t)lane < rest) S.carry[b * 4 + lane] = keep;
-    if (lane == 0) {
-      S.gpos[b] = g + used;
-      S.ccnt[b] = rest;
-      S.tcnt[b] = 0;
-      S.tcur[b] = 0;
-    }
+    const int b = lo;
+    const uint32_t g = S.gpos[b];
+    const uint32_t h = min(S.ccnt[b] + S.tcnt[b], (4u - (g & 3u)) & 3u);
+    const uint32_t k = h + 4u * (sct - S.fstart[b]);
+    const uint2 a = seq(b, k), bb = seq(b, k + 1), cc = seq(b, k + 2), dd = seq(b, k + 3);
+    if ((uint64_t)g + k + 3 < lim) st_sector(out + g + k, a.x, a.y, bb.x, bb.y, cc.x, cc.y, dd.x, dd.y);
+    else bad |= kErrNotList;
   }
-  if (tid == 0) S.nt = 0;
+  __syncthreads();                                   // sector writers done with carry/gpos/ccnt
+  // heads and new carries: one thread per bucket (reads before it writes)
+  for (int b = tid; b < nb; b += blockDim.x) {
+    const uint32_t m = S.ccnt[b] + S.tcnt[b], g = S.gpos[b];
+    const uint32_t h = min(m, (4u - (g & 3u)) & 3u);
+    for (uint32_t k = 0; k < h; ++k)
+      if ((uint64_t)g + k < lim) out[g + k] = seq(b, k);
+    const uint32_t used = h + 4u * ((m - h) / 4u), rest = m - used;
+    const uint2 k0 = rest > 0 ? seq(b, used) : make_uint2(0u, 0u);
+    const uint2 k1 = rest > 1 ? seq(b, used + 1) : make_uint2(0u, 0u);
+    const uint2 k2 = rest > 2 ? seq(b, used + 2) : make_uint2(0u, 0u);
+    if (rest > 0) S.carry[b * 4 + 0] = k0;
+    if (rest > 1) S.carry[b * 4 + 1] = k1;
+    if (rest > 2) S.carry[b * 4 + 2] = k2;
+    S.gpos[b] = g + used;
+    S.ccnt[b] = rest;
+    S.tcnt[b] = 0;
+    S.tcur[b] = 0;
+  }
   __syncthreads();
 }
 
@@ -388,7 +449,6 @@ __device__ void part_init(PartSmem &S, int nb, const uint32_t *__restrict__ offs
     S.ccnt[b] = 0; S.tcnt[b] = 0; S.tcur[b] = 0;
     S.gpos[b] = offs[b];
   }
-  if (threadIdx.x == 0) S.nt = 0;
   __syncthreads();
 }
 
@@ -415,9 +475,7 @@ k_la_hist(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log, 
   __syncthreads();
   const uint32_t c0 = (uint32_t)((uint64_t)total_chunks * blockIdx.x / gridDim.x);
   const uint32_t c1 = (uint32_t)((uint64_t)total_chunks * (blockIdx.x + 1) / gridDim.x);
-  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (uint32_t id = c0 + warp; id < c1; id += nwarps)
-    decode_chunk(log, hdr, id, G.n, [&](uint32_t y, uint32_t, uint32_t) { atomicAdd(&sh[bucket_a(y, G)], 1u); });
+  decode_chunks(log, hdr, c0, c1, G.n, [&](uint32_t y) { atomicAdd(&sh[bucket_a(y, G)], 1u); });
   __syncthreads();
   for (int b = threadIdx.x; b < (int)G.na; b += blockDim.x) hist[(size_t)blockIdx.x * G.na + b] = sh[b];
 }
@@ -457,22 +515,33 @@ k_la_write(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log,
   part_init(S, G.na, offs + (size_t)blockIdx.x * G.na);
   const uint32_t c0 = (uint32_t)((uint64_t)total_chunks * blockIdx.x / gridDim.x);
   const uint32_t c1 = (uint32_t)((uint64_t)total_chunks * (blockIdx.x + 1) / gridDim.x);
+  // a tile: every warp decodes 2 x kDecodeIlp chunks, each lane keeps its
+  // (at most one per chunk) elements in registers
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  constexpr uint32_t kChunksPerTile = kPartTile / kChunk;
+  const uint32_t per_tile = (uint32_t)nwarps * 2 * kDecodeIlp;
   uint32_t bad = 0;
-  for (uint32_t t0 = c0; t0 < c1; t0 += kChunksPerTile) {
-    const uint32_t t1 = min(c1, t0 + kChunksPerTile);
-    for (uint32_t id = t0 + warp; id < t1; id += nwarps)
-      decode_chunk(log, hdr, id, G.n, [&](uint32_t y, uint32_t c, uint32_t o) {
-        uint32_t val = 0;
-        if (c < nn) val = __ldcg(r1 + c) - o;
-        else bad |= kErrInternal;
-        const uint32_t k = atomicAdd(&S.nt, 1u);
-        S.tmp[k] = make_uint2(y, val);
-        S.tb[k] = (uint16_t)bucket_a(y, G);
-      });
-    __syncthreads();
-    part_emit_tile(S, G.na, out, G.n, bad);
+  for (uint32_t t0 = c0; t0 < c1; t0 += per_tile) {
+    uint2 item[kIpt];
+    uint32_t off[kIpt], bk[kIpt];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      uint2 it[kDecodeIlp];
+      uint32_t of[kDecodeIlp];
+      decode_ilp(log, hdr, t0 + ((uint32_t)r * nwarps + warp) * kDecodeIlp, c1, G.n, it, of);
+#pragma unroll
+      for (int j = 0; j < kDecodeIlp; ++j) { item[r * kDecodeIlp + j] = it[j]; off[r * kDecodeIlp + j] = of[j]; }
+    }
+#pragma unroll
+    for (int i = 0; i < kIpt; ++i) {                // rank = R_1[ruler] - offset
+      if (item[i].x == kLogEnd) continue;
+      const uint32_t c = item[i].y;
+      uint32_t val = 0;
+      if (c < nn) val = __ldcg(r1 + c) - off[i];
+      else bad |= kErrInternal;
+      item[i].y = val;
+      bk[i] = bucket_a(item[i].x, G);
+    }
+    part_emit_tile(S, G.na, item, bk, out, G.n, bad);
   }
   part_flush(S, G.na, out, G.n);
   if (bad) record_error(err, bad);
@@ -517,19 +586,16 @@ k_lb_write(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, con
   lb_range(G, p0, p1);
   uint32_t bad = 0;
   for (uint32_t t0 = p0; t0 < p1; t0 += kPartTile) {
-    const uint32_t t1 = min(p1, t0 + kPartTile);
-    for (uint32_t p = t0 + threadIdx.x; p < t1; p += blockDim.x) {
-      const uint2 v = __ldcs(in + p);
-      if (v.x < G.n) {
-        const uint32_t k = atomicAdd(&S.nt, 1u);
-        S.tmp[k] = v;
-        S.tb[k] = (uint16_t)bucket_b(v.x, G);
-      } else {
-        bad |= kErrInternal;
-      }
+    uint2 item[kIpt];
+    uint32_t bk[kIpt];
+#pragma unroll
+    for (int i = 0; i < kIpt; ++i) {
+      const uint32_t p = t0 + (uint32_t)i * blockDim.x + threadIdx.x;
+      item[i] = p < p1 ? __ldcs(in + p) : make_uint2(kLogEnd, 0u);
+      if (item[i].x != kLogEnd && item[i].x >= G.n) { bad |= kErrInternal; item[i].x = kLogEnd; }
+      bk[i] = item[i].x != kLogEnd ? bucket_b(item[i].x, G) : 0u;
     }
-    __syncthreads();
-    part_emit_tile(S, nbk, out, G.n, bad);
+    part_emit_tile(S, nbk, item, bk, out, G.n, bad);
   }
   part_flush(S, nbk, out, G.n);
   if (bad) record_error(err, bad);
