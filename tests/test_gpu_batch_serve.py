@@ -1,0 +1,130 @@
+"""Batched form in a CUDA graph, and the serving loop (GPU).
+
+The batch of k instances is one launch sequence over the forest they form;
+with the list bound given (max_lists) and a caller workspace it neither
+synchronises nor allocates, so it is captured in a CUDA graph and replayed
+on new data.  The server must return, for every request, exactly what the
+same request returns when ranked alone.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2606_09318_gb300 as lr  # noqa: E402
+
+
+def dev(a):
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).cuda()
+
+
+def test_batch_in_cuda_graph():
+    k = 96
+    offsets, succ, w = gen.batch_instances(k, 11, lo_exp=4.0, hi_exp=16.0)
+    n = int(offsets[-1])
+    want = oracle.rank_batch(offsets, succ, w, np.int64)
+    d_off, d_succ, d_w = dev(offsets), dev(succ), dev(w)
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    ws = torch.empty(lr.workspace_size(n, k, weighted=True, max_lists=k), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    kw = dict(out=out, max_lists=k, n_total=n, sync=False, stream=s, workspace=ws)
+    with torch.cuda.stream(s):
+        lr.rank_batch(d_off, d_succ, d_w, **kw)            # warm-up outside capture
+    s.synchronize()
+    assert lr.device_status(s) == 0
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    g = torch.cuda.CUDAGraph()
+    out.fill_(0)
+    with torch.cuda.graph(g, stream=s):
+        lr.rank_batch(d_off, d_succ, d_w, **kw)
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    # new data of the same shapes, same graph
+    offsets2 = offsets.copy()
+    succ2 = np.concatenate([gen.random_list(int(offsets[j + 1] - offsets[j]), 900 + j) for j in range(k)])
+    w2 = gen.weights_i64(n, 901)
+    d_succ.copy_(dev(succ2.astype(np.uint32)))
+    d_w.copy_(dev(w2))
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.rank_batch(offsets2, succ2.astype(np.uint32), w2, np.int64))
+
+
+def test_batch_equals_per_instance_loop():
+    k = 40
+    offsets, succ, w = gen.batch_instances(k, 12, lo_exp=2.0, hi_exp=17.0)
+    got = lr.rank_batch(dev(offsets), dev(succ), dev(w), max_lists=k).cpu().numpy()
+    for j in range(k):
+        a, b = int(offsets[j]), int(offsets[j + 1])
+        one = lr.rank(dev(succ[a:b]), dev(w[a:b])).cpu().numpy()
+        np.testing.assert_array_equal(got[a:b], one)
+
+
+def _requests(num, seed):
+    g = np.random.default_rng(seed)
+    reqs = []
+    for i in range(num):
+        m = int(2 ** g.uniform(4, 17))
+        kind = "random" if i % 2 == 0 else "locality"
+        succ = gen.list_of_order_kind(kind, m, seed * 100 + i)
+        w = gen.weights_i64(m, seed * 100 + i + 7)
+        reqs.append((succ, w))
+    return reqs
+
+
+@pytest.mark.parametrize("n_streams,plain", [(2, False), (3, False), (1, True)])
+def test_server_alone_equals_in_mix(n_streams, plain):
+    reqs = _requests(40, 5)
+    srv = lr.Server(budget_bytes=2_000_000_000, n_streams=n_streams, max_batch=16, plain=plain)
+    tickets = []
+    for i, (succ, w) in enumerate(reqs):
+        if i % 3 == 0:   # device-resident request, ranked in place
+            tickets.append(srv.submit(dev(succ), dev(w)))
+        else:            # host request, copied by the server
+            tickets.append(srv.submit(torch.from_numpy(succ.view(np.int32)), torch.from_numpy(w)))
+    for (succ, w), t in zip(reqs, tickets):
+        out, info = srv.wait(t)
+        alone = lr.rank(dev(succ), dev(w)).cpu().numpy()
+        np.testing.assert_array_equal(out.cpu().numpy(), alone)
+        np.testing.assert_array_equal(alone, oracle.rank(succ, w, np.int64))
+        assert info["t_submit_ms"] <= info["t_admit_ms"] <= info["t_launch_ms"] <= info["t_done_ms"]
+    st = srv.stats()
+    assert st["completed"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
+    if not plain:
+        assert st["batches"] <= len(reqs)
+    srv.close()
+
+
+def test_server_budget_and_errors():
+    srv = lr.Server(budget_bytes=50_000_000, n_streams=2)
+    big = torch.zeros(10_000_000, dtype=torch.int32)
+    with pytest.raises(lr.LRError) as e:
+        srv.submit(big)
+    assert e.value.name == "LR_ERR_BUDGET"
+    # an invalid request fails alone; its neighbours in the batch still succeed
+    good = gen.random_list(5000, 1)
+    bad = good.copy()
+    bad[3] = 5000
+    t1 = srv.submit(torch.from_numpy(good.view(np.int32)))
+    t2 = srv.submit(torch.from_numpy(bad.view(np.int32)))
+    t3 = srv.submit(torch.from_numpy(good.view(np.int32)))
+    out1, _ = srv.wait(t1)
+    with pytest.raises(lr.LRError) as e2:
+        srv.wait(t2)
+    assert e2.value.name == "LR_ERR_OUT_OF_RANGE"
+    out3, _ = srv.wait(t3)
+    np.testing.assert_array_equal(out1.numpy(), oracle.rank(good))
+    np.testing.assert_array_equal(out3.numpy(), oracle.rank(good))
+    with pytest.raises(lr.LRError):
+        srv.wait(123456)
+    srv.close()
