@@ -276,6 +276,14 @@ def run_ours(args):
         e2e = {"value": ws * n * e2e_steps / t / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n}
 
+    # the chase is a dependent random walk: measure the GPU's random-access
+    # ceiling on a buffer far larger than L2 (same memory, same run)
+    probe = None
+    if not args.no_probe:
+        buf = torch.empty(2 << 30, dtype=torch.uint8, device=dev)
+        probe = lr.probe_memory(buf, stream)
+        del buf
+
     hbm, src = measured_peaks()
     chase_ms = prof["ms_chase0"] / max(1, prof["chase0_launches"])
     achieved = BYTES_PER_ELEM_CHASE * n / (chase_ms * 1e-3) / 1e9
@@ -294,7 +302,13 @@ def run_ours(args):
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_source": src,
                      "traffic": ncu_traffic(n), "algorithmic_bytes": BYTES_PER_ELEM_CHASE * n,
-                     "ms_per_launch": round(chase_ms, 4)},
+                     "ms_per_launch": round(chase_ms, 4),
+                     "random_access_ceiling": None if probe is None else {
+                         "gather_g_per_s": round(probe["gather_gsteps"], 2),
+                         "gather_exchange_g_per_s": round(probe["gather_xchg_gsteps"], 2),
+                         "copy_gbs": round(probe["copy_gbs"], 1),
+                         "chase_frac_of_exchange_ceiling": round(
+                             n / (chase_ms * 1e-3) / 1e9 / probe["gather_xchg_gsteps"], 4)}},
         "pipeline": {"random_sector_roofline_gelem_s": round(sector_roof, 2),
                      "frac": round(value / ws / sector_roof, 4),
                      "phases_ms_per_step": {k[3:]: round(prof[k] / steps_prof, 4) for k in
@@ -346,6 +360,179 @@ def run_reference(args):
     }), flush=True)
 
 
+def _device_random_order(m, g, dev):
+    import torch
+    return torch.randperm(m, device=dev, generator=g, dtype=torch.int64)
+
+
+def _device_locality_order(m, g, dev, window=256):
+    import torch
+    full = (m // window) * window
+    order = torch.arange(m, device=dev, dtype=torch.int64)
+    if full:
+        keys = torch.rand(full // window, window, device=dev, generator=g)
+        idx = torch.argsort(keys, dim=1) + torch.arange(0, full, window, device=dev).unsqueeze(1)
+        order[:full] = idx.reshape(-1)
+    if full < m:
+        order[full:] = full + torch.randperm(m - full, device=dev, generator=g)
+    return order
+
+
+def _fill_succ(succ_view, order):
+    """succ_view[order[i]] = order[i+1] (local ids), tail points to itself."""
+    succ_view[order[:-1]] = order[1:].to(succ_view.dtype)
+    succ_view[order[-1]] = order[-1].to(succ_view.dtype)
+
+
+def run_batch(args):
+    """1024 independent random-order instances, sizes floor(2^U), U ~ U[8,22],
+    int64 weights in [0, 2^20): one CUDA-graph replay of the batched call per
+    step, against a host loop of one lr_rank_ex call per instance."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2606_09318_gb300 as lr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    k = 1024
+    lens = gen.batch_lengths(k, gen.config_seed(4), 8.0, 22.0)
+    offsets = np.zeros(k + 1, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    n = int(offsets[-1])
+    g = torch.Generator(device=dev)
+    g.manual_seed(4000)
+    succ = torch.empty(n, dtype=torch.int32, device=dev)
+    for j in range(k):
+        a, b = int(offsets[j]), int(offsets[j + 1])
+        _fill_succ(succ[a:b], _device_random_order(b - a, g, dev))
+    w = torch.randint(0, 1 << 20, (n,), dtype=torch.int64, device=dev, generator=g)
+    d_off = torch.from_numpy(offsets).to(dev)
+    out_b = torch.empty(n, dtype=torch.int64, device=dev)
+    out_l = torch.empty(n, dtype=torch.int64, device=dev)
+    ws = torch.empty(lr.workspace_size(n, k, weighted=True, max_lists=k), dtype=torch.uint8, device=dev)
+    s = torch.cuda.Stream()
+    kw = dict(out=out_b, max_lists=k, n_total=n, sync=False, stream=s, workspace=ws)
+    with torch.cuda.stream(s):
+        lr.rank_batch(d_off, succ, w, **kw)
+    s.synchronize()
+    assert lr.device_status(s) == 0
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        lr.rank_batch(d_off, succ, w, **kw)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(steps):
+            fn()
+        e1.record(s)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    with torch.cuda.stream(s):
+        ms_b = timed(graph.replay, args.steps, args.warmup)
+        views = [(int(offsets[j]), int(offsets[j + 1])) for j in range(k)]
+
+        def loop():
+            for a, b in views:
+                lr.rank_ex(succ[a:b], w[a:b], out=out_l[a:b], max_lists=1, sync=False, stream=s)
+        launches0 = lr.kernel_launch_count()
+        ms_l = timed(loop, max(1, args.steps // 2), 1)
+        per_loop_launches = (lr.kernel_launch_count() - launches0) / (max(1, args.steps // 2) + 1)
+    assert lr.device_status(s) == 0
+    if not torch.equal(out_b, out_l):
+        raise RuntimeError("batched and per-instance results differ")
+    print(json.dumps({
+        "workload": "batch", "metric": "G list elements ranked/s, 1024 instances in one CUDA graph",
+        "value": round(n / (ms_b * 1e-3) / 1e9, 4), "unit": UNIT, "ms_per_step": round(ms_b, 3),
+        "n_total": n, "k": k, "dtype": "i64 weights, i64 ranks",
+        "per_instance_loop": {"value": round(n / (ms_l * 1e-3) / 1e9, 4), "ms_per_step": round(ms_l, 3),
+                              "kernel_launches_per_step": per_loop_launches},
+        "speedup_vs_loop": round(ms_l / ms_b, 3),
+        "config": {"workload": "batched: 1024 random-order instances, sizes floor(2^U), U~U[8,22], "
+                               "int64 weights in [0,2^20), graph-captured"},
+    }), flush=True)
+
+
+def run_serve(args):
+    """Poisson request stream, sizes floor(2^U) with U ~ U[10,26], random or
+    locality order with p = 0.5, int64 weights, 40 GB budget: continuous
+    batching against plain per-request launches on the same trace."""
+    import threading as th
+    import numpy as np
+    import torch
+    import gen
+    import paper_2606_09318_gb300 as lr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5000)
+    pool_n = 40
+    arrivals, sizes, kinds, _ = gen.serving_trace(args.requests + args.serve_warmup, gen.config_seed(5),
+                                                 rate_per_s=1.0)
+    pool = []
+    for i in range(pool_n):
+        m = int(sizes[i])
+        order = _device_random_order(m, g, dev) if kinds[i] == "random" else _device_locality_order(m, g, dev)
+        sc = torch.empty(m, dtype=torch.int32, device=dev)
+        _fill_succ(sc, order)
+        pool.append((sc, torch.randint(0, 1 << 20, (m,), dtype=torch.int64, device=dev, generator=g)))
+    mean_n = float(np.mean([p[0].numel() for p in pool]))
+    results = {}
+    for mode in ("batched", "plain"):
+        srv = lr.Server(budget_bytes=40_000_000_000, n_streams=args.serve_streams, max_batch=256,
+                        plain=(mode == "plain"))
+        total = args.requests + args.serve_warmup
+        # offered load: args.load x a capacity guess in elements/s
+        rate = args.load * args.serve_capacity / mean_n
+        gaps = np.random.default_rng(55).exponential(1.0 / rate, size=total)
+        outs = [torch.empty(p[0].numel(), dtype=torch.int64, device=dev) for p in pool]
+        tickets = [None] * total
+        t_start = time.perf_counter()
+
+        def submitter():
+            t = t_start
+            for i in range(total):
+                t += gaps[i]
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                sc, wv = pool[i % pool_n]
+                tickets[i] = srv.submit(sc, wv, out=outs[i % pool_n])
+        thr = th.Thread(target=submitter)
+        thr.start()
+        lat, elems, t_first, t_last = [], 0, None, None
+        for i in range(total):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            _, info = srv.wait(tickets[i])
+            if i >= args.serve_warmup:
+                lat.append(info["t_done_ms"] - info["t_submit_ms"])
+                elems += pool[i % pool_n][0].numel()
+                t_first = info["t_submit_ms"] if t_first is None else min(t_first, info["t_submit_ms"])
+                t_last = info["t_done_ms"] if t_last is None else max(t_last, info["t_done_ms"])
+        thr.join()
+        st = srv.stats()
+        srv.close()
+        lat = np.array(lat)
+        results[mode] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                         "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                         "elements_per_s": round(elems / ((t_last - t_first) * 1e-3), 1),
+                         "batches": int(st["batches"]), "requests": int(args.requests)}
+    print(json.dumps({
+        "workload": "serve", "metric": "served G list elements/s and p50/p99 latency",
+        "value": round(results["batched"]["elements_per_s"] / 1e9, 4), "unit": UNIT,
+        "batched": results["batched"], "plain": results["plain"],
+        "offered_load": args.load, "capacity_guess_elem_s": args.serve_capacity, "mean_request": mean_n,
+        "config": {"workload": "serving: Poisson arrivals, sizes floor(2^U) U~U[10,26], random/locality "
+                               "orders p=0.5, int64 weights, 40 GB budget, device-resident inputs "
+                               "(a pool of %d generated requests reused round-robin)" % pool_n},
+    }), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -355,11 +542,23 @@ def main():
     ap.add_argument("--n", type=int, default=1 << 28)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-probe", action="store_true", help="skip the random-access probe")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+                    help="single: the headline (default); batch / serve: the batched and serving sets")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: measured requests")
+    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-streams", type=int, default=2)
+    ap.add_argument("--load", type=float, default=0.8, help="serve: offered load / capacity guess")
+    ap.add_argument("--serve-capacity", type=float, default=12e9, help="serve: capacity guess, elements/s")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

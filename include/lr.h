@@ -199,6 +199,25 @@ typedef struct lr_profile {
 lr_status lr_profile_enable(int32_t on);
 lr_status lr_profile_read(lr_profile *out, int32_t reset);
 
+/*
+ * Memory-system probe (measurement only; the paper has no counterpart).
+ * The chase of Algorithm 1 is a dependent random walk, so its ceiling on a
+ * GPU is the rate of random 32-byte accesses that miss L2, not the streaming
+ * bandwidth.  On the caller's device buffer (>= 64 MiB, 256-byte aligned,
+ * far larger than L2 for a meaningful number; its contents are destroyed)
+ * this measures a streaming copy, a dependent random 8-byte gather and a
+ * dependent random 8-byte atomic exchange, each over one seeded random
+ * cycle through the buffer.  Waits for the device.
+ */
+typedef struct lr_probe_result {
+    double copy_gbs;            /* streaming read + write, GB/s                  */
+    double gather_gsteps;       /* dependent random loads, G steps/s             */
+    double gather_xchg_gsteps;  /* dependent random exchanges, G steps/s         */
+    size_t footprint_bytes;     /* bytes the random walks covered                */
+} lr_probe_result;
+
+lr_status lr_probe_memory(void *buf, size_t bytes, lr_probe_result *out, lr_stream stream);
+
 /* Kernels launched by the library since load (all streams). Host-only. */
 int64_t lr_kernel_launch_count(void);
 

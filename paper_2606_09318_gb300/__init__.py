@@ -17,7 +17,7 @@ import threading
 __all__ = [
     "LRError", "Tuning", "load", "lib_path", "rank", "rank_ex", "rank_batch", "rank_host",
     "device_status", "workspace_size", "status_string", "version", "profile_enable",
-    "profile_read", "kernel_launch_count", "Server", "STATUS",
+    "profile_read", "kernel_launch_count", "probe_memory", "Server", "STATUS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -84,6 +84,11 @@ class _ServerStats(ctypes.Structure):
                 ("elements_per_s", ctypes.c_double), ("peak_resident_bytes", ctypes.c_size_t)]
 
 
+class _ProbeResult(ctypes.Structure):
+    _fields_ = [("copy_gbs", ctypes.c_double), ("gather_gsteps", ctypes.c_double),
+                ("gather_xchg_gsteps", ctypes.c_double), ("footprint_bytes", ctypes.c_size_t)]
+
+
 _lock = threading.Lock()
 _lib = None
 _V, _I32, _I64, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
@@ -101,6 +106,7 @@ _SIGS = {
     "lr_profile_enable": (ctypes.c_int, [_I32]),
     "lr_profile_read": (ctypes.c_int, [ctypes.POINTER(_Profile), _I32]),
     "lr_kernel_launch_count": (_I64, []),
+    "lr_probe_memory": (ctypes.c_int, [_V, _SZ, ctypes.POINTER(_ProbeResult), _V]),
     "lr_server_config_default": (None, [ctypes.POINTER(_ServerConfig)]),
     "lr_server_create": (ctypes.c_int, [ctypes.POINTER(_ServerConfig), ctypes.POINTER(_V)]),
     "lr_server_submit": (ctypes.c_int, [_V, ctypes.POINTER(_Request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -321,6 +327,15 @@ def profile_read(reset=True):
 
 def kernel_launch_count():
     return int(load().lr_kernel_launch_count())
+
+
+def probe_memory(buf, stream=None):
+    """Random-access and streaming ceilings measured on a CUDA byte buffer
+    (contents destroyed); see lr_probe_memory in include/lr.h."""
+    r = _ProbeResult()
+    _check(load().lr_probe_memory(ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
+                                  ctypes.byref(r), _stream_handle(stream)), "lr_probe_memory")
+    return {f: getattr(r, f) for f, _ in _ProbeResult._fields_}
 
 
 class Server:
