@@ -533,6 +533,106 @@ def run_serve(args):
     }), flush=True)
 
 
+def _device_identity_order(m, dev):
+    import torch
+    return torch.arange(m, device=dev, dtype=torch.int64)
+
+
+def _time_call(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _check_recurrence(succ, w, rank, dev):
+    """Exactness at sizes the oracle cannot reach in seconds: tail 0 and
+    rank[i] = w[i] + rank[succ[i]] on every element (wrapping as int64)."""
+    import torch
+    n = succ.numel()
+    sl = succ.to(torch.int64) & 0xFFFFFFFF
+    idx = torch.arange(n, device=dev)
+    term = sl == idx
+    r = rank.to(torch.int64)
+    ww = torch.ones(n, dtype=torch.int64, device=dev) if w is None else w.to(torch.int64)
+    tail_ok = bool((r[term] == 0).all())
+    diff = r[~term] - ww[~term] - r[sl[~term]]
+    if rank.dtype == torch.int32:               # int32 ranks wrap modulo 2^32
+        diff = diff % (1 << 32)
+    return tail_ok and bool((diff == 0).all())
+
+
+def run_sweep(args):
+    """Configurations beyond the headline, one JSON line per case: the size
+    sweep 2^24..2^30 in three orders, unweighted and with int32 weights in
+    [-1000, 1000] (int64 ranks); the forest of 2^27 elements; the Euler tour
+    of a random recursive tree with 2^26 vertices (+-1 int32 weights, int32
+    ranks).  Every output is checked with the rank recurrence."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2606_09318_gb300 as lr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(2024)
+    sizes = [int(x) for x in args.sweep_sizes.split(",")]
+    cases = []
+    for lg in sizes:
+        for kind in ("random", "locality", "identity"):
+            for weighted in (False, True):
+                cases.append((lg, kind, weighted))
+    for lg, kind, weighted in cases:
+        n = 1 << lg
+        order = {"random": lambda: _device_random_order(n, g, dev),
+                 "locality": lambda: _device_locality_order(n, g, dev),
+                 "identity": lambda: _device_identity_order(n, dev)}[kind]()
+        succ = torch.empty(n, dtype=torch.int32, device=dev)
+        _fill_succ(succ, order)
+        del order
+        w = torch.randint(-1000, 1001, (n,), dtype=torch.int32, device=dev, generator=g) if weighted else None
+        out = torch.empty(n, dtype=torch.int64 if weighted else torch.int32, device=dev)
+        ms = _time_call(lambda: lr.rank_ex(succ, w, out=out, sync=False), args.steps, args.warmup)
+        assert lr.device_status() == 0
+        ok = _check_recurrence(succ, w, out, dev)
+        print(json.dumps({"workload": "sweep", "n": n, "log2n": lg, "order": kind,
+                          "weights": "int32 [-1000,1000] -> int64 ranks" if weighted else "none -> int32 ranks",
+                          "ms": round(ms, 3), "g_elem_s": round(n / (ms * 1e-3) / 1e9, 3),
+                          "exact": ok}), flush=True)
+        del succ, w, out
+        torch.cuda.empty_cache()
+    # forest: 16 lists of 2^22 plus geometric(mean 64) lists, labels permuted (host generator)
+    fs, nl = gen.forest(1 << 27, gen.config_seed(3), n_long=16, long_len=1 << 22, mean_short=64)
+    succ = torch.from_numpy(fs.view(np.int32)).to(dev)
+    out = torch.empty(succ.numel(), dtype=torch.int32, device=dev)
+    ms = _time_call(lambda: lr.rank_ex(succ, out=out, sync=False), args.steps, args.warmup)
+    assert lr.device_status() == 0
+    print(json.dumps({"workload": "sweep", "case": "forest 2^27 (16 x 2^22 + geometric mean 64)",
+                      "n": int(succ.numel()), "lists": nl, "ms": round(ms, 3),
+                      "g_elem_s": round(succ.numel() / (ms * 1e-3) / 1e9, 3),
+                      "exact": _check_recurrence(succ, None, out, dev)}), flush=True)
+    del succ, out
+    parent = gen.random_recursive_tree(1 << 26, gen.config_seed(3, 1))
+    es, ew = gen.euler_tour(parent)
+    del parent
+    succ = torch.from_numpy(es.view(np.int32)).to(dev)
+    w = torch.from_numpy(ew).to(dev)
+    out = torch.empty(succ.numel(), dtype=torch.int32, device=dev)
+    ms = _time_call(lambda: lr.rank_ex(succ, w, out=out, sync=False), args.steps, args.warmup)
+    assert lr.device_status() == 0
+    print(json.dumps({"workload": "sweep", "case": "Euler tour of a random recursive tree, 2^26 vertices",
+                      "n": int(succ.numel()), "ms": round(ms, 3),
+                      "g_elem_s": round(succ.numel() / (ms * 1e-3) / 1e9, 3),
+                      "exact": _check_recurrence(succ, w, out, dev)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,9 +643,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access probe")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "sweep"],
                     help="single: the headline (default); batch / serve: the batched and serving sets")
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured requests")
+    ap.add_argument("--sweep-sizes", default="24,26,28,30", help="sweep: log2 sizes")
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-streams", type=int, default=2)
     ap.add_argument("--load", type=float, default=0.8, help="serve: offered load / capacity guess")
@@ -559,6 +660,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -173,10 +173,18 @@ __device__ __forceinline__ Rec8 xchg_rec(Rec8 *p, uint32_t cid, uint64_t off) {
   const unsigned long long ov = atomicExch(reinterpret_cast<unsigned long long *>(p), nv);
   return Rec8{(uint32_t)ov, (uint32_t)(ov >> 32)};
 }
+// 16-byte records: one 128-bit atomic exchange at L2 (sm_90 and later).
 __device__ __forceinline__ Rec16 xchg_rec(Rec16 *p, uint32_t cid, uint64_t off) {
-  Rec16 v = ld_rec(p);           // 16-byte records: dependent load/store
-  if (v.tag == kUnvisited) st_rec(p, cid, off);
-  return v;
+  const unsigned long long nlo = (unsigned long long)cid << 32, nhi = off;
+  unsigned long long olo, ohi;
+  asm volatile("{\n\t.reg .b128 d, b;\n\tmov.b128 b, {%2, %3};\n\t"
+               "atom.global.exch.b128 d, [%4], b;\n\tmov.b128 {%0, %1}, d;\n\t}"
+               : "=l"(olo), "=l"(ohi) : "l"(nlo), "l"(nhi), "l"(p) : "memory");
+  Rec16 r;
+  r.succ = (uint32_t)olo;
+  r.tag = (uint32_t)(olo >> 32);
+  r.w = ohi;
+  return r;
 }
 
 // The raw successor array read as a record (level 0 of the log path): no tag,

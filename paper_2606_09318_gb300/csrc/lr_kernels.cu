@@ -539,7 +539,9 @@ cudaError_t launch_chase(LevelDesc *desc, int lev, void *work, bool rec16, void 
                          const uint32_t *ns, uint32_t *qctr, int grid, int block, uint32_t *err,
                          int xchg, cudaStream_t s) {
   Rec16 *nx = reinterpret_cast<Rec16 *>(next_work);
-  if (rec16)
+  if (rec16 && xchg)
+    k_chase<Rec16, true><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<Rec16 *>(work), nx, ns, qctr, err);
+  else if (rec16)
     k_chase<Rec16, false><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<Rec16 *>(work), nx, ns, qctr, err);
   else if (xchg)
     k_chase<Rec8, true><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<Rec8 *>(work), nx, ns, qctr, err);
