@@ -133,6 +133,22 @@ lr_status lr_rank_host(const uint32_t *succ_host, const void *weight_host, int64
                        void *rank_host, const lr_opts *opts, lr_stream stream);
 
 /*
+ * Same, without waiting: copy-in, ranking and copy-out are enqueued on
+ * `stream` (through device staging buffers owned by the stream's context) and
+ * the call returns.  rank_host is valid once the stream has been synchronised;
+ * lr_get_device_status(stream) then returns the status.  Host buffers should
+ * be pinned for the copies to be asynchronous; the caller keeps them alive and
+ * untouched until then.  Calls on two or more streams overlap one call's
+ * copies with another call's kernels, but the streams' kernels then share
+ * the GPU and finish together; lr_pipeline below keeps the ranking of a
+ * sequence of host lists back to back.  With opts->max_lists == 0 the call
+ * still waits once to count the lists; pass a bound to keep it fully
+ * asynchronous.
+ */
+lr_status lr_rank_host_async(const uint32_t *succ_host, const void *weight_host, int64_t n,
+                             void *rank_host, const lr_opts *opts, lr_stream stream);
+
+/*
  * Bytes of workspace a call with these sizes needs when the caller passes
  * lr_opts.workspace.  k = 0 for lr_rank_ex.  Uses opts->max_lists as the
  * bound on the number of lists (0: assumes every element may be a head).
@@ -270,6 +286,52 @@ lr_status lr_server_submit(lr_server *s, const lr_request *req, uint64_t *ticket
 lr_status lr_server_wait(lr_server *s, uint64_t ticket, int64_t timeout_ms, lr_result *res);
 lr_status lr_server_stats_get(lr_server *s, lr_server_stats *out);
 void lr_server_destroy(lr_server *s);
+
+/*
+ * Host-buffer pipeline: ranks a sequence of HOST-resident lists (Section 1.1
+ * problem, one list or forest per submission) with each list's copies
+ * overlapping the ranking of its neighbours.  A pipeline owns three CUDA
+ * streams on the current device (copy-in, ranking, copy-out), `depth` device
+ * slots of max_n elements (successors, weights, ranks) and one engine
+ * workspace, all allocated by lr_pipeline_create.  Submission j uses slot
+ * j % depth; its copy-in waits
+ * until the ranking of submission j - depth has read the slot, its ranking
+ * waits for its copy-in and for the copy-out of submission j - depth, and
+ * rankings run one after another in submission order.
+ *
+ * opts (copied at create; NULL = defaults) fixes wtype, rtype, tuning,
+ * validate, seed and max_lists for every submission; opts->workspace must be
+ * NULL.  With max_lists > 0 (a bound on the lists of every submission; a
+ * submission with more fails with LR_ERR_CAPACITY) the engine workspace is
+ * allocated at create and submissions neither allocate nor wait.  With
+ * max_lists == 0 each submission first counts its lists, so the submitting
+ * thread waits for the ranking stream to reach it (the copies of the next
+ * submission still overlap this ranking), and the engine grows its own
+ * buffers to the count.  depth: 2..4 (0 selects 2).  Device memory:
+ * depth * max_n * (4 + weight bytes + rank bytes), plus
+ * lr_workspace_size(max_n, 0, opts) when max_lists > 0.
+ *
+ * Host buffers should be pinned (cudaHostAlloc / cudaHostRegister); pageable
+ * buffers work but their copies block the submitting thread.  The caller
+ * keeps every submitted buffer alive and unmodified, and reads no rank
+ * buffer, until lr_pipeline_wait returns.  One pipeline is used by one host
+ * thread at a time; distinct pipelines are independent.
+ */
+typedef struct lr_pipeline lr_pipeline;
+
+lr_status lr_pipeline_create(int64_t max_n, const lr_opts *opts, int32_t depth, lr_pipeline **out);
+/* Enqueue one list; 0 <= n <= max_n; weight_host non-NULL exactly when
+ * opts->wtype != LR_NONE.  Returns argument errors at once; errors the
+ * device finds are reported by lr_pipeline_wait. */
+lr_status lr_pipeline_submit(lr_pipeline *p, const uint32_t *succ_host, const void *weight_host,
+                             int64_t n, void *rank_host);
+/* Wait for every submission since the previous wait.  Returns LR_OK, or the
+ * status of the first submission that failed, with its 0-based index since
+ * the previous wait in *failed_index (-1 when none; may be NULL).  Rank
+ * buffers of the other submissions are valid. */
+lr_status lr_pipeline_wait(lr_pipeline *p, int64_t *failed_index);
+/* Wait, then release the streams, events and device memory. */
+void lr_pipeline_destroy(lr_pipeline *p);
 
 #ifdef __cplusplus
 }

@@ -99,6 +99,7 @@ _SIGS = {
     "lr_rank_batch": (ctypes.c_int, [_V, _V, _V, _V, _I32, _V]),
     "lr_rank_batch_ex": (ctypes.c_int, [_V, _V, _V, _V, _I32, ctypes.POINTER(_Opts), _V]),
     "lr_rank_host": (ctypes.c_int, [_V, _V, _I64, _V, ctypes.POINTER(_Opts), _V]),
+    "lr_rank_host_async": (ctypes.c_int, [_V, _V, _I64, _V, ctypes.POINTER(_Opts), _V]),
     "lr_workspace_size": (_SZ, [_I64, _I32, ctypes.POINTER(_Opts)]),
     "lr_get_device_status": (ctypes.c_int, [_V]),
     "lr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -113,6 +114,10 @@ _SIGS = {
     "lr_server_wait": (ctypes.c_int, [_V, ctypes.c_uint64, _I64, ctypes.POINTER(_Result)]),
     "lr_server_stats_get": (ctypes.c_int, [_V, ctypes.POINTER(_ServerStats)]),
     "lr_server_destroy": (None, [_V]),
+    "lr_pipeline_create": (ctypes.c_int, [_I64, ctypes.POINTER(_Opts), _I32, ctypes.POINTER(_V)]),
+    "lr_pipeline_submit": (ctypes.c_int, [_V, _V, _V, _I64, _V]),
+    "lr_pipeline_wait": (ctypes.c_int, [_V, ctypes.POINTER(_I64)]),
+    "lr_pipeline_destroy": (None, [_V]),
 }
 
 
@@ -267,8 +272,12 @@ def rank_batch(offsets, succ, weight=None, out=None, rank_dtype=None, validate=F
 
 
 def rank_host(succ, weight=None, out=None, rank_dtype=None, validate=False, seed=0x5EED,
-              max_lists=0, stream=None):
-    """End-to-end form on host tensors / numpy arrays: copy in, rank, copy out."""
+              max_lists=0, stream=None, wait=True):
+    """End-to-end form on host tensors / numpy arrays: copy in, rank, copy out.
+
+    wait=False enqueues everything on `stream` and returns at once (the
+    lr_rank_host_async entry point); `out` is valid after the stream is
+    synchronised, and device_status(stream) gives the status."""
     import numpy as np
     torch = _torch()
     lib = load()
@@ -292,8 +301,9 @@ def rank_host(succ, weight=None, out=None, rank_dtype=None, validate=False, seed
         out = np.empty(n, dtype=rdt)
     rp = host_ptr(out)[0]
     o = _opts(wt, LR_I32 if out.dtype in (np.int32, torch.int32) else LR_I64, validate, seed, max_lists)
-    code = lib.lr_rank_host(sp, wp, n, rp, ctypes.byref(o), _stream_handle(stream))
-    _check(code, "lr_rank_host")
+    fn = lib.lr_rank_host if wait else lib.lr_rank_host_async
+    code = fn(sp, wp, n, rp, ctypes.byref(o), _stream_handle(stream))
+    _check(code, "lr_rank_host" if wait else "lr_rank_host_async")
     return out
 
 
@@ -336,6 +346,76 @@ def probe_memory(buf, stream=None):
     _check(load().lr_probe_memory(ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
                                   ctypes.byref(r), _stream_handle(stream)), "lr_probe_memory")
     return {f: getattr(r, f) for f, _ in _ProbeResult._fields_}
+
+
+class Pipeline:
+    """Host-buffer pipeline (lr_pipeline_* of the C ABI): submissions of
+    host-resident lists whose copies overlap the neighbouring rankings.
+
+    Submitted arrays (and outputs) are kept referenced until wait(); pass
+    pinned tensors for the copies to overlap."""
+
+    def __init__(self, max_n, wtype=None, rank_dtype=None, depth=2, max_lists=0,
+                 validate=False, seed=0x5EED, tuning=None):
+        import numpy as np
+        torch = _torch()
+        self._wt = {None: LR_NONE, "int32": LR_I32, "int64": LR_I64, np.int32: LR_I32,
+                    np.int64: LR_I64, torch.int32: LR_I32, torch.int64: LR_I64}[wtype]
+        rdt = rank_dtype or (torch.int32 if self._wt == LR_NONE else torch.int64)
+        self._rdt = {torch.int32: torch.int32, np.int32: torch.int32, "int32": torch.int32,
+                     torch.int64: torch.int64, np.int64: torch.int64, "int64": torch.int64}[rdt]
+        o = _opts(self._wt, LR_I32 if self._rdt == torch.int32 else LR_I64, validate, seed,
+                  max_lists, tuning)
+        h = ctypes.c_void_p()
+        _check(load().lr_pipeline_create(int(max_n), ctypes.byref(o), int(depth), ctypes.byref(h)),
+               "lr_pipeline_create")
+        self._h = h
+        self._keep = []
+
+    def submit(self, succ, weight=None, out=None):
+        """Enqueue one host list; returns the output (valid after wait())."""
+        import numpy as np
+        torch = _torch()
+
+        def host(a):
+            if isinstance(a, torch.Tensor):
+                assert not a.is_cuda and a.is_contiguous()
+                return a
+            return torch.from_numpy(np.ascontiguousarray(a))
+
+        succ = host(succ)
+        weight = None if weight is None else host(weight)
+        n = succ.numel()
+        if out is None:
+            out = torch.empty(n, dtype=self._rdt)
+        out = host(out)
+        _check(load().lr_pipeline_submit(self._h, ctypes.c_void_p(succ.data_ptr()),
+                                         None if weight is None else ctypes.c_void_p(weight.data_ptr()),
+                                         n, ctypes.c_void_p(out.data_ptr())), "lr_pipeline_submit")
+        self._keep.append((succ, weight, out))
+        return out
+
+    def wait(self):
+        """Wait for every submission; raises LRError naming the first failed one."""
+        idx = ctypes.c_int64(-1)
+        code = load().lr_pipeline_wait(self._h, ctypes.byref(idx))
+        self._keep = []
+        if code != 0:
+            err = LRError(code, "lr_pipeline_wait (submission %d)" % idx.value)
+            err.index = idx.value
+            raise err
+
+    def close(self):
+        if self._h:
+            load().lr_pipeline_destroy(self._h)
+            self._h = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

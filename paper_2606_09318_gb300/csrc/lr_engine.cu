@@ -224,6 +224,25 @@ Ctx *get_ctx(cudaStream_t stream, lr_status *st) {
   return c;
 }
 
+void release_ctx(cudaStream_t stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  Ctx *c = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_mu);
+    auto it = g_ctx.find(std::make_pair(dev, (uintptr_t)stream));
+    if (it == g_ctx.end()) return;
+    c = it->second;
+    g_ctx.erase(it);
+  }
+  cudaStreamSynchronize(stream);
+  if (c->fixed) cudaFree(c->fixed);
+  if (c->var) cudaFree(c->var);
+  if (c->hostpath) cudaFree(c->hostpath);
+  cudaFreeHost(c->host_words);
+  delete c;
+}
+
 static bool stream_capturing(cudaStream_t s) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
@@ -522,6 +541,8 @@ lr_status run_ptr_batch(const int64_t *offsets, int32_t k, int64_t n_total,
   return run(in, nullptr, s);
 }
 
+lr_status status_from_bits(uint32_t bits) { return map_device_bits(bits); }
+
 lr_status device_status(cudaStream_t s) {
   lr_status st;
   Ctx *c = get_ctx(s, &st);
@@ -666,8 +687,23 @@ lr_status lr_rank_batch(const int64_t *offsets, const uint32_t *succ, const void
   return lr_rank_batch_ex(offsets, succ, weight, rank, k, &o, stream);
 }
 
+// Enqueue copy-in, ranking and copy-out on `stream` through the stream's own
+// device staging buffers; `sync` waits and returns the final status.
+static lr_status rank_host_impl(const uint32_t *succ_host, const void *weight_host, int64_t n,
+                                void *rank_host, const lr_opts *opts, lr_stream stream, bool sync);
+
 lr_status lr_rank_host(const uint32_t *succ_host, const void *weight_host, int64_t n,
                        void *rank_host, const lr_opts *opts, lr_stream stream) {
+  return rank_host_impl(succ_host, weight_host, n, rank_host, opts, stream, true);
+}
+
+lr_status lr_rank_host_async(const uint32_t *succ_host, const void *weight_host, int64_t n,
+                             void *rank_host, const lr_opts *opts, lr_stream stream) {
+  return rank_host_impl(succ_host, weight_host, n, rank_host, opts, stream, false);
+}
+
+static lr_status rank_host_impl(const uint32_t *succ_host, const void *weight_host, int64_t n,
+                                void *rank_host, const lr_opts *opts, lr_stream stream, bool sync) {
   lr_opts d;
   if (!opts) { lr_opts_default(&d); if (weight_host) { d.wtype = LR_I64; d.rtype = LR_I64; } opts = &d; }
   if (n < 0 || n > LR_MAX_N) return LR_ERR_INVALID_ARGUMENT;
@@ -695,7 +731,7 @@ lr_status lr_rank_host(const uint32_t *succ_host, const void *weight_host, int64
   st = lr_rank_ex(dsucc, dw, n, drank, &o, stream);
   if (st != LR_OK) return st;
   LR_TRY(cudaMemcpyAsync(rank_host, drank, (size_t)rb * n, cudaMemcpyDeviceToHost, s));
-  return device_status(s);
+  return sync ? device_status(s) : LR_OK;
 }
 
 size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts) {

@@ -58,6 +58,11 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
                uint64_t seed, int chase_grid, bool force_srs, bool log0);
 int chase_grid_for(const Tuning &u, bool rec16, bool log0);
 Ctx *get_ctx(cudaStream_t stream, lr_status *st);
+// Forget the context of a stream that is about to be destroyed (waits for
+// the stream, frees the context's buffers).
+void release_ctx(cudaStream_t stream);
+// Status for the error bits a call leaves in Ctx::host_words[0].
+lr_status status_from_bits(uint32_t bits);
 lr_status ensure_buffer(void **buf, size_t *cur, size_t want, cudaStream_t s);
 lr_status device_status(cudaStream_t s);
 // Unweighted int32 ranking inside caller-provided scratch with a caller-provided

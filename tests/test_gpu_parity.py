@@ -192,3 +192,26 @@ def test_level0_paths(path, monkeypatch):
     succ, _ = gen.forest(1 << 20, 3, n_long=4, long_len=1 << 14, mean_short=64)
     check_equal(succ)
     check_equal(gen.random_list(300_000, 4), rank_dtype=np.int64)
+
+
+def test_host_async_two_streams():
+    """lr_rank_host_async: calls alternate between two streams; each result is exact."""
+    n = (1 << 20) + 3
+    succ = gen.random_list(n, 46)
+    want = oracle.rank(succ)
+    hs = torch.from_numpy(succ.view(np.int32)).pin_memory()
+    outs = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for i in range(4):
+        lr.rank_host(hs, out=outs[i % 2].numpy(), stream=streams[i % 2], wait=False, max_lists=1)
+    torch.cuda.synchronize()
+    for j in range(2):
+        assert lr.device_status(streams[j]) == 0
+        np.testing.assert_array_equal(outs[j].numpy(), want)
+    w = gen.weights_i32(n, 47)
+    hw = torch.from_numpy(w).pin_memory()
+    out64 = torch.empty(n, dtype=torch.int64).pin_memory()
+    lr.rank_host(hs, hw, out=out64.numpy(), stream=streams[0], wait=False)
+    torch.cuda.synchronize()
+    assert lr.device_status(streams[0]) == 0
+    np.testing.assert_array_equal(out64.numpy(), oracle.rank(succ, w, np.int64))
