@@ -144,9 +144,25 @@ class ClockSampler:
             except (ValueError, IndexError):
                 pass
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+            out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        else:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        out.update(self.memory_facts())
+        return out
+
+    def memory_facts(self):
+        """ECC mode and memory clock: the random-access rate differs between
+        boxes, and these are the settings that could explain it."""
+        try:
+            r = subprocess.run(["nvidia-smi", "-i", str(self.gpu),
+                                "--query-gpu=ecc.mode.current,clocks.mem,clocks.max.mem",
+                                "--format=csv,noheader,nounits"],
+                               capture_output=True, text=True, timeout=20)
+            ecc, mem, mem_max = [x.strip() for x in r.stdout.strip().split(",")]
+            return {"ecc": ecc, "mem_mhz": float(mem), "mem_max_mhz": float(mem_max)}
+        except Exception:
+            return {}
 
 
 def kernel_source_hash():
