@@ -664,6 +664,52 @@ def run_sweep(args):
                       "exact": _check_recurrence(succ, w, out, dev)}), flush=True)
 
 
+def run_pd_compare(args):
+    """The paper's comparison of the sparse ruling set with pointer doubling
+    (Sections 1 and 3), on one GPU: random-order single lists of 2^20..2^28
+    (and the locality order at 2^28), unweighted, int32 ranks, ranked by the
+    default algorithm and by whole-list Wyllie pointer doubling
+    (lr_tuning.algorithm = LR_ALGO_WYLLIE).  One JSON line per size; both
+    outputs are checked with the rank recurrence."""
+    import torch
+    import paper_2606_09318_gb300 as lr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(2025)
+    pd = lr.Tuning(algorithm=lr.ALGO_WYLLIE)
+    hbm, src = measured_peaks()
+    sizes = [int(x) for x in args.pd_sizes.split(",")]
+    cases = [(lg, "random") for lg in sizes] + [(max(sizes), "locality")]
+    for lg, kind in cases:
+        n = 1 << lg
+        order = (_device_random_order(n, g, dev) if kind == "random" else _device_locality_order(n, g, dev))
+        succ = torch.empty(n, dtype=torch.int32, device=dev)
+        _fill_succ(succ, order)
+        del order
+        out_s = torch.empty(n, dtype=torch.int32, device=dev)
+        out_p = torch.empty(n, dtype=torch.int32, device=dev)
+        ms_s = _time_call(lambda: lr.rank_ex(succ, out=out_s, sync=False), args.steps, args.warmup)
+        assert lr.device_status() == 0
+        ms_p = _time_call(lambda: lr.rank_ex(succ, out=out_p, tuning=pd, sync=False),
+                          max(3, args.steps // 4), args.warmup)
+        assert lr.device_status() == 0
+        exact = _check_recurrence(succ, None, out_s, dev) and bool(torch.equal(out_s, out_p))
+        rounds = max(1, (n - 1).bit_length())
+        # a Wyllie round streams 8 B in and 8 B out per element and gathers one
+        # random 32 B sector per unfinished element (at most n)
+        gb_round = n * (16 + 32) / 1e9
+        print(json.dumps({"workload": "pd_compare", "n": n, "log2n": lg, "order": kind,
+                          "srs_ms": round(ms_s, 3), "srs_g_elem_s": round(n / (ms_s * 1e-3) / 1e9, 3),
+                          "wyllie_ms": round(ms_p, 3), "wyllie_g_elem_s": round(n / (ms_p * 1e-3) / 1e9, 3),
+                          "wyllie_rounds": rounds, "wyllie_ms_per_round": round(ms_p / rounds, 3),
+                          "wyllie_round_gbs_bound": round(gb_round / (ms_p / rounds * 1e-3), 1),
+                          "hbm_peak_gbs": hbm, "peak_source": src,
+                          "srs_speedup": round(ms_p / ms_s, 2), "exact": exact}), flush=True)
+        del succ, out_s, out_p
+        torch.cuda.empty_cache()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -674,8 +720,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access probe")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "sweep"],
-                    help="single: the headline (default); batch / serve: the batched and serving sets")
+    ap.add_argument("--pd-sizes", default="20,22,24,26,28", help="log2 sizes of --workload pd")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "sweep", "pd"],
+                    help="single: the headline (default); batch / serve: the batched and serving sets; "
+                         "sweep: sizes and orders; pd: against whole-list pointer doubling")
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured requests")
     ap.add_argument("--sweep-sizes", default="24,26,28,30", help="sweep: log2 sizes")
     ap.add_argument("--serve-warmup", type=int, default=200)
@@ -693,6 +741,8 @@ def main():
         run_serve(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "pd":
+        run_pd_compare(args)
     else:
         run_ours(args)
 

@@ -77,8 +77,22 @@ typedef struct lr_tuning {
     uint32_t cutoff;     /* largest level ranked by the single-CTA base case     */
     uint32_t chase_block;/* threads per CTA of the chase kernel (default 256)    */
     uint32_t chase_ctas; /* CTAs per SM of the chase kernel (default: occupancy) */
-    uint32_t reserved[3];
+    uint32_t algorithm;  /* LR_ALGO_SRS (0, default) or LR_ALGO_WYLLIE            */
+    uint32_t reserved[2];
 } lr_tuning;
+
+/*
+ * Algorithms behind lr_tuning.algorithm.  LR_ALGO_WYLLIE is pointer doubling
+ * over the whole list, the baseline the paper compares against (Sections 1
+ * and 3): ceil(log2 n) rounds, each replacing every unfinished element's
+ * (successor, partial rank) by its successor's, double buffered.  Same
+ * inputs, outputs, errors and batch form as the default; about log2(n)
+ * random accesses per element instead of one or two, so it serves as the
+ * comparison workload.  Its workspace is lr_workspace_size with the same
+ * tuning; max_lists does not apply and it never synchronises.
+ */
+#define LR_ALGO_SRS 0u
+#define LR_ALGO_WYLLIE 1u
 
 typedef struct lr_opts {
     lr_dtype wtype;           /* weight type: LR_NONE (unweighted), LR_I32, LR_I64   */

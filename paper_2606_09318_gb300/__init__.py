@@ -42,7 +42,10 @@ class LRError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("f0_inv", ctypes.c_uint32), ("f_inv", ctypes.c_uint32), ("cutoff", ctypes.c_uint32),
                 ("chase_block", ctypes.c_uint32), ("chase_ctas", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 3)]
+                ("algorithm", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
+
+
+ALGO_SRS, ALGO_WYLLIE = 0, 1
 
 
 class _Opts(ctypes.Structure):

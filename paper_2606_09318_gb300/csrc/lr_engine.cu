@@ -58,7 +58,9 @@ Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted) {
   u.ctas = env_u32(env, "ctas", u.ctas);
   u.xchg = env_u32(env, "xchg", 1);
   u.logmode = env_u32(env, "log", 0);
+  u.algo = env_u32(env, "algo", LR_ALGO_SRS);
   if (t) {
+    if (t->algorithm) u.algo = t->algorithm;
     if (t->f0_inv) u.f0_inv = t->f0_inv;
     if (t->f_inv) u.f_inv = t->f_inv;
     if (t->cutoff) u.cutoff = t->cutoff;
@@ -340,6 +342,74 @@ static lr_status map_device_bits(uint32_t bits) {
     if (e__ != cudaSuccess) return from_cuda(e__);     \
   } while (0)
 
+// Copy the call's device error word to the context's pinned status word;
+// with sync, wait and return the status it encodes.
+static lr_status finish_call(Ctx *c, const uint32_t *err, int sync, cudaStream_t s) {
+  LR_TRY(cudaMemcpyAsync(c->host_words, err, 4, cudaMemcpyDeviceToHost, s));
+  c->pending_status = true;
+  if (sync) {
+    LR_TRY(cudaStreamSynchronize(s));
+    c->pending_status = false;
+    const uint32_t bits = c->host_words[0];
+    c->host_words[0] = 0;
+    return map_device_bits(bits);
+  }
+  return LR_OK;
+}
+
+// Workspace of the pointer-doubling algorithm: error word and scratch sums,
+// the has-predecessor bitmap (validation), two record arrays.
+struct WyPlan {
+  size_t off_err, off_sums, off_bitmap, off_a, off_b, zero_bytes, bytes;
+};
+
+static WyPlan wyllie_plan(uint64_t n, bool w16) {
+  WyPlan q;
+  size_t o = 0;
+  q.off_err = o; o = align_up(o + 16);
+  q.off_sums = o; o = align_up(o + 16);
+  q.zero_bytes = o;
+  q.off_bitmap = o; o = align_up(o + sizeof(uint32_t) * ((n + 31) / 32));
+  q.off_a = o; o = align_up(o + (w16 ? 16 : 8) * n);
+  q.off_b = o; o = align_up(o + (w16 ? 16 : 8) * n);
+  q.bytes = o;
+  return q;
+}
+
+// 16-byte records exactly when weighted: the layout k_prep0 writes.
+static bool wyllie_w16(const Inputs &in) { return in.wtype != 0; }
+
+// Whole-list pointer doubling (lr_wyllie.cu) on the same inputs and outputs.
+static lr_status run_wyllie(const Inputs &in, Ctx *c, cudaStream_t s) {
+  const bool w16 = wyllie_w16(in);
+  const WyPlan q = wyllie_plan(in.n, w16);
+  char *base = nullptr;
+  if (in.ws) {
+    if (in.ws_bytes < q.bytes) return LR_ERR_INVALID_ARGUMENT;
+    base = (char *)in.ws;
+  } else {
+    const lr_status st = ensure_buffer(&c->var, &c->var_bytes, q.bytes, s);
+    if (st != LR_OK) return st;
+    base = (char *)c->var;
+  }
+  uint32_t *err = (uint32_t *)(base + q.off_err);
+  uint32_t *bitmap = (uint32_t *)(base + q.off_bitmap);
+  unsigned long long *sums = (unsigned long long *)(base + q.off_sums);
+  void *A = base + q.off_a, *B = base + q.off_b;
+  Profiler prof;
+  if (!in.ctx) prof.begin(s, (int64_t)in.n);
+  LR_TRY(cudaMemsetAsync(base, 0, in.validate ? q.off_a : q.zero_bytes, s));
+  // without validation the scratch sums stand in for the bitmap, so the
+  // pass issues no per-element atomics
+  LR_TRY(launch_prep0(in.succ, in.weight, in.wtype, (uint32_t)in.n, A, bitmap, err, in.validate,
+                      in.offsets, in.k, in.validate ? nullptr : sums, s));
+  prof.mark(PH_PREP);
+  LR_TRY(launch_wyllie(A, B, w16, (uint32_t)in.n, in.rank, in.rank_bytes, err, s));
+  prof.mark(PH_BASE);
+  prof.end();
+  return finish_call(c, err, in.sync, s);
+}
+
 lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   const bool ptrs = in.sptr != nullptr;
   lr_status st = LR_OK;
@@ -353,6 +423,8 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   }
   const bool capturing = stream_capturing(s);
   const Tuning u = resolve_tuning(tuning, (int64_t)in.n, in.wtype != 0);
+  if (u.algo == LR_ALGO_WYLLIE && !ptrs) return run_wyllie(in, c, s);
+  if (u.algo != LR_ALGO_SRS && u.algo != LR_ALGO_WYLLIE) return LR_ERR_INVALID_ARGUMENT;
   const bool rec16_0 = in.wtype != 0;
   const bool log0 = u.logmode && !ptrs && in.offsets == nullptr && in.wtype == 0 &&
                     in.rank_bytes == 4 && in.n > u.cutoff && in.n <= (1ull << 30);
@@ -494,16 +566,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   }
   prof.mark(PH_FINAL);
   prof.end();
-  LR_TRY(cudaMemcpyAsync(c->host_words, err, 4, cudaMemcpyDeviceToHost, s));
-  c->pending_status = true;
-  if (in.sync) {
-    LR_TRY(cudaStreamSynchronize(s));
-    c->pending_status = false;
-    const uint32_t bits = c->host_words[0];
-    c->host_words[0] = 0;
-    return map_device_bits(bits);
-  }
-  return LR_OK;
+  return finish_call(c, err, in.sync, s);
 }
 
 lr_status run_fixed_scratch(const uint32_t *succ, int64_t n, int32_t *rank, void *scratch,
@@ -741,6 +804,13 @@ size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts) {
   const Tuning u = resolve_tuning(opts->tuning, n_total, opts->wtype != LR_NONE);
   // The chase grid depends on the device; size for a generous upper bound so
   // the answer needs no GPU: 256 SMs x 16 CTAs.
+  if (u.algo == LR_ALGO_WYLLIE) {
+    Inputs in;
+    memset(&in, 0, sizeof(in));
+    in.wtype = opts->wtype != LR_NONE;
+    in.rank_bytes = opts->rtype == LR_I64 ? 8 : 4;
+    return wyllie_plan((uint64_t)n_total, wyllie_w16(in)).bytes;
+  }
   const uint64_t h = opts->max_lists > 0 ? (uint64_t)opts->max_lists : (uint64_t)n_total;
   const bool log0 = u.logmode && k == 0 && opts->wtype == LR_NONE && opts->rtype == LR_I32 &&
                     (uint64_t)n_total > u.cutoff && n_total <= ((int64_t)1 << 30);

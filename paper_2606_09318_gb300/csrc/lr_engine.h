@@ -10,7 +10,7 @@
 namespace lr {
 
 struct Tuning {
-  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, logmode;
+  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, logmode, algo;
 };
 
 struct Plan {

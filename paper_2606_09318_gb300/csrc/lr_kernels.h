@@ -67,6 +67,13 @@ cudaError_t launch_pd(LevelDesc *desc, int lev, const void *work, uint32_t cap, 
                       uint32_t *nxt0, uint32_t *nxt1, uint64_t *val0, uint64_t *val1, void *rout,
                       int rank_bytes, uint32_t *err, cudaStream_t s);
 
+// Whole-list Wyllie pointer doubling (lr_wyllie.cu).  bufA holds k_prep0's
+// records (8 B, or 16 B when weighted: w16), bufB the same size; ranks go
+// to `rank` (4 or 8 bytes each).
+uint32_t wyllie_rounds(uint64_t n);
+cudaError_t launch_wyllie(void *bufA, void *bufB, bool w16, uint32_t n, void *rank, int rank_bytes,
+                          uint32_t *err, cudaStream_t s);
+
 cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec16,
                             const void *rnext, void *rout, int rank_bytes, uint32_t cap,
                             uint32_t *err, cudaStream_t s);
