@@ -41,13 +41,24 @@ static uint32_t env_u32(const char *spec, const char *key, uint32_t dflt) {
   return dflt;
 }
 
+// Default ruler fraction at level 0 by size (measured on GB300, random
+// order, f = 1/8 above level 0).  Small lists are bound by the latency of
+// the dependent exchanges along one segment, so they take more rulers and
+// shorter segments; from 2^27 up the chase is bound by the random-access
+// rate and 1/64 keeps the recursion smallest.
+static uint32_t default_f0_inv(int64_t n) {
+  if (n < ((int64_t)1 << 16)) return 4;
+  if (n < ((int64_t)1 << 22)) return 8;
+  if (n < ((int64_t)1 << 27)) return 16;
+  return 64;
+}
+
 Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted) {
-  (void)n;
   (void)weighted;
   Tuning u;
-  u.f0_inv = 64;
+  u.f0_inv = default_f0_inv(n);
   u.f_inv = 8;
-  u.cutoff = 8192;
+  u.cutoff = kMaxCutoff;
   u.block = 256;
   u.ctas = 0;
   const char *env = getenv("LR_TUNING");
