@@ -55,6 +55,15 @@ def _load():
             lib.lro_rank_batch.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                            ctypes.c_int]
+            lib.lro_rank_ext.restype = ctypes.c_int
+            lib.lro_rank_ext.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+            lib.lro_rank_ext_batch.restype = ctypes.c_int
+            lib.lro_rank_ext_batch.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                               ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -114,3 +123,38 @@ def rank_batch(offsets, succ, weight=None, rank_dtype=np.int64):
     if st != OK:
         raise ValueError("oracle: " + STATUS_NAMES.get(st, str(st)))
     return out
+
+
+def rank_ext(succ, weight=None, rank_dtype=np.int32, inclusive=False):
+    """Rank plus the other outputs Section 1.1 defines: returns
+    (rank, term, prefix) -- the terminal of every element's list and the
+    head-relative rank; inclusive=True adds the terminal's own weight to rank
+    (the paper's in-place form).  Raises ValueError on invalid input."""
+    succ, weight, rdt = _check_inputs(succ, weight, rank_dtype)
+    n = succ.shape[0]
+    out = np.zeros(n, dtype=rdt)
+    term = np.zeros(n, dtype=np.uint32)
+    prefix = np.zeros(n, dtype=rdt)
+    wcode = _W_CODES[None if weight is None else weight.dtype]
+    st = _load().lro_rank_ext(_ptr(succ), _ptr(weight), wcode, n, _ptr(out), _R_CODES[rdt],
+                              _ptr(term), _ptr(prefix), 1 if inclusive else 0)
+    if st != OK:
+        raise ValueError("oracle: " + STATUS_NAMES.get(st, str(st)))
+    return out, term, prefix
+
+
+def rank_ext_batch(offsets, succ, weight=None, rank_dtype=np.int64, inclusive=False):
+    """Batched rank_ext; terminal ids are local to their instance."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    succ, weight, rdt = _check_inputs(succ, weight, rank_dtype)
+    k = offsets.shape[0] - 1
+    n = succ.shape[0]
+    out = np.zeros(n, dtype=rdt)
+    term = np.zeros(n, dtype=np.uint32)
+    prefix = np.zeros(n, dtype=rdt)
+    wcode = _W_CODES[None if weight is None else weight.dtype]
+    st = _load().lro_rank_ext_batch(_ptr(offsets), k, _ptr(succ), _ptr(weight), wcode, _ptr(out),
+                                    _R_CODES[rdt], _ptr(term), _ptr(prefix), 1 if inclusive else 0)
+    if st != OK:
+        raise ValueError("oracle: " + STATUS_NAMES.get(st, str(st)))
+    return out, term, prefix

@@ -136,3 +136,77 @@ int lro_rank_batch(const int64_t *offsets, int32_t k, const uint32_t *succ,
     }
     return LRO_OK;
 }
+
+/*
+ * Full output of Section 1.1: besides the rank, the paper's result names for
+ * every element the terminal of its list (it overwrites succ[i] with it), and
+ * its in-place form leaves the terminal's own weight in rank[t].  Computed
+ * here straight from those definitions, after lro_rank has validated the
+ * input and produced the (exclusive) ranks:
+ *   term[i]   = the element reached from i by following succ until
+ *               succ[x] == x;
+ *   prefix[i] = the sum of the link weights from the head of i's list up to
+ *               i, not counting i's own link (0 at a head);
+ *   inclusive: rank[i] += weight of the terminal (1 when unweighted), i.e. the
+ *               terminal's weight is no longer ignored.
+ * term and prefix may be NULL (not produced); prefix has the rank type.
+ */
+int lro_rank_ext(const uint32_t *succ, const void *weight, int wtype, int64_t n,
+                 void *rank, int rtype, uint32_t *term, void *prefix, int inclusive)
+{
+    int st = lro_rank(succ, weight, wtype, n, rank, rtype);
+    if (st != LRO_OK || n == 0) return st;
+    uint8_t *haspred = (uint8_t *)calloc((size_t)n, 1);
+    if (!haspred) return LRO_NO_MEMORY;
+    for (int64_t i = 0; i < n; ++i)
+        if ((int64_t)succ[i] != i) haspred[succ[i]] = 1;
+    for (int64_t h = 0; h < n; ++h) {
+        if (haspred[h]) continue;
+        /* find the terminal of h's list */
+        uint32_t t = (uint32_t)h;
+        while (succ[t] != t) t = succ[t];
+        /* walk again from the head: terminal, running prefix, inclusive rank */
+        uint64_t acc = 0;
+        uint64_t wt = weight_of(weight, wtype, t);
+        uint32_t x = (uint32_t)h;
+        for (;;) {
+            if (term) term[x] = t;
+            if (prefix) store_rank(prefix, rtype, x, acc);
+            if (inclusive) {
+                uint64_t r = rtype == LRO_R_I32 ? (uint64_t)((uint32_t *)rank)[x]
+                                                : ((uint64_t *)rank)[x];
+                store_rank(rank, rtype, x, r + wt);
+            }
+            if (succ[x] == x) break;
+            acc += weight_of(weight, wtype, x);
+            x = succ[x];
+        }
+    }
+    free(haspred);
+    return LRO_OK;
+}
+
+/* Batched form of lro_rank_ext: terminal ids are local to their instance. */
+int lro_rank_ext_batch(const int64_t *offsets, int32_t k, const uint32_t *succ,
+                       const void *weight, int wtype, void *rank, int rtype,
+                       uint32_t *term, void *prefix, int inclusive)
+{
+    if (k < 0 || !offsets) return LRO_INVALID;
+    if (k > 0 && offsets[0] != 0) return LRO_INVALID;
+    for (int32_t j = 0; j < k; ++j)
+        if (offsets[j + 1] < offsets[j]) return LRO_INVALID;
+    size_t wsz = wtype == LRO_W_I32 ? 4 : 8;
+    size_t rsz = rtype == LRO_R_I32 ? 4 : 8;
+    for (int32_t j = 0; j < k; ++j) {
+        int64_t a = offsets[j], len = offsets[j + 1] - offsets[j];
+        const void *wj = wtype == LRO_W_NONE ? NULL
+                         : (const void *)((const char *)weight + (size_t)a * wsz);
+        int st = lro_rank_ext(succ + a, wj, wtype, len,
+                              (void *)((char *)rank + (size_t)a * rsz), rtype,
+                              term ? term + a : NULL,
+                              prefix ? (void *)((char *)prefix + (size_t)a * rsz) : NULL,
+                              inclusive);
+        if (st != LRO_OK) return st;
+    }
+    return LRO_OK;
+}

@@ -251,3 +251,150 @@ def test_mutants_are_caught(tmp_path):
         so = tmp_path / ("m_%s.so" % name)
         subprocess.check_call(["gcc", "-std=c11", "-O1", "-fPIC", "-shared", "-o", str(so), str(mutant_c)])
         assert not _pins_pass(ctypes.CDLL(str(so))), "pins did not catch mutant %s" % name
+
+
+# ---------------------------------------------------------------- extra outputs
+# Section 1.1 also names each element's terminal as part of the result, and
+# the in-place form counts the terminal's weight.  Pins for oracle.rank_ext.
+
+def brute_force_ext(succ, weight=None):
+    """term[i]: the end of the walk from i.  prefix[x]: the sum of w[j] over
+    every strict ancestor j of x (every j whose walk passes through x).
+    O(n^2) walks from every element; a formulation unlike the oracle's."""
+    succ = np.asarray(succ, dtype=np.int64)
+    n = succ.shape[0]
+    w = np.ones(n, dtype=np.int64) if weight is None else np.asarray(weight, dtype=np.int64)
+    term = np.zeros(n, dtype=np.int64)
+    prefix = np.zeros(n, dtype=np.int64)
+    for j in range(n):
+        x = j
+        while succ[x] != x:
+            x = succ[x]
+            prefix[x] += w[j]
+        term[j] = x
+    return term, prefix
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_ext_brute_force_forest(seed):
+    succ, _ = gen.forest(400, seed, n_long=2, long_len=60, mean_short=7)
+    w = gen.weights_i32(400, seed + 10)
+    for weight in (None, w):
+        r, t, p = oracle.rank_ext(succ, weight, np.int64)
+        bt, bp = brute_force_ext(succ, weight)
+        np.testing.assert_array_equal(t, bt)
+        np.testing.assert_array_equal(p, bp)
+        np.testing.assert_array_equal(r, brute_force(succ, weight, np.int64))
+        ri, ti, pi = oracle.rank_ext(succ, weight, np.int64, inclusive=True)
+        wt = np.ones(400, dtype=np.int64) if weight is None else weight.astype(np.int64)
+        np.testing.assert_array_equal(ri, r + wt[bt])
+        np.testing.assert_array_equal(ti, bt)
+        np.testing.assert_array_equal(pi, bp)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 1000])
+def test_ext_identity_closed_form(n):
+    succ = gen.identity_list(n)
+    r, t, p = oracle.rank_ext(succ)
+    np.testing.assert_array_equal(t, np.full(n, n - 1))
+    np.testing.assert_array_equal(p, np.arange(n))
+    ri, _, _ = oracle.rank_ext(succ, inclusive=True)
+    np.testing.assert_array_equal(ri, n - np.arange(n))
+    w = gen.weights_i64(n, n, lo=-50, hi=50)
+    r, t, p = oracle.rank_ext(succ, w, np.int64)
+    excl = np.concatenate([[0], np.cumsum(w[:-1])])          # sum of the links before i
+    np.testing.assert_array_equal(p, excl)
+    ri, _, _ = oracle.rank_ext(succ, w, np.int64, inclusive=True)
+    np.testing.assert_array_equal(ri, np.cumsum(w[::-1])[::-1])   # suffix sums including the tail
+
+
+def test_ext_invariants_forest():
+    succ, nl = gen.forest(1 << 16, 9, n_long=4, long_len=1 << 12, mean_short=32)
+    w = gen.weights_i32(1 << 16, 10)
+    r, t, p = oracle.rank_ext(succ, w, np.int64)
+    s = succ.astype(np.int64)
+    idx = np.arange(s.shape[0])
+    assert np.all(s[t] == t)                                 # a terminal ends every walk
+    assert np.all(t[s] == t)                                 # the terminal is shared along a list
+    tot = p[t]                                               # the total sits at the terminal
+    np.testing.assert_array_equal(p + r, tot)
+    nt = s != idx
+    np.testing.assert_array_equal(p[s[nt]], p[nt] + w[nt])   # forward recurrence
+    heads = np.setdiff1d(idx, s[nt])
+    assert heads.shape[0] == nl and np.all(p[heads] == 0)
+    assert np.unique(t).shape[0] == nl
+
+
+@pytest.mark.parametrize("V", [2, 3, 50, 20000])
+def test_ext_euler_tour_depths(V):
+    """Euler-tour technique: the prefix sum of the +-1 arcs before an arc is
+    the depth of the node the tour stands on."""
+    parent = gen.random_recursive_tree(V, 50 + V)
+    succ, w = gen.euler_tour(parent)
+    _, t, p = oracle.rank_ext(succ, w, np.int32)
+    depth = np.zeros(V, dtype=np.int64)
+    for v in range(1, V):
+        depth[v] = depth[parent[v]] + 1
+    v = np.arange(1, V)
+    down, up = 2 * (v - 1), 2 * (v - 1) + 1
+    np.testing.assert_array_equal(p[down], depth[parent[v]])
+    np.testing.assert_array_equal(p[up], depth[v])
+    assert np.all(t == t[0]) and succ[t[0]] == t[0]
+
+
+def test_ext_batch_local_terminals():
+    offsets, succ, w = gen.batch_instances(10, 78, lo_exp=0.0, hi_exp=9.0)
+    r, t, p = oracle.rank_ext_batch(offsets, succ, w, np.int64, inclusive=True)
+    for j in range(10):
+        a, b = offsets[j], offsets[j + 1]
+        rj, tj, pj = oracle.rank_ext(succ[a:b], w[a:b], np.int64, inclusive=True)
+        np.testing.assert_array_equal(r[a:b], rj)
+        np.testing.assert_array_equal(t[a:b], tj)
+        np.testing.assert_array_equal(p[a:b], pj)
+        assert np.all(t[a:b] < b - a)
+
+
+_EXT_MUTATIONS = {
+    "prefix_counts_own_link": ("            acc += weight_of(weight, wtype, x);\n            x = succ[x];",
+                               "            x = succ[x];\n            acc += weight_of(weight, wtype, x);"),
+    "inclusive_uses_head_weight": ("uint64_t wt = weight_of(weight, wtype, t);",
+                                   "uint64_t wt = weight_of(weight, wtype, h);"),
+    "term_is_head": ("if (term) term[x] = t;", "if (term) term[x] = (uint32_t)h;"),
+    "prefix_starts_at_head_weight": ("        uint64_t acc = 0;\n        uint64_t wt",
+                                     "        uint64_t acc = weight_of(weight, wtype, h);\n        uint64_t wt"),
+}
+
+
+def _ext_pins_pass(lib):
+    lib.lro_rank_ext.restype = ctypes.c_int
+    lib.lro_rank_ext.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                 ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_int]
+    for seed in (1, 2):
+        succ, _ = gen.forest(300, seed, n_long=2, long_len=50, mean_short=6)
+        succ = np.ascontiguousarray(succ, dtype=np.uint32)
+        w = gen.weights_i32(300, seed + 20)
+        bt, bp = brute_force_ext(succ, w)
+        for incl in (0, 1):
+            r = np.zeros(300, dtype=np.int64)
+            t = np.zeros(300, dtype=np.uint32)
+            p = np.zeros(300, dtype=np.int64)
+            st = lib.lro_rank_ext(succ.ctypes.data, w.ctypes.data, 1, 300, r.ctypes.data, 2,
+                                  t.ctypes.data, p.ctypes.data, incl)
+            want_r = brute_force(succ, w, np.int64) + (w.astype(np.int64)[bt] if incl else 0)
+            if st != 0 or not (np.array_equal(t, bt) and np.array_equal(p, bp) and np.array_equal(r, want_r)):
+                return False
+    return True
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_ext_mutants_are_caught(tmp_path):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "lr_oracle.c")).read()
+    assert _ext_pins_pass(ctypes.CDLL(oracle.build()))
+    for name, (old, new) in _EXT_MUTATIONS.items():
+        assert src.count(old) == 1, "mutation site for %s is gone from the oracle" % name
+        mutant_c = tmp_path / ("e_%s.c" % name)
+        mutant_c.write_text(src.replace(old, new, 1))
+        so = tmp_path / ("e_%s.so" % name)
+        subprocess.check_call(["gcc", "-std=c11", "-O1", "-fPIC", "-shared", "-o", str(so), str(mutant_c)])
+        assert not _ext_pins_pass(ctypes.CDLL(str(so))), "pins did not catch mutant %s" % name
