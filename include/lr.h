@@ -141,6 +141,36 @@ lr_status lr_rank_batch_ex(const int64_t *offsets, const uint32_t *succ, const v
                            void *rank, int32_t k, const lr_opts *opts, lr_stream stream);
 
 /*
+ * Extra outputs of the default algorithm (Section 1.1 defines the result
+ * as each element's rank AND the terminal of its list; its in-place form
+ * counts the terminal's own weight).  All pointers are device memory owned
+ * by the caller, n entries each, none aliasing succ, weight or rank:
+ *   term            uint32: the terminal (last element) of i's list; in the
+ *                   batched form a LOCAL id within i's instance.  NULL: not
+ *                   produced.
+ *   prefix          opts->rtype: head-relative rank, the sum of the link
+ *                   weights from i's head to i (0 at a head; the list's
+ *                   total at its terminal).  NULL: not produced.
+ *   inclusive_tail  1: rank[i] also counts the terminal's own weight
+ *                   (weight[t], or 1 when unweighted), so rank[t] = w(t).
+ *                   prefix is the same either way.
+ * Not available with LR_ALGO_WYLLIE (LR_ERR_INVALID_ARGUMENT).  Errors as
+ * for lr_rank_ex; on error the extra outputs are unspecified too.
+ */
+typedef struct lr_outputs {
+    uint32_t *term;
+    void *prefix;
+    int32_t inclusive_tail;
+} lr_outputs;
+
+lr_status lr_rank_outputs(const uint32_t *succ, const void *weight, int64_t n, void *rank,
+                          const lr_outputs *outs, const lr_opts *opts, lr_stream stream);
+
+lr_status lr_rank_batch_outputs(const int64_t *offsets, const uint32_t *succ, const void *weight,
+                                void *rank, int32_t k, const lr_outputs *outs, const lr_opts *opts,
+                                lr_stream stream);
+
+/*
  * End-to-end form with HOST buffers (pageable or pinned): copies succ and
  * weight to the device, ranks, copies rank back and waits.  Returns the
  * final status (argument or device error).
@@ -171,6 +201,11 @@ lr_status lr_rank_host_async(const uint32_t *succ_host, const void *weight_host,
  * Host-only; needs no GPU.
  */
 size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts);
+
+/* Same for a call with extra outputs: only which pointers of *outs are
+ * non-NULL (and inclusive_tail) matters; outs == NULL is lr_workspace_size. */
+size_t lr_workspace_size_outputs(int64_t n_total, int32_t k, const lr_outputs *outs,
+                                 const lr_opts *opts);
 
 /*
  * Wait for `stream` and return (and clear) the status the device recorded

@@ -55,6 +55,11 @@ class _Opts(ctypes.Structure):
                 ("max_lists", ctypes.c_int64), ("n_total", ctypes.c_int64)]
 
 
+class _Outputs(ctypes.Structure):
+    _fields_ = [("term", ctypes.c_void_p), ("prefix", ctypes.c_void_p),
+                ("inclusive_tail", ctypes.c_int32)]
+
+
 class _Profile(ctypes.Structure):
     _fields_ = [("ms_prep", ctypes.c_double), ("ms_select", ctypes.c_double),
                 ("ms_chase0", ctypes.c_double), ("ms_chase_rest", ctypes.c_double),
@@ -104,6 +109,11 @@ _SIGS = {
     "lr_rank_host": (ctypes.c_int, [_V, _V, _I64, _V, ctypes.POINTER(_Opts), _V]),
     "lr_rank_host_async": (ctypes.c_int, [_V, _V, _I64, _V, ctypes.POINTER(_Opts), _V]),
     "lr_workspace_size": (_SZ, [_I64, _I32, ctypes.POINTER(_Opts)]),
+    "lr_workspace_size_outputs": (_SZ, [_I64, _I32, ctypes.POINTER(_Outputs), ctypes.POINTER(_Opts)]),
+    "lr_rank_outputs": (ctypes.c_int, [_V, _V, _I64, _V, ctypes.POINTER(_Outputs),
+                                       ctypes.POINTER(_Opts), _V]),
+    "lr_rank_batch_outputs": (ctypes.c_int, [_V, _V, _V, _V, _I32, ctypes.POINTER(_Outputs),
+                                             ctypes.POINTER(_Opts), _V]),
     "lr_get_device_status": (ctypes.c_int, [_V]),
     "lr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lr_version": (ctypes.c_char_p, []),
@@ -274,6 +284,70 @@ def rank_batch(offsets, succ, weight=None, out=None, rank_dtype=None, validate=F
     return out
 
 
+def _outputs(succ, rdt, term, prefix, inclusive_tail):
+    """Allocate (or check) the extra output tensors; returns (struct, term, prefix)."""
+    torch = _torch()
+    o = _Outputs()
+    t = p = None
+    if term is not None and term is not False:
+        t = torch.empty(succ.numel(), dtype=torch.int32, device=succ.device) if term is True else term
+        o.term = _dev_ptr(t, "term", (torch.int32,) + tuple(d for d in (getattr(torch, "uint32", None),) if d))
+    if prefix is not None and prefix is not False:
+        p = torch.empty(succ.numel(), dtype=rdt, device=succ.device) if prefix is True else prefix
+        o.prefix = _dev_ptr(p, "prefix", (rdt,))
+    o.inclusive_tail = 1 if inclusive_tail else 0
+    for a in (t, p):
+        if a is not None and a.numel() != succ.numel():
+            raise ValueError("extra output has the wrong length")
+    return o, t, p
+
+
+def rank_outputs(succ, weight=None, term=True, prefix=False, inclusive_tail=False, out=None,
+                 rank_dtype=None, validate=False, seed=0x5EED, max_lists=0, tuning=None, sync=True,
+                 stream=None, workspace=None):
+    """Rank plus the other outputs of Section 1.1 (lr_rank_outputs): term /
+    prefix may be True (allocate), a CUDA tensor to fill, or False/None.
+    Returns (rank, term, prefix); term holds int32 views of the uint32 ids."""
+    torch = _torch()
+    lib = load()
+    rdt = out.dtype if out is not None else _rank_dtype(weight, rank_dtype)
+    sp = _dev_ptr(succ, "succ", _succ_dtypes())
+    n = succ.numel()
+    wp = None if weight is None else _dev_ptr(weight, "weight", (torch.int32, torch.int64))
+    if out is None:
+        out = torch.empty(n, dtype=rdt, device=succ.device)
+    rp = _dev_ptr(out, "out", (torch.int32, torch.int64))
+    outs, t, p = _outputs(succ, rdt, term, prefix, inclusive_tail)
+    o = _opts(_wcode(weight), LR_I32 if rdt == torch.int32 else LR_I64, validate, seed,
+              max_lists, tuning, sync, workspace=workspace)
+    code = lib.lr_rank_outputs(sp, wp, n, rp, ctypes.byref(outs), ctypes.byref(o), _stream_handle(stream))
+    _check(code, "lr_rank_outputs")
+    return out, t, p
+
+
+def rank_batch_outputs(offsets, succ, weight=None, term=True, prefix=False, inclusive_tail=False,
+                       out=None, rank_dtype=None, validate=False, seed=0x5EED, max_lists=0,
+                       n_total=0, tuning=None, sync=True, stream=None, workspace=None):
+    """Batched rank_outputs (lr_rank_batch_outputs); terminal ids are local."""
+    torch = _torch()
+    lib = load()
+    op = _dev_ptr(offsets, "offsets", (torch.int64,))
+    k = offsets.numel() - 1
+    rdt = out.dtype if out is not None else _rank_dtype(weight, rank_dtype)
+    sp = _dev_ptr(succ, "succ", _succ_dtypes())
+    wp = None if weight is None else _dev_ptr(weight, "weight", (torch.int32, torch.int64))
+    if out is None:
+        out = torch.empty(succ.numel(), dtype=rdt, device=succ.device)
+    rp = _dev_ptr(out, "out", (torch.int32, torch.int64))
+    outs, t, p = _outputs(succ, rdt, term, prefix, inclusive_tail)
+    o = _opts(_wcode(weight), LR_I32 if rdt == torch.int32 else LR_I64, validate, seed,
+              max_lists, tuning, sync, n_total=n_total or succ.numel(), workspace=workspace)
+    code = lib.lr_rank_batch_outputs(op, sp, wp, rp, k, ctypes.byref(outs), ctypes.byref(o),
+                                     _stream_handle(stream))
+    _check(code, "lr_rank_batch_outputs")
+    return out, t, p
+
+
 def rank_host(succ, weight=None, out=None, rank_dtype=None, validate=False, seed=0x5EED,
               max_lists=0, stream=None, wait=True):
     """End-to-end form on host tensors / numpy arrays: copy in, rank, copy out.
@@ -315,7 +389,10 @@ def device_status(stream=None):
     return load().lr_get_device_status(_stream_handle(stream))
 
 
-def workspace_size(n_total, k=0, weighted=False, rank64=None, max_lists=0, tuning=None):
+def workspace_size(n_total, k=0, weighted=False, rank64=None, max_lists=0, tuning=None,
+                   term=False, prefix=False, inclusive_tail=False):
+    """lr_workspace_size (or lr_workspace_size_outputs when extra outputs
+    are named: only whether each is asked for matters)."""
     if rank64 is None:
         rank64 = weighted
     o = _Opts()
@@ -325,6 +402,13 @@ def workspace_size(n_total, k=0, weighted=False, rank64=None, max_lists=0, tunin
     o.max_lists = int(max_lists)
     if tuning is not None:
         o.tuning = ctypes.pointer(tuning)
+    if term or prefix or inclusive_tail:
+        outs = _Outputs()
+        outs.term = 1 if term else None        # only non-NULL-ness is read
+        outs.prefix = 1 if prefix else None
+        outs.inclusive_tail = 1 if inclusive_tail else 0
+        return int(load().lr_workspace_size_outputs(int(n_total), int(k), ctypes.byref(outs),
+                                                    ctypes.byref(o)))
     return int(load().lr_workspace_size(int(n_total), int(k), ctypes.byref(o)))
 
 

@@ -100,7 +100,7 @@ int chase_grid_for(const Tuning &u, bool rec16, bool log0) {
 
 // Static plan for n elements and at most h lists.
 Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,
-               uint64_t seed, int chase_grid, bool force_srs, bool log0) {
+               uint64_t seed, int chase_grid, bool force_srs, bool log0, bool term, bool t0ws) {
   Plan p;
   memset(&p, 0, sizeof(p));
   p.n = n;
@@ -185,6 +185,19 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
     p.off_pd[1] = o; o = align_up(o + 4 * (size_t)p.cap[L]);
     p.off_pd[2] = o; o = align_up(o + 8 * (size_t)p.cap[L]);
     p.off_pd[3] = o; o = align_up(o + 8 * (size_t)p.cap[L]);
+  }
+  p.term = term;
+  if (term) {
+    for (int l = 1; l <= L; ++l) {
+      p.off_T[l] = o; o = align_up(o + 4 * (size_t)p.cap[l]);
+      p.off_tid[l] = o; o = align_up(o + 4 * (size_t)p.cap[l]);
+    }
+    p.off_hC = o; o = align_up(o + 4 * (size_t)p.hcap);   // keeps level 0's head list intact
+    if (p.has_pd) {
+      p.off_pdt[0] = o; o = align_up(o + 4 * (size_t)p.cap[L]);
+      p.off_pdt[1] = o; o = align_up(o + 4 * (size_t)p.cap[L]);
+    }
+    if (t0ws) { p.off_T0 = o; o = align_up(o + 4 * (size_t)n); }
   }
   p.var_bytes = std::max<size_t>(o, 256);
   return p;
@@ -336,6 +349,9 @@ struct Inputs {
   void *const *rptr;
   Ctx *ctx;                      // use this context instead of the per-stream one
   int count_in_ws;               // caller workspace, but still count the lists first
+  uint32_t *term;                // extra outputs (device, optional): terminal ids,
+  void *prefix;                  // head-relative ranks,
+  int incl;                      // inclusive-tail ranks
 };
 
 static lr_status map_device_bits(uint32_t bits) {
@@ -434,17 +450,23 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   }
   const bool capturing = stream_capturing(s);
   const Tuning u = resolve_tuning(tuning, (int64_t)in.n, in.wtype != 0);
-  if (u.algo == LR_ALGO_WYLLIE && !ptrs) return run_wyllie(in, c, s);
+  if (u.algo == LR_ALGO_WYLLIE && !ptrs) {
+    if (in.term || in.prefix || in.incl) return LR_ERR_INVALID_ARGUMENT;   // default algorithm only
+    return run_wyllie(in, c, s);
+  }
   if (u.algo != LR_ALGO_SRS && u.algo != LR_ALGO_WYLLIE) return LR_ERR_INVALID_ARGUMENT;
   const bool rec16_0 = in.wtype != 0;
-  const bool log0 = u.logmode && !ptrs && in.offsets == nullptr && in.wtype == 0 &&
+  const bool extras = in.term != nullptr || in.prefix != nullptr || in.incl != 0;
+  if (extras && ptrs) return LR_ERR_INVALID_ARGUMENT;
+  const bool log0 = u.logmode && !ptrs && !extras && in.offsets == nullptr && in.wtype == 0 &&
                     in.rank_bytes == 4 && in.n > u.cutoff && in.n <= (1ull << 30);
+  const bool t0ws = extras && in.term == nullptr;
   const int grid = chase_grid_for(u, rec16_0, log0);
   const bool need_count = in.max_lists <= 0 && (in.ws == nullptr || in.count_in_ws) &&
                           (in.n > u.cutoff || ptrs);
   if (need_count && capturing) return LR_ERR_CAPTURE;
   uint64_t hb = in.max_lists > 0 ? (uint64_t)in.max_lists : in.n;
-  Plan p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0);
+  Plan p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws);
 
   // fixed part (level 0)
   char *fixed = nullptr;
@@ -494,7 +516,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     }
     LR_TRY(cudaStreamSynchronize(s));
     hb = std::max<uint64_t>(1, c->host_words[1]);
-    p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0);
+    p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws);
   }
   if (!in.ws) {
     st = ensure_buffer(&c->var, &c->var_bytes, p.var_bytes, s);
@@ -528,16 +550,30 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
 
   auto work_of = [&](int l) -> void * { return l == 0 ? work0 : (void *)(var + p.off_work[l]); };
   auto R_of = [&](int l) -> void * { return l == 0 ? in.rank : (void *)(var + p.off_R[l]); };
+  // terminal ids: T_l of every element of level l (the caller's array, or
+  // workspace, at level 0), tid_l of every terminal of level l >= 1
+  uint32_t *T0 = extras ? (in.term ? in.term : (uint32_t *)(var + p.off_T0)) : nullptr;
+  auto T_of = [&](int l) -> uint32_t * {
+    if (!extras) return nullptr;
+    return l == 0 ? T0 : (uint32_t *)(var + p.off_T[l]);
+  };
+  auto tid_of = [&](int l) -> uint32_t * {
+    return (extras && l > 0) ? (uint32_t *)(var + p.off_tid[l]) : nullptr;
+  };
   uint32_t *hA = (uint32_t *)(var + p.off_hA);
   uint32_t *hB = (uint32_t *)(var + p.off_hB);
+  uint32_t *hC = extras ? (uint32_t *)(var + p.off_hC) : hA;
   uint32_t *ns = (uint32_t *)(var + p.off_ns);
   const int L = p.nlev - 1;
   for (int l = 0; l < L; ++l) {
     const bool r16 = l > 0 || rec16_0;
-    uint32_t *hin = (l & 1) ? hB : hA;
-    uint32_t *hout = (l & 1) ? hA : hB;
+    // head lists alternate between buffers; with extra outputs level 0's
+    // list (hA) stays intact for the prefix pass
+    uint32_t *hin = l == 0 ? hA : ((l & 1) ? hB : hC);
+    uint32_t *hout = l == 0 ? hB : ((l & 1) ? hC : hB);
     if (l > 0) {
-      LR_TRY(launch_base(desc, l, work_of(l), r16, R_of(l), p.rank_bytes, p.cutoff, err, s));
+      LR_TRY(launch_base(desc, l, work_of(l), r16, R_of(l), p.rank_bytes, p.cutoff, err, tid_of(l),
+                         T_of(l), s));
       prof.mark(PH_BASE);
     }
     const int kind = (l == 0 && log0) ? kRecKindSucc : (r16 ? kRecKind16 : kRecKind8);
@@ -551,14 +587,18 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     else
       LR_TRY(launch_chase(desc, l, work_of(l), r16, work_of(l + 1), ns,
                           qctr + (size_t)l * p.chase_grid, p.chase_grid, p.chase_block, err,
-                          (int)u.xchg, s));
+                          (int)u.xchg, tid_of(l), tid_of(l + 1), s));
     prof.mark(l == 0 ? PH_CHASE0 : PH_CHASE);
   }
-  LR_TRY(launch_base(desc, L, work_of(L), L > 0 || rec16_0, R_of(L), p.rank_bytes, p.cutoff, err, s));
+  LR_TRY(launch_base(desc, L, work_of(L), L > 0 || rec16_0, R_of(L), p.rank_bytes, p.cutoff, err,
+                     tid_of(L), T_of(L), s));
   if (p.has_pd) {
+    uint32_t *pt0 = extras ? (uint32_t *)(var + p.off_pdt[0]) : nullptr;
+    uint32_t *pt1 = extras ? (uint32_t *)(var + p.off_pdt[1]) : nullptr;
     LR_TRY(launch_pd(desc, L, work_of(L), p.cap[L], p.pd_rounds, (uint32_t *)(var + p.off_pd[0]),
                      (uint32_t *)(var + p.off_pd[1]), (uint64_t *)(var + p.off_pd[2]),
-                     (uint64_t *)(var + p.off_pd[3]), R_of(L), p.rank_bytes, err, s));
+                     (uint64_t *)(var + p.off_pd[3]), R_of(L), p.rank_bytes, err, tid_of(L), pt0, pt1,
+                     T_of(L), s));
   }
   prof.mark(PH_BASE);
   for (int l = L - 1; l >= 0; --l) {
@@ -573,8 +613,12 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
                                   in.offsets, in.k, err, s));
     else
       LR_TRY(launch_finalize(desc, l, work_of(l), l > 0 || rec16_0, R_of(l + 1), R_of(l),
-                             p.rank_bytes, p.cap[l], err, s));
+                             p.rank_bytes, p.cap[l], err, T_of(l + 1), T_of(l), tid_of(l), s));
   }
+  if (extras)
+    LR_TRY(launch_outputs(desc, bitmap, hA0, (uint32_t)in.n, T0, in.rank, in.prefix, p.rank_bytes,
+                          in.incl, in.weight, in.wtype, in.offsets, in.k,
+                          in.offsets != nullptr && in.term != nullptr, s));
   prof.mark(PH_FINAL);
   prof.end();
   return finish_call(c, err, in.sync, s);
@@ -674,8 +718,15 @@ static lr_status check_types(const void *weight, lr_dtype wtype, lr_dtype rtype,
   return LR_OK;
 }
 
-lr_status lr_rank_ex(const uint32_t *succ, const void *weight, int64_t n, void *rank,
-                     const lr_opts *opts, lr_stream stream) {
+static void set_outputs(Inputs &in, const lr_outputs *outs) {
+  if (!outs) return;
+  in.term = outs->term;
+  in.prefix = outs->prefix;
+  in.incl = outs->inclusive_tail != 0;
+}
+
+static lr_status rank_ex_impl(const uint32_t *succ, const void *weight, int64_t n, void *rank,
+                              const lr_outputs *outs, const lr_opts *opts, lr_stream stream) {
   lr_opts d;
   if (!opts) { lr_opts_default(&d); if (weight) { d.wtype = LR_I64; d.rtype = LR_I64; } opts = &d; }
   if (n < 0 || n > LR_MAX_N) return LR_ERR_INVALID_ARGUMENT;
@@ -698,7 +749,18 @@ lr_status lr_rank_ex(const uint32_t *succ, const void *weight, int64_t n, void *
   in.sync = opts->sync;
   in.ws = opts->workspace;
   in.ws_bytes = opts->ws_bytes;
+  set_outputs(in, outs);
   return run(in, opts->tuning, (cudaStream_t)stream);
+}
+
+lr_status lr_rank_ex(const uint32_t *succ, const void *weight, int64_t n, void *rank,
+                     const lr_opts *opts, lr_stream stream) {
+  return rank_ex_impl(succ, weight, n, rank, nullptr, opts, stream);
+}
+
+lr_status lr_rank_outputs(const uint32_t *succ, const void *weight, int64_t n, void *rank,
+                          const lr_outputs *outs, const lr_opts *opts, lr_stream stream) {
+  return rank_ex_impl(succ, weight, n, rank, outs, opts, stream);
 }
 
 lr_status lr_rank(const uint32_t *succ, const void *weight, int64_t n, void *rank, lr_stream stream) {
@@ -709,8 +771,9 @@ lr_status lr_rank(const uint32_t *succ, const void *weight, int64_t n, void *ran
   return lr_rank_ex(succ, weight, n, rank, &o, stream);
 }
 
-lr_status lr_rank_batch_ex(const int64_t *offsets, const uint32_t *succ, const void *weight,
-                           void *rank, int32_t k, const lr_opts *opts, lr_stream stream) {
+static lr_status rank_batch_impl(const int64_t *offsets, const uint32_t *succ, const void *weight,
+                                 void *rank, int32_t k, const lr_outputs *outs, const lr_opts *opts,
+                                 lr_stream stream) {
   lr_opts d;
   if (!opts) { lr_opts_default(&d); if (weight) { d.wtype = LR_I64; d.rtype = LR_I64; } opts = &d; }
   if (k < 0 || (k > 0 && !offsets)) return LR_ERR_INVALID_ARGUMENT;
@@ -750,7 +813,19 @@ lr_status lr_rank_batch_ex(const int64_t *offsets, const uint32_t *succ, const v
   in.sync = opts->sync;
   in.ws = opts->workspace;
   in.ws_bytes = opts->ws_bytes;
+  set_outputs(in, outs);
   return run(in, opts->tuning, s);
+}
+
+lr_status lr_rank_batch_ex(const int64_t *offsets, const uint32_t *succ, const void *weight,
+                           void *rank, int32_t k, const lr_opts *opts, lr_stream stream) {
+  return rank_batch_impl(offsets, succ, weight, rank, k, nullptr, opts, stream);
+}
+
+lr_status lr_rank_batch_outputs(const int64_t *offsets, const uint32_t *succ, const void *weight,
+                                void *rank, int32_t k, const lr_outputs *outs, const lr_opts *opts,
+                                lr_stream stream) {
+  return rank_batch_impl(offsets, succ, weight, rank, k, outs, opts, stream);
 }
 
 lr_status lr_rank_batch(const int64_t *offsets, const uint32_t *succ, const void *weight,
@@ -809,6 +884,11 @@ static lr_status rank_host_impl(const uint32_t *succ_host, const void *weight_ho
 }
 
 size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts) {
+  return lr_workspace_size_outputs(n_total, k, nullptr, opts);
+}
+
+size_t lr_workspace_size_outputs(int64_t n_total, int32_t k, const lr_outputs *outs,
+                                 const lr_opts *opts) {
   lr_opts d;
   if (!opts) { lr_opts_default(&d); opts = &d; }
   if (n_total <= 0) return 0;
@@ -823,10 +903,12 @@ size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts) {
     return wyllie_plan((uint64_t)n_total, wyllie_w16(in)).bytes;
   }
   const uint64_t h = opts->max_lists > 0 ? (uint64_t)opts->max_lists : (uint64_t)n_total;
-  const bool log0 = u.logmode && k == 0 && opts->wtype == LR_NONE && opts->rtype == LR_I32 &&
+  const bool extras = outs && (outs->term || outs->prefix || outs->inclusive_tail);
+  const bool log0 = u.logmode && !extras && k == 0 && opts->wtype == LR_NONE && opts->rtype == LR_I32 &&
                     (uint64_t)n_total > u.cutoff && n_total <= ((int64_t)1 << 30);
   Plan p = make_plan((uint64_t)n_total, h, u, opts->wtype != LR_NONE,
-                     opts->rtype == LR_I64 ? 8 : 4, opts->seed, 256 * 16, false, log0);
+                     opts->rtype == LR_I64 ? 8 : 4, opts->seed, 256 * 16, false, log0, extras,
+                     extras && !outs->term);
   return p.fixed_bytes + p.var_bytes;
 }
 

@@ -34,6 +34,8 @@ struct Plan {
   // variable part
   size_t off_work[kMaxLevels + 1], off_R[kMaxLevels + 1];
   size_t off_hA, off_hB, off_ns, off_pd[4];
+  bool term;                        // terminal ids carried through the levels
+  size_t off_T[kMaxLevels + 1], off_tid[kMaxLevels + 1], off_T0, off_hC, off_pdt[2];
   size_t off_log, off_hdr, off_pairs, off_pairsB, off_hist, off_histB;   // log path
   uint32_t per_cta, total_chunks, shift;
   int part_ctas;
@@ -54,8 +56,11 @@ struct Ctx {
 };
 
 Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted);
+// term: also lay out the terminal-id arrays of every level; t0ws: and the
+// level-0 terminal ids (when the caller does not receive them).
 Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,
-               uint64_t seed, int chase_grid, bool force_srs, bool log0);
+               uint64_t seed, int chase_grid, bool force_srs, bool log0, bool term = false,
+               bool t0ws = false);
 int chase_grid_for(const Tuning &u, bool rec16, bool log0);
 Ctx *get_ctx(cudaStream_t stream, lr_status *st);
 // Forget the context of a stream that is about to be destroyed (waits for

@@ -480,10 +480,14 @@ __device__ __forceinline__ Rec visit(Rec *p, uint32_t cid, uint64_t off) {
   }
 }
 
-template <class Rec, bool XCHG>
+// TERM: a ruler whose segment ends at a terminal y becomes a terminal of the
+// next level; it records y's original id (y itself at level 0, tid_cur[y]
+// deeper) in tid_next, so the terminal of every element can be carried back.
+template <class Rec, bool XCHG, bool TERM>
 __global__ void __launch_bounds__(512)
 k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__restrict__ next,
-        const uint32_t *__restrict__ ns, uint32_t *__restrict__ qctr, uint32_t *__restrict__ err) {
+        const uint32_t *__restrict__ ns, uint32_t *__restrict__ qctr, uint32_t *__restrict__ err,
+        const uint32_t *__restrict__ tid_cur, uint32_t *__restrict__ tid_next) {
   const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
   const uint32_t n = d.n, r = d.r;
@@ -504,6 +508,7 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
     uint32_t steps = 1, nxt = c;
     bad |= rec_tag(v) != kUnvisited;
     uint32_t y = rec_succ(v);
+    uint32_t tend = (TERM && y == rho && rec_tag(v) == kUnvisited) ? rho : kEnd;
     if (y != rho && rec_tag(v) == kUnvisited) {
       for (;;) {
         if (y >= n) { bad |= 4u; break; }   // never produced by prep or a chase
@@ -518,13 +523,19 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
         if (rec_tag(v) != kUnvisited) { bad |= 1u; break; }   // second predecessor
         o += rec_weight(v, y);
         const uint32_t s = rec_succ(v);
-        if (s == y) break;           // terminal: the reduced element is terminal too
+        if (s == y) {                // terminal: the reduced element is terminal too
+          if constexpr (TERM) tend = y;
+          break;
+        }
         if (steps > n) { bad |= 2u; break; }
         y = s;
       }
     }
     __stcg(reinterpret_cast<uint4 *>(next + c),
            make_uint4(nxt, kUnvisited, (uint32_t)o, (uint32_t)(o >> 32)));
+    if constexpr (TERM) {
+      if (tend != kEnd) tid_next[c] = tid_cur ? __ldcg(tid_cur + tend) : tend;
+    }
     visited += steps;
     c64 = cnext;
   }
@@ -537,24 +548,25 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
 
 cudaError_t launch_chase(LevelDesc *desc, int lev, void *work, bool rec16, void *next_work,
                          const uint32_t *ns, uint32_t *qctr, int grid, int block, uint32_t *err,
-                         int xchg, cudaStream_t s) {
+                         int xchg, const uint32_t *tid_cur, uint32_t *tid_next, cudaStream_t s) {
   Rec16 *nx = reinterpret_cast<Rec16 *>(next_work);
-  if (rec16 && xchg)
-    k_chase<Rec16, true><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<Rec16 *>(work), nx, ns, qctr, err);
-  else if (rec16)
-    k_chase<Rec16, false><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<Rec16 *>(work), nx, ns, qctr, err);
-  else if (xchg)
-    k_chase<Rec8, true><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<Rec8 *>(work), nx, ns, qctr, err);
-  else
-    k_chase<Rec8, false><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<Rec8 *>(work), nx, ns, qctr, err);
+#define LR_CHASE(REC, X, T)                                                                          k_chase<REC, X, T><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<REC *>(work), nx, ns, qctr,                                             err, tid_cur, tid_next)
+  if (tid_next) {
+    if (rec16) { if (xchg) LR_CHASE(Rec16, true, true); else LR_CHASE(Rec16, false, true); }
+    else { if (xchg) LR_CHASE(Rec8, true, true); else LR_CHASE(Rec8, false, true); }
+  } else {
+    if (rec16) { if (xchg) LR_CHASE(Rec16, true, false); else LR_CHASE(Rec16, false, false); }
+    else { if (xchg) LR_CHASE(Rec8, true, false); else LR_CHASE(Rec8, false, false); }
+  }
+#undef LR_CHASE
   count_launch();
   return cudaGetLastError();
 }
 
 int chase_occupancy(bool rec16, int block) {
   int nb = 0;
-  if (rec16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chase<Rec16, false>, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chase<Rec8, false>, block, 0);
+  if (rec16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chase<Rec16, false, false>, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chase<Rec8, false, false>, block, 0);
   return nb > 0 ? nb : 1;
 }
 
@@ -568,11 +580,23 @@ __device__ __forceinline__ RT propagate(uint32_t c, uint64_t o, uint32_t nn, con
   return (RT)(base - (RT)o);
 }
 
-// Ruler propagation: every element gets its ruler's rank minus its offset.
-template <class Rec, class RT>
+// Terminal of element i at this level: its ruler's, or its own original id
+// for a resolved singleton (a head that is its own terminal).
+__device__ __forceinline__ uint32_t propagate_term(uint32_t c, uint32_t i, uint32_t nn,
+                                                   const uint32_t *tnext, const uint32_t *tid_cur) {
+  if (c < nn) return __ldcg(tnext + c);
+  if (c == kZeroCid) return tid_cur ? __ldcg(tid_cur + i) : i;
+  return kEnd;
+}
+
+// Ruler propagation: every element gets its ruler's rank minus its offset
+// (TERM: and its ruler's terminal).
+template <class Rec, class RT, bool TERM>
 __global__ void __launch_bounds__(256)
 k_finalize(const LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ work,
-           const RT *__restrict__ rnext, RT *__restrict__ rout, uint32_t *__restrict__ err, int vec) {
+           const RT *__restrict__ rnext, RT *__restrict__ rout, uint32_t *__restrict__ err, int vec,
+           const uint32_t *__restrict__ tnext, uint32_t *__restrict__ tout,
+           const uint32_t *__restrict__ tid_cur) {
   const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
   const uint32_t n = d.n, nn = desc[lev + 1].n;
@@ -584,6 +608,7 @@ k_finalize(const LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ 
     const uint32_t i0 = g * 4u;
     const uint32_t cnt = min(4u, n - i0);
     RT out[4];
+    uint32_t cid[4] = {kEnd, kEnd, kEnd, kEnd};
     if constexpr (sizeof(Rec) == 8) {
       if (cnt == 4u) {
         const uint4 *p = reinterpret_cast<const uint4 *>(work + i0);
@@ -592,17 +617,26 @@ k_finalize(const LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ 
         out[1] = propagate<RT>(a.w, a.z, nn, rnext, bad);
         out[2] = propagate<RT>(b.y, b.x, nn, rnext, bad);
         out[3] = propagate<RT>(b.w, b.z, nn, rnext, bad);
+        if constexpr (TERM) { cid[0] = a.y; cid[1] = a.w; cid[2] = b.y; cid[3] = b.w; }
       } else {
         for (uint32_t j = 0; j < cnt; ++j) {
           Rec v = ld_rec(work + i0 + j);
           out[j] = propagate<RT>(done_cid(v), done_off(v), nn, rnext, bad);
+          if constexpr (TERM) cid[j] = done_cid(v);
         }
       }
     } else {
       for (uint32_t j = 0; j < cnt; ++j) {
         uint4 a = __ldcs(reinterpret_cast<const uint4 *>(work + i0 + j));
         out[j] = propagate<RT>(a.y, ((uint64_t)a.w << 32) | a.z, nn, rnext, bad);
+        if constexpr (TERM) cid[j] = a.y;
       }
+    }
+    if constexpr (TERM) {
+      uint32_t t[4];
+      for (uint32_t j = 0; j < 4u; ++j) t[j] = j < cnt ? propagate_term(cid[j], i0 + j, nn, tnext, tid_cur) : 0u;
+      if (vec && cnt == 4u) __stcs(reinterpret_cast<uint4 *>(tout + i0), make_uint4(t[0], t[1], t[2], t[3]));
+      else for (uint32_t j = 0; j < cnt; ++j) tout[i0 + j] = t[j];
     }
     if (vec && cnt == 4u) {
       if constexpr (sizeof(RT) == 4) {
@@ -661,18 +695,97 @@ cudaError_t launch_finalize_ptrs(LevelDesc *desc, const void *work, bool rec16, 
 
 cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec16,
                             const void *rnext, void *rout, int rank_bytes, uint32_t cap,
-                            uint32_t *err, cudaStream_t s) {
+                            uint32_t *err, const uint32_t *tnext, uint32_t *tout,
+                            const uint32_t *tid_cur, cudaStream_t s) {
   const int block = 256;
   const int grid = stream_grid(((uint64_t)cap + 3) / 4, block);
-  const int vec = ((uintptr_t)rout & 15u) == 0;
-#define LR_FIN(REC, RT)                                                                     \
-  k_finalize<REC, RT><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<const REC *>(work), \
-                                             reinterpret_cast<const RT *>(rnext),            \
-                                             reinterpret_cast<RT *>(rout), err, vec)
-  if (rec16) { if (rank_bytes == 4) LR_FIN(Rec16, uint32_t); else LR_FIN(Rec16, unsigned long long); }
-  else { if (rank_bytes == 4) LR_FIN(Rec8, uint32_t); else LR_FIN(Rec8, unsigned long long); }
+  const int vec = ((uintptr_t)rout & 15u) == 0 && ((uintptr_t)tout & 15u) == 0;
+#define LR_FIN(REC, RT, T)                                                                      \
+  k_finalize<REC, RT, T><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<const REC *>(work), \
+                                                reinterpret_cast<const RT *>(rnext),            \
+                                                reinterpret_cast<RT *>(rout), err, vec, tnext,  \
+                                                tout, tid_cur)
+  if (tout) {
+    if (rec16) { if (rank_bytes == 4) LR_FIN(Rec16, uint32_t, true); else LR_FIN(Rec16, unsigned long long, true); }
+    else { if (rank_bytes == 4) LR_FIN(Rec8, uint32_t, true); else LR_FIN(Rec8, unsigned long long, true); }
+  } else {
+    if (rec16) { if (rank_bytes == 4) LR_FIN(Rec16, uint32_t, false); else LR_FIN(Rec16, unsigned long long, false); }
+    else { if (rank_bytes == 4) LR_FIN(Rec8, uint32_t, false); else LR_FIN(Rec8, unsigned long long, false); }
+  }
 #undef LR_FIN
   count_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- extra outputs (level 0)
+// The paper's output also names each element's terminal (Section 1.1) and
+// its in-place form counts the terminal's own weight; the head-relative
+// (prefix) rank is the list's total minus the rank.  term[] holds global
+// terminal ids when these passes run.
+//
+// Head pass: the total of each list (the rank of its head) is stored at its
+// terminal's entry of prefix.
+template <class RT>
+__global__ void __launch_bounds__(kHeadThreads)
+k_out_heads(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ bitmap,
+            const uint32_t *__restrict__ hlist, const uint32_t *__restrict__ term,
+            const RT *__restrict__ rank, RT *__restrict__ prefix) {
+  const LevelDesc d = desc[0];
+  for_each_head(d, bitmap, hlist, [&](uint32_t h) {
+    const uint32_t t = __ldcg(term + h);
+    if (t < d.n) prefix[t] = __ldcg(rank + h);
+  });
+}
+
+// Streaming pass: prefix[i] = total - rank[i] (a terminal's entry holds the
+// total and keeps it, its rank being 0, so the pass may run in place); the
+// inclusive form adds the terminal's weight (1 when unweighted); in the
+// batched form terminal ids become local to their instance.
+template <class RT>
+__global__ void __launch_bounds__(256)
+k_out_fix(uint32_t n, uint32_t *__restrict__ term, RT *__restrict__ rank, RT *__restrict__ prefix,
+          int incl, const void *__restrict__ weight, int wtype, const int64_t *__restrict__ offsets,
+          int32_t k, int local) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t t = term[i];
+    if (t >= n) continue;                       // an error the device already recorded
+    const RT r = rank[i];
+    if (prefix) prefix[i] = (RT)(__ldcg(prefix + t) - r);
+    if (incl) {
+      uint64_t wt = 1u;
+      if (wtype == 1) wt = (uint64_t)(int64_t)__ldg(reinterpret_cast<const int *>(weight) + t);
+      else if (wtype == 2) wt = (uint64_t)__ldg(reinterpret_cast<const long long *>(weight) + t);
+      rank[i] = (RT)(r + (RT)wt);
+    }
+    if (local) {
+      int32_t lo = 0, hi = k;
+      while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if ((uint64_t)__ldg(offsets + mid) <= i) lo = mid; else hi = mid;
+      }
+      term[i] = (uint32_t)(t - (uint64_t)__ldg(offsets + lo));
+    }
+  }
+}
+
+cudaError_t launch_outputs(const LevelDesc *desc, const uint32_t *bitmap, const uint32_t *hlist0,
+                           uint32_t n, uint32_t *term, void *rank, void *prefix, int rank_bytes,
+                           int incl, const void *weight, int wtype, const int64_t *offsets, int32_t k,
+                           int local, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int grid = stream_grid(n, 256);
+  int launches = 0;
+  if (rank_bytes == 4) {
+    uint32_t *r = reinterpret_cast<uint32_t *>(rank), *p = reinterpret_cast<uint32_t *>(prefix);
+    if (p) { k_out_heads<uint32_t><<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, bitmap, hlist0, term, r, p); ++launches; }
+    if (p || incl || local) { k_out_fix<uint32_t><<<grid, 256, 0, s>>>(n, term, r, p, incl, weight, wtype, offsets, k, local); ++launches; }
+  } else {
+    unsigned long long *r = reinterpret_cast<unsigned long long *>(rank);
+    unsigned long long *p = reinterpret_cast<unsigned long long *>(prefix);
+    if (p) { k_out_heads<unsigned long long><<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, bitmap, hlist0, term, r, p); ++launches; }
+    if (p || incl || local) { k_out_fix<unsigned long long><<<grid, 256, 0, s>>>(n, term, r, p, incl, weight, wtype, offsets, k, local); ++launches; }
+  }
+  count_launch(launches);
   return cudaGetLastError();
 }
 
@@ -682,44 +795,62 @@ cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec
 // successor's successor, reading the old values before anyone writes.
 // Values are inclusive (a terminal starts with its own weight), so after
 // ceil(log2 n) rounds val[i] is the rank of i at this level.
+// With tout, term[] follows the same rounds: a terminal starts with its
+// original id (tid, or its own index at level 0) and every other element
+// with kEnd; an element takes its successor's entry, which is known exactly
+// when that successor has reached the end, i.e. when the element does.
 template <class Rec, class RT>
 __global__ void __launch_bounds__(kBaseThreads)
 k_base(LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ work, RT *__restrict__ rout,
-       uint32_t *__restrict__ err) {
+       uint32_t *__restrict__ err, const uint32_t *__restrict__ tid, uint32_t *__restrict__ tout) {
   extern __shared__ unsigned char smem_raw[];
   LevelDesc &d = desc[lev];
   if (d.mode != kModeBase) return;
   const uint32_t n = d.n;
+  const bool with_term = tout != nullptr;
   uint32_t *nxt = reinterpret_cast<uint32_t *>(smem_raw);
   RT *val = reinterpret_cast<RT *>(smem_raw + ((kMaxCutoff * 4 + 15) & ~15));
+  uint32_t *term = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(val) + (size_t)kMaxCutoff * sizeof(RT));
   constexpr int PER = (kMaxCutoff + kBaseThreads - 1) / kBaseThreads;
   for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
     Rec v = ld_rec(work + j);
     const uint32_t s = rec_succ(v);
     nxt[j] = (s == j || s >= n) ? kEnd : s;
     val[j] = (RT)rec_weight(v, j);
+    if (with_term) term[j] = s == j ? (tid ? __ldcg(tid + j) : j) : kEnd;
     if (s >= n) record_error(err, kErrInternal);
   }
   __syncthreads();
   uint32_t rounds = 0;
   while ((1ull << rounds) < n) ++rounds;
   for (uint32_t it = 0; it < rounds; ++it) {
-    uint32_t tn[PER];
+    uint32_t tn[PER], tt[PER];
     RT tv[PER];
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
       const uint32_t j = threadIdx.x + e * kBaseThreads;
       if (j < n) {
         const uint32_t a = nxt[j];
-        if (a != kEnd) { tv[e] = val[j] + val[a]; tn[e] = nxt[a]; }
-        else { tv[e] = val[j]; tn[e] = kEnd; }
+        if (a != kEnd) {
+          tv[e] = val[j] + val[a];
+          tn[e] = nxt[a];
+          tt[e] = with_term ? term[a] : 0u;
+        } else {
+          tv[e] = val[j];
+          tn[e] = kEnd;
+          tt[e] = with_term ? term[j] : 0u;
+        }
       }
     }
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
       const uint32_t j = threadIdx.x + e * kBaseThreads;
-      if (j < n) { nxt[j] = tn[e]; val[j] = tv[e]; }
+      if (j < n) {
+        nxt[j] = tn[e];
+        val[j] = tv[e];
+        if (with_term) term[j] = tt[e];
+      }
     }
     __syncthreads();
   }
@@ -727,22 +858,25 @@ k_base(LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ work, RT *
   for (uint32_t j = threadIdx.x; j < n; j += blockDim.x) {
     if (nxt[j] != kEnd) bad = 1;
     rout[j] = val[j];
+    if (with_term) tout[j] = term[j];
   }
   if (bad) record_error(err, kErrCycle);
   if (threadIdx.x == 0) d.visited = n;
 }
 
 static size_t base_smem(int rank_bytes) {
-  return ((kMaxCutoff * 4 + 15) & ~15) + (size_t)kMaxCutoff * rank_bytes;
+  // nxt, val and the terminal ids of up to kMaxCutoff elements
+  return ((kMaxCutoff * 4 + 15) & ~15) + (size_t)kMaxCutoff * rank_bytes + (size_t)kMaxCutoff * 4;
 }
 
 cudaError_t launch_base(LevelDesc *desc, int lev, const void *work, bool rec16, void *rout,
-                        int rank_bytes, uint32_t cutoff, uint32_t *err, cudaStream_t s) {
+                        int rank_bytes, uint32_t cutoff, uint32_t *err, const uint32_t *tid,
+                        uint32_t *tout, cudaStream_t s) {
   (void)cutoff;
   const size_t sm = base_smem(rank_bytes);
 #define LR_BASE(REC, RT)                                                                         \
   k_base<REC, RT><<<1, kBaseThreads, sm, s>>>(desc, lev, reinterpret_cast<const REC *>(work), \
-                                              reinterpret_cast<RT *>(rout), err)
+                                              reinterpret_cast<RT *>(rout), err, tid, tout)
   if (rec16) { if (rank_bytes == 4) LR_BASE(Rec16, uint32_t); else LR_BASE(Rec16, unsigned long long); }
   else { if (rank_bytes == 4) LR_BASE(Rec8, uint32_t); else LR_BASE(Rec8, unsigned long long); }
 #undef LR_BASE
@@ -754,38 +888,52 @@ cudaError_t launch_base(LevelDesc *desc, int lev, const void *work, bool rec16, 
 // Fallback base case for a last level larger than one CTA can hold (many
 // lists whose heads keep the levels from shrinking).  Same rounds as the
 // single-CTA version, one kernel per round, ping-pong buffers.
+// With term arrays (t0/t1 non-null) the terminal ids follow the rounds as in
+// the single-CTA base case.
 __global__ void k_pd_init(const LevelDesc *__restrict__ desc, int lev, const Rec16 *__restrict__ work,
-                          uint32_t *__restrict__ nxt, uint64_t *__restrict__ val) {
+                          uint32_t *__restrict__ nxt, uint64_t *__restrict__ val,
+                          const uint32_t *__restrict__ tid, uint32_t *__restrict__ term) {
   const LevelDesc d = desc[lev];
   if (d.mode != kModePd) return;
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) {
     Rec16 v = ld_rec(work + j);
     nxt[j] = (v.succ == j || v.succ >= d.n) ? kEnd : v.succ;
     val[j] = v.w;
+    if (term) term[j] = v.succ == j ? (tid ? __ldcg(tid + j) : j) : kEnd;
   }
 }
 
 __global__ void k_pd_round(const LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ nin,
                            const uint64_t *__restrict__ vin, uint32_t *__restrict__ nout,
-                           uint64_t *__restrict__ vout) {
+                           uint64_t *__restrict__ vout, const uint32_t *__restrict__ tin,
+                           uint32_t *__restrict__ tout) {
   const LevelDesc d = desc[lev];
   if (d.mode != kModePd) return;
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) {
     const uint32_t a = nin[j];
-    if (a != kEnd) { vout[j] = vin[j] + vin[a]; nout[j] = nin[a]; }
-    else { vout[j] = vin[j]; nout[j] = kEnd; }
+    if (a != kEnd) {
+      vout[j] = vin[j] + vin[a];
+      nout[j] = nin[a];
+      if (tout) tout[j] = tin[a];
+    } else {
+      vout[j] = vin[j];
+      nout[j] = kEnd;
+      if (tout) tout[j] = tin[j];
+    }
   }
 }
 
 template <class RT>
 __global__ void k_pd_out(LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ nxt,
-                         const uint64_t *__restrict__ val, RT *__restrict__ rout, uint32_t *__restrict__ err) {
+                         const uint64_t *__restrict__ val, RT *__restrict__ rout, uint32_t *__restrict__ err,
+                         const uint32_t *__restrict__ term, uint32_t *__restrict__ tout) {
   const LevelDesc d = desc[lev];
   if (d.mode != kModePd) return;
   uint32_t bad = 0;
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < d.n; j += gridDim.x * blockDim.x) {
     bad |= nxt[j] != kEnd;
     rout[j] = (RT)val[j];
+    if (tout) tout[j] = term[j];
   }
   if (bad) record_error(err, kErrCycle);
   if (blockIdx.x == 0 && threadIdx.x == 0) desc[lev].visited = d.n;
@@ -793,22 +941,27 @@ __global__ void k_pd_out(LevelDesc *__restrict__ desc, int lev, const uint32_t *
 
 cudaError_t launch_pd(LevelDesc *desc, int lev, const void *work, uint32_t cap, uint32_t rounds,
                       uint32_t *nxt0, uint32_t *nxt1, uint64_t *val0, uint64_t *val1, void *rout,
-                      int rank_bytes, uint32_t *err, cudaStream_t s) {
+                      int rank_bytes, uint32_t *err, const uint32_t *tid, uint32_t *t0, uint32_t *t1,
+                      uint32_t *tout, cudaStream_t s) {
   const int block = 256;
   const int grid = stream_grid(cap, block);
-  k_pd_init<<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<const Rec16 *>(work), nxt0, val0);
-  uint32_t *na = nxt0, *nb = nxt1;
+  if (!tout) t0 = t1 = nullptr;
+  k_pd_init<<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<const Rec16 *>(work), nxt0, val0, tid, t0);
+  uint32_t *na = nxt0, *nb = nxt1, *ta = t0, *tb = t1;
   uint64_t *va = val0, *vb = val1;
   for (uint32_t it = 0; it < rounds; ++it) {
-    k_pd_round<<<grid, block, 0, s>>>(desc, lev, na, va, nb, vb);
+    k_pd_round<<<grid, block, 0, s>>>(desc, lev, na, va, nb, vb, ta, tb);
     uint32_t *tn = na; na = nb; nb = tn;
     uint64_t *tv = va; va = vb; vb = tv;
+    uint32_t *tt = ta; ta = tb; tb = tt;
   }
   if (rank_bytes == 4)
-    k_pd_out<uint32_t><<<grid, block, 0, s>>>(desc, lev, na, va, reinterpret_cast<uint32_t *>(rout), err);
+    k_pd_out<uint32_t><<<grid, block, 0, s>>>(desc, lev, na, va, reinterpret_cast<uint32_t *>(rout), err,
+                                              ta, tout);
   else
     k_pd_out<unsigned long long><<<grid, block, 0, s>>>(desc, lev, na, va,
-                                                        reinterpret_cast<unsigned long long *>(rout), err);
+                                                        reinterpret_cast<unsigned long long *>(rout), err,
+                                                        ta, tout);
   count_launch(2 + (int)rounds);
   return cudaGetLastError();
 }

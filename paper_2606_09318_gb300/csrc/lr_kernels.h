@@ -56,16 +56,28 @@ cudaError_t launch_heads(LevelDesc *desc, int lev, int nlev, const uint32_t *bit
                          uint32_t *hnext, uint64_t *blockcnt, uint32_t *err, uint32_t cutoff,
                          uint32_t hcap, uint32_t has_pd, cudaStream_t s);
 
+// Terminal ids (all optional; null when the call does not ask for them):
+// tid_cur/tid_next hold the original id of each terminal of this/the next
+// level (written by the chase), tout/tnext the terminal of every element.
 cudaError_t launch_chase(LevelDesc *desc, int lev, void *work, bool rec16, void *next_work,
                          const uint32_t *ns, uint32_t *qctr, int grid, int block, uint32_t *err,
-                         int xchg, cudaStream_t s);
+                         int xchg, const uint32_t *tid_cur, uint32_t *tid_next, cudaStream_t s);
 
 cudaError_t launch_base(LevelDesc *desc, int lev, const void *work, bool rec16, void *rout,
-                        int rank_bytes, uint32_t cutoff, uint32_t *err, cudaStream_t s);
+                        int rank_bytes, uint32_t cutoff, uint32_t *err, const uint32_t *tid,
+                        uint32_t *tout, cudaStream_t s);
 
 cudaError_t launch_pd(LevelDesc *desc, int lev, const void *work, uint32_t cap, uint32_t rounds,
                       uint32_t *nxt0, uint32_t *nxt1, uint64_t *val0, uint64_t *val1, void *rout,
-                      int rank_bytes, uint32_t *err, cudaStream_t s);
+                      int rank_bytes, uint32_t *err, const uint32_t *tid, uint32_t *t0, uint32_t *t1,
+                      uint32_t *tout, cudaStream_t s);
+
+// Level-0 extra outputs after the ranks and terminal ids are written:
+// prefix (head-relative) ranks, the inclusive-tail form, local terminal ids.
+cudaError_t launch_outputs(const LevelDesc *desc, const uint32_t *bitmap, const uint32_t *hlist0,
+                           uint32_t n, uint32_t *term, void *rank, void *prefix, int rank_bytes,
+                           int incl, const void *weight, int wtype, const int64_t *offsets, int32_t k,
+                           int local, cudaStream_t s);
 
 // Whole-list Wyllie pointer doubling (lr_wyllie.cu).  bufA holds k_prep0's
 // records (8 B, or 16 B when weighted: w16), bufB the same size; ranks go
@@ -76,7 +88,8 @@ cudaError_t launch_wyllie(void *bufA, void *bufB, bool w16, uint32_t n, void *ra
 
 cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec16,
                             const void *rnext, void *rout, int rank_bytes, uint32_t cap,
-                            uint32_t *err, cudaStream_t s);
+                            uint32_t *err, const uint32_t *tnext, uint32_t *tout,
+                            const uint32_t *tid_cur, cudaStream_t s);
 
 // Log path (unweighted level 0, see lr_log.cu).
 cudaError_t launch_sum0(const uint32_t *succ, uint32_t n, unsigned long long *acc, uint32_t *err,
