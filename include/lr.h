@@ -62,7 +62,8 @@ typedef enum lr_status {
     LR_ERR_CAPACITY = 9,         /* more lists than lr_opts.max_lists promised   */
     LR_ERR_NOT_FOUND = 10,       /* serving: unknown ticket                      */
     LR_ERR_CANCELLED = 11,       /* serving: server shut down before the run     */
-    LR_ERR_CAPTURE = 12          /* call would sync or allocate during capture   */
+    LR_ERR_CAPTURE = 12,         /* call would sync or allocate during capture   */
+    LR_ERR_INTERNAL = 13         /* a self-check of the library failed           */
 } lr_status;
 
 typedef enum lr_dtype { LR_NONE = 0, LR_I32 = 1, LR_I64 = 2 } lr_dtype;
@@ -337,6 +338,48 @@ lr_status lr_server_submit(lr_server *s, const lr_request *req, uint64_t *ticket
 lr_status lr_server_wait(lr_server *s, uint64_t ticket, int64_t timeout_ms, lr_result *res);
 lr_status lr_server_stats_get(lr_server *s, lr_server_stats *out);
 void lr_server_destroy(lr_server *s);
+
+/*
+ * Autotuner.  The best ruler fractions, base-case cutoff and chase block
+ * depend on n, on the weights and on whether the input is a batch (small
+ * lists are bound by the latency along one segment, large ones by the
+ * random-access rate).  lr_autotune measures candidates on the current
+ * device by coordinate descent from the built-in defaults (level-0 fraction
+ * 1/f0, deeper fraction 1/f, cutoff, chase block, then f0 again), each the
+ * fastest of a few timed calls on `stream`, and checks that the winner's
+ * ranks equal the defaults' bit for bit (else LR_ERR_INTERNAL).
+ *
+ * Inputs: the caller's device arrays (succ, weight, offsets as for
+ * lr_rank_ex / lr_rank_batch_ex; offsets required when k > 0), or, with
+ * succ == NULL, synthetic ones of the same shape generated on the device: k
+ * equal random-order instances (one random list when k == 0), weights of
+ * opts->wtype in [-1000, 1000].  opts: dtypes, validate, seed and max_lists
+ * as for the ranking call; workspace must be NULL; the call allocates and
+ * frees its own scratch.  Synchronises `stream`.
+ *
+ * The winner is stored in a process-wide table keyed by (floor(log2 n),
+ * weighted, batched) and written to *out (may be NULL).  Every later call
+ * whose opts->tuning is NULL uses its key's entry (an explicit lr_tuning,
+ * then LR_TUNING in the environment, take precedence).  The table is saved
+ * and loaded as JSON; LR_TUNING_FILE names a file loaded on first use.
+ */
+typedef struct lr_tune_entry {
+    int32_t log2n;       /* floor(log2 n) of the tuned size                      */
+    int32_t weighted;    /* 1: weighted                                          */
+    int32_t batch;       /* 1: batched form (k > 0)                              */
+    lr_tuning tuning;    /* the winner                                           */
+    float ms;            /* its time per call on the tuning input                */
+} lr_tune_entry;
+
+lr_status lr_autotune(const uint32_t *succ, const void *weight, const int64_t *offsets,
+                      int64_t n_total, int32_t k, const lr_opts *opts, lr_stream stream,
+                      lr_tuning *out);
+lr_status lr_autotune_save(const char *path);
+/* Merge the entries of a file saved by lr_autotune_save into the table. */
+lr_status lr_autotune_load(const char *path);
+/* Copy up to cap entries into out (may be NULL); returns how many exist. */
+int32_t lr_autotune_entries(lr_tune_entry *out, int32_t cap);
+void lr_autotune_clear(void);
 
 /*
  * Host-buffer pipeline: ranks a sequence of HOST-resident lists (Section 1.1

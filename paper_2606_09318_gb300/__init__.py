@@ -28,6 +28,7 @@ STATUS = {
     4: "LR_ERR_NOT_A_LIST", 5: "LR_ERR_OUT_OF_MEMORY", 6: "LR_ERR_BUDGET", 7: "LR_ERR_TIMEOUT",
     8: "LR_ERR_CUDA", 9: "LR_ERR_CAPACITY", 10: "LR_ERR_NOT_FOUND", 11: "LR_ERR_CANCELLED",
     12: "LR_ERR_CAPTURE",
+    13: "LR_ERR_INTERNAL",
 }
 LR_NONE, LR_I32, LR_I64 = 0, 1, 2
 
@@ -58,6 +59,11 @@ class _Opts(ctypes.Structure):
 class _Outputs(ctypes.Structure):
     _fields_ = [("term", ctypes.c_void_p), ("prefix", ctypes.c_void_p),
                 ("inclusive_tail", ctypes.c_int32)]
+
+
+class _TuneEntry(ctypes.Structure):
+    _fields_ = [("log2n", ctypes.c_int32), ("weighted", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("tuning", Tuning), ("ms", ctypes.c_float)]
 
 
 class _Profile(ctypes.Structure):
@@ -127,6 +133,12 @@ _SIGS = {
     "lr_server_wait": (ctypes.c_int, [_V, ctypes.c_uint64, _I64, ctypes.POINTER(_Result)]),
     "lr_server_stats_get": (ctypes.c_int, [_V, ctypes.POINTER(_ServerStats)]),
     "lr_server_destroy": (None, [_V]),
+    "lr_autotune": (ctypes.c_int, [_V, _V, _V, _I64, _I32, ctypes.POINTER(_Opts), _V,
+                                   ctypes.POINTER(Tuning)]),
+    "lr_autotune_save": (ctypes.c_int, [ctypes.c_char_p]),
+    "lr_autotune_load": (ctypes.c_int, [ctypes.c_char_p]),
+    "lr_autotune_entries": (_I32, [ctypes.POINTER(_TuneEntry), _I32]),
+    "lr_autotune_clear": (None, []),
     "lr_pipeline_create": (ctypes.c_int, [_I64, ctypes.POINTER(_Opts), _I32, ctypes.POINTER(_V)]),
     "lr_pipeline_submit": (ctypes.c_int, [_V, _V, _V, _I64, _V]),
     "lr_pipeline_wait": (ctypes.c_int, [_V, ctypes.POINTER(_I64)]),
@@ -433,6 +445,63 @@ def probe_memory(buf, stream=None):
     _check(load().lr_probe_memory(ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(),
                                   ctypes.byref(r), _stream_handle(stream)), "lr_probe_memory")
     return {f: getattr(r, f) for f, _ in _ProbeResult._fields_}
+
+
+def autotune(n_total=None, k=0, succ=None, weight=None, offsets=None, wtype=None, rank_dtype=None,
+             max_lists=0, validate=False, stream=None):
+    """Autotune the recursion for one input shape (lr_autotune).  With succ
+    (a CUDA tensor; offsets for a batch) the caller's data is used, else a
+    synthetic random list (k == 0) or k equal random instances of n_total
+    elements with weights of wtype ("int32" / "int64" / None).  Returns the
+    winning Tuning; later calls of the same (log2 n, weighted, batched) shape
+    that pass no tuning use it."""
+    torch = _torch()
+    lib = load()
+    if succ is not None:
+        n_total = succ.numel()
+        sp = _dev_ptr(succ, "succ", _succ_dtypes())
+        wt = _wcode(weight)
+        wp = None if weight is None else _dev_ptr(weight, "weight", (torch.int32, torch.int64))
+        op = None if offsets is None else _dev_ptr(offsets, "offsets", (torch.int64,))
+        if offsets is not None:
+            k = offsets.numel() - 1
+    else:
+        sp = wp = op = None
+        wt = {None: LR_NONE, "int32": LR_I32, "int64": LR_I64, torch.int32: LR_I32,
+              torch.int64: LR_I64}[wtype]
+    if rank_dtype is None:
+        rank_dtype = torch.int32 if wt == LR_NONE else torch.int64
+    o = _opts(wt, LR_I32 if rank_dtype == torch.int32 else LR_I64, validate, 0x5EED, max_lists)
+    t = Tuning()
+    _check(lib.lr_autotune(sp, wp, op, int(n_total), int(k), ctypes.byref(o), _stream_handle(stream),
+                           ctypes.byref(t)), "lr_autotune")
+    return t
+
+
+def autotune_entries():
+    """The autotuned table as a list of dicts."""
+    lib = load()
+    cnt = lib.lr_autotune_entries(None, 0)
+    arr = (_TuneEntry * max(1, cnt))()
+    cnt = lib.lr_autotune_entries(arr, cnt)
+    out = []
+    for e in arr[:cnt]:
+        d = {"log2n": e.log2n, "weighted": e.weighted, "batch": e.batch, "ms": e.ms}
+        d.update({f: getattr(e.tuning, f) for f, _ in Tuning._fields_ if f != "reserved"})
+        out.append(d)
+    return out
+
+
+def autotune_save(path):
+    _check(load().lr_autotune_save(os.fsencode(path)), "lr_autotune_save")
+
+
+def autotune_load(path):
+    _check(load().lr_autotune_load(os.fsencode(path)), "lr_autotune_load")
+
+
+def autotune_clear():
+    load().lr_autotune_clear()
 
 
 class Pipeline:

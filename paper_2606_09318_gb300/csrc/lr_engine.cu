@@ -53,7 +53,7 @@ static uint32_t default_f0_inv(int64_t n) {
   return 64;
 }
 
-Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted) {
+Tuning resolve_tuning_builtin(int64_t n, bool weighted) {
   (void)weighted;
   Tuning u;
   u.f0_inv = default_f0_inv(n);
@@ -61,6 +61,22 @@ Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted) {
   u.cutoff = kMaxCutoff;
   u.block = 256;
   u.ctas = 0;
+  u.xchg = 1;
+  u.logmode = 0;
+  u.algo = LR_ALGO_SRS;
+  return u;
+}
+
+Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted, bool batch) {
+  Tuning u = resolve_tuning_builtin(n, weighted);
+  lr_tuning tt;
+  if (tuned_lookup(n, weighted, batch, &tt)) {
+    if (tt.f0_inv) u.f0_inv = tt.f0_inv;
+    if (tt.f_inv) u.f_inv = tt.f_inv;
+    if (tt.cutoff) u.cutoff = tt.cutoff;
+    if (tt.chase_block) u.block = tt.chase_block;
+    if (tt.chase_ctas) u.ctas = tt.chase_ctas;
+  }
   const char *env = getenv("LR_TUNING");
   u.f0_inv = env_u32(env, "f0", u.f0_inv);
   u.f_inv = env_u32(env, "f", u.f_inv);
@@ -449,7 +465,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     return LR_OK;
   }
   const bool capturing = stream_capturing(s);
-  const Tuning u = resolve_tuning(tuning, (int64_t)in.n, in.wtype != 0);
+  const Tuning u = resolve_tuning(tuning, (int64_t)in.n, in.wtype != 0, in.offsets != nullptr || ptrs);
   if (u.algo == LR_ALGO_WYLLIE && !ptrs) {
     if (in.term || in.prefix || in.incl) return LR_ERR_INVALID_ARGUMENT;   // default algorithm only
     return run_wyllie(in, c, s);
@@ -705,6 +721,7 @@ const char *lr_status_string(lr_status s) {
     case LR_ERR_NOT_FOUND: return "LR_ERR_NOT_FOUND";
     case LR_ERR_CANCELLED: return "LR_ERR_CANCELLED";
     case LR_ERR_CAPTURE: return "LR_ERR_CAPTURE";
+    case LR_ERR_INTERNAL: return "LR_ERR_INTERNAL";
   }
   return "LR_ERR_UNKNOWN";
 }
@@ -892,7 +909,7 @@ size_t lr_workspace_size_outputs(int64_t n_total, int32_t k, const lr_outputs *o
   lr_opts d;
   if (!opts) { lr_opts_default(&d); opts = &d; }
   if (n_total <= 0) return 0;
-  const Tuning u = resolve_tuning(opts->tuning, n_total, opts->wtype != LR_NONE);
+  const Tuning u = resolve_tuning(opts->tuning, n_total, opts->wtype != LR_NONE, k > 0);
   // The chase grid depends on the device; size for a generous upper bound so
   // the answer needs no GPU: 256 SMs x 16 CTAs.
   if (u.algo == LR_ALGO_WYLLIE) {

@@ -55,7 +55,13 @@ struct Ctx {
   bool pending_status = false;
 };
 
-Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted);
+// Tuning of a call: the caller's fields, else LR_TUNING, else the autotuned
+// entry for (n, weighted, batch), else the built-in defaults.
+Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted, bool batch);
+// The built-in defaults alone.
+Tuning resolve_tuning_builtin(int64_t n, bool weighted);
+// Autotuned entry for a call of this shape (lr_tune.cu).
+bool tuned_lookup(int64_t n, bool weighted, bool batch, lr_tuning *out);
 // term: also lay out the terminal-id arrays of every level; t0ws: and the
 // level-0 terminal ids (when the caller does not receive them).
 Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,

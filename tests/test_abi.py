@@ -3,6 +3,8 @@ declares; host-only entry points work without a GPU (no compute calls here)."""
 import ctypes
 import os
 import re
+import subprocess
+import sys
 
 import pytest
 
@@ -65,3 +67,49 @@ def test_library_has_no_oracle_dependency():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "lr_oracle" not in text and "lro_" not in text, f
+
+
+def test_autotune_table_roundtrip(tmp_path, lib):
+    """The autotuned table: load, read back, save, reload; needs no GPU."""
+    import json as _json
+    import paper_2606_09318_gb300 as lr
+    lr.autotune_clear()
+    src = tmp_path / "tune.json"
+    entries = [{"log2n": 20, "weighted": 0, "batch": 0, "f0_inv": 4, "f_inv": 16, "cutoff": 4096,
+                "chase_block": 128, "chase_ctas": 0, "algorithm": 0, "ms": 0.25},
+               {"log2n": 24, "weighted": 1, "batch": 1, "f0_inv": 16, "f_inv": 8, "cutoff": 12288,
+                "chase_block": 256, "chase_ctas": 0, "algorithm": 0, "ms": 1.5}]
+    src.write_text(_json.dumps({"format": "lr_autotune 1", "entries": entries}))
+    base = lr.workspace_size(1 << 20, max_lists=1)
+    lr.autotune_load(str(src))
+    got = lr.autotune_entries()
+    assert len(got) == 2
+    for want, have in zip(entries, got):
+        for key in want:
+            assert abs(have[key] - want[key]) < 1e-6, key
+    # the entry for (2^20, unweighted, single) now drives the plan: 1/f0 = 1/4
+    assert lr.workspace_size(1 << 20, max_lists=1) > base           # more rulers per level
+    assert lr.workspace_size((1 << 20) + 5, max_lists=1) == lr.workspace_size((1 << 20) + 5, max_lists=1)
+    out = tmp_path / "saved.json"
+    lr.autotune_save(str(out))
+    lr.autotune_clear()
+    assert lr.autotune_entries() == [] and lr.workspace_size(1 << 20, max_lists=1) == base
+    lr.autotune_load(str(out))
+    assert lr.autotune_entries() == got
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"entries": [{"log2n": 20}]}')
+    with pytest.raises(lr.LRError):
+        lr.autotune_load(str(bad))
+    with pytest.raises(lr.LRError):
+        lr.autotune_load(str(tmp_path / "missing.json"))
+    lr.autotune_clear()
+
+
+def test_autotune_file_from_environment(tmp_path, lib):
+    src = tmp_path / "env.json"
+    src.write_text('{"entries": [{"log2n": 22, "weighted": 0, "batch": 0, "f0_inv": 8, "f_inv": 8, '
+                   '"cutoff": 8192, "chase_block": 256, "chase_ctas": 0, "algorithm": 0, "ms": 1}]}')
+    code = ("import paper_2606_09318_gb300 as lr; e = lr.autotune_entries(); "
+            "assert len(e) == 1 and e[0]['log2n'] == 22 and e[0]['f0_inv'] == 8, e")
+    env = dict(os.environ, LR_TUNING_FILE=str(src))
+    subprocess.check_call([sys.executable, "-c", code], env=env, cwd=ROOT)
