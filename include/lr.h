@@ -81,8 +81,26 @@ typedef struct lr_tuning {
     uint32_t chase_block;/* threads per CTA of the chase kernel (default 256)    */
     uint32_t chase_ctas; /* CTAs per SM of the chase kernel (default: occupancy) */
     uint32_t algorithm;  /* LR_ALGO_SRS (0, default) or LR_ALGO_WYLLIE            */
-    uint32_t reserved[2];
+    uint32_t contract;   /* tile-local contraction: 0 auto (default),            */
+                         /* LR_CONTRACT_OFF or LR_CONTRACT_ON                     */
+    uint32_t reserved[1];
 } lr_tuning;
+
+/*
+ * Tile-local contraction (Section 2.3, restated for one GPU): before the
+ * ruling set, every maximal sublist inside a tile of 4096 consecutive ids is
+ * contracted in shared memory to one node, the ruling set ranks the list of
+ * those nodes, and a final pass restores every element.  It pays when links
+ * mostly stay inside tiles (locality and identity orders).  Auto (the
+ * default) samples 16384 links first and contracts when at least half stay
+ * inside their tile; it applies to single-instance calls that count their
+ * lists anyway (max_lists == 0, no workspace, not during capture, no extra
+ * outputs, n >= 16384).  LR_CONTRACT_ON skips the sample; LR_CONTRACT_OFF
+ * never contracts.  Results are identical either way.
+ */
+#define LR_CONTRACT_AUTO 0u
+#define LR_CONTRACT_OFF 1u
+#define LR_CONTRACT_ON 2u
 
 /*
  * Algorithms behind lr_tuning.algorithm.  LR_ALGO_WYLLIE is pointer doubling

@@ -43,10 +43,12 @@ class LRError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("f0_inv", ctypes.c_uint32), ("f_inv", ctypes.c_uint32), ("cutoff", ctypes.c_uint32),
                 ("chase_block", ctypes.c_uint32), ("chase_ctas", ctypes.c_uint32),
-                ("algorithm", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
+                ("algorithm", ctypes.c_uint32), ("contract", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 1)]
 
 
 ALGO_SRS, ALGO_WYLLIE = 0, 1
+CONTRACT_AUTO, CONTRACT_OFF, CONTRACT_ON = 0, 1, 2
 
 
 class _Opts(ctypes.Structure):

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblr.so")
-SOURCES = ["lr_kernels.cu", "lr_log.cu", "lr_engine.cu", "lr_server.cu", "lr_noalloc.cu", "lr_probe.cu", "lr_pipeline.cu", "lr_wyllie.cu", "lr_tune.cu"]
+SOURCES = ["lr_kernels.cu", "lr_log.cu", "lr_engine.cu", "lr_server.cu", "lr_noalloc.cu", "lr_probe.cu", "lr_pipeline.cu", "lr_wyllie.cu", "lr_tune.cu", "lr_contract.cu"]
 HEADERS = ["lr_device.cuh", "lr_kernels.h", "lr_engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr",

@@ -64,6 +64,7 @@ Tuning resolve_tuning_builtin(int64_t n, bool weighted) {
   u.xchg = 1;
   u.logmode = 0;
   u.algo = LR_ALGO_SRS;
+  u.contract = LR_CONTRACT_AUTO;
   return u;
 }
 
@@ -86,8 +87,10 @@ Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted, bool batch) 
   u.xchg = env_u32(env, "xchg", 1);
   u.logmode = env_u32(env, "log", 0);
   u.algo = env_u32(env, "algo", LR_ALGO_SRS);
+  u.contract = env_u32(env, "contract", u.contract);
   if (t) {
     if (t->algorithm) u.algo = t->algorithm;
+    if (t->contract) u.contract = t->contract;
     if (t->f0_inv) u.f0_inv = t->f0_inv;
     if (t->f_inv) u.f_inv = t->f_inv;
     if (t->cutoff) u.cutoff = t->cutoff;
@@ -240,6 +243,7 @@ lr_status setup_device_once() {
   if (dev >= 0 && dev < 64 && !g_setup_done[dev]) {
     e = kernels_setup();
     if (e == cudaSuccess) e = log_setup();
+    if (e == cudaSuccess) e = lc_setup();
     if (e != cudaSuccess) return from_cuda(e);
     g_setup_done[dev] = true;
   }
@@ -281,6 +285,8 @@ void release_ctx(cudaStream_t stream) {
   if (c->fixed) cudaFree(c->fixed);
   if (c->var) cudaFree(c->var);
   if (c->hostpath) cudaFree(c->hostpath);
+  if (c->contract) cudaFree(c->contract);
+  if (c->contract2) cudaFree(c->contract2);
   cudaFreeHost(c->host_words);
   delete c;
 }
@@ -341,6 +347,13 @@ struct Profiler {
     std::lock_guard<std::mutex> g(g_mu);
     g_prof_pending.push_back(call);
   }
+  // drop a call that turned out not to happen (its marks are not recorded)
+  void cancel() {
+    if (!on) return;
+    for (auto &m : call.marks) cudaEventDestroy(m.ev);
+    call.marks.clear();
+    on = false;
+  }
 };
 enum { PH_PREP = 0, PH_SELECT, PH_CHASE0, PH_CHASE, PH_BASE, PH_FINAL };
 
@@ -368,6 +381,8 @@ struct Inputs {
   uint32_t *term;                // extra outputs (device, optional): terminal ids,
   void *prefix;                  // head-relative ranks,
   int incl;                      // inclusive-tail ranks
+  uint32_t *err_ext;             // record device errors here (and do not clear it)
+  int no_contract;               // never contract (the contracted list itself)
 };
 
 static lr_status map_device_bits(uint32_t bits) {
@@ -453,6 +468,93 @@ static lr_status run_wyllie(const Inputs &in, Ctx *c, cudaStream_t s) {
   return finish_call(c, err, in.sync, s);
 }
 
+lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s);
+
+// Tile-local contraction (lr_contract.cu) around the ruling set: count the
+// local heads of every tile, build the contracted list, rank it (inclusive
+// form, through run() itself), restore every element.  Returns
+// LR_ERR_NOT_FOUND (nothing enqueued that writes outputs) when the exact
+// count shows that contraction would not shrink the list enough.
+static lr_status run_contracted(const Inputs &in, const lr_tuning *tuning, Ctx *c, bool decided,
+                                cudaStream_t s) {
+  const uint32_t n = (uint32_t)in.n;
+  const uint32_t nt = lc_tiles(n);
+  const size_t words = (size_t)nt * lc_tile_words();
+  size_t o = 0;
+  const size_t off_err = o; o = align_up(o + 16);
+  const size_t off_tmp = o; o = align_up(o + 16);
+  const size_t off_hb = o; o = align_up(o + 4 * words);
+  const size_t off_wpre = o; o = align_up(o + 2 * words);
+  const size_t off_tcnt = o; o = align_up(o + 4 * (size_t)nt);
+  const size_t off_tpre = o; o = align_up(o + 4 * ((size_t)nt + 1));
+  const size_t off_tail = o; o = align_up(o + 2 * (size_t)n);
+  lr_status st = ensure_buffer(&c->contract, &c->contract_bytes, o, s);
+  if (st != LR_OK) return st;
+  char *b = (char *)c->contract;
+  uint32_t *err = (uint32_t *)(b + off_err);
+  uint32_t *tmp = (uint32_t *)(b + off_tmp);
+  LR_TRY(cudaMemsetAsync(b, 0, off_hb, s));
+  if (!decided) {
+    // sample: how many links stay inside their tile
+    const uint32_t samples = 16384;
+    LR_TRY(launch_lc_sample(in.succ, n, samples, tmp, s));
+    LR_TRY(cudaMemcpyAsync(c->host_words + 1, tmp, 4, cudaMemcpyDeviceToHost, s));
+    LR_TRY(cudaStreamSynchronize(s));
+    if (c->host_words[1] * 2 < samples) return LR_ERR_NOT_FOUND;
+  }
+  Profiler prof;
+  prof.begin(s, (int64_t)in.n);
+  uint32_t *hb = (uint32_t *)(b + off_hb);
+  uint16_t *wpre = (uint16_t *)(b + off_wpre);
+  uint32_t *tcnt = (uint32_t *)(b + off_tcnt);
+  uint32_t *tpre = (uint32_t *)(b + off_tpre);
+  uint16_t *tail16 = (uint16_t *)(b + off_tail);
+  LR_TRY(launch_lc_solve(in.succ, in.weight, in.wtype, n, in.rank, in.rank_bytes, tail16, hb, wpre, tcnt,
+                         tpre, err, s));
+  LR_TRY(cudaMemcpyAsync(c->host_words + 1, tpre + nt, 4, cudaMemcpyDeviceToHost, s));
+  LR_TRY(cudaStreamSynchronize(s));
+  const uint64_t m = c->host_words[1];
+  if (!decided && m * 5 > (uint64_t)n * 3) { prof.cancel(); return LR_ERR_NOT_FOUND; }
+  // the contracted list: successors, weights (int32 unweighted: at most one
+  // tile's links; int64 weighted), ranks in the caller's type
+  const int wc = in.wtype == 0 ? 1 : 2;
+  const size_t wb = wc == 1 ? 4 : 8;
+  size_t o2 = 0;
+  const size_t off_sc = o2; o2 = align_up(o2 + 4 * std::max<uint64_t>(m, 1));
+  const size_t off_wc = o2; o2 = align_up(o2 + wb * std::max<uint64_t>(m, 1));
+  const size_t off_rc = o2; o2 = align_up(o2 + (size_t)in.rank_bytes * std::max<uint64_t>(m, 1));
+  st = ensure_buffer(&c->contract2, &c->contract2_bytes, o2, s);
+  if (st != LR_OK) return st;
+  char *b2 = (char *)c->contract2;
+  LR_TRY(launch_lc_nodes(in.succ, in.weight, in.wtype, n, in.rank, in.rank_bytes, tail16, hb, wpre, tpre,
+                         (uint32_t *)(b2 + off_sc), b2 + off_wc, err, s));
+  prof.mark(PH_PREP);
+  if (m > 0) {
+    Inputs sub;
+    memset(&sub, 0, sizeof(sub));
+    sub.succ = (const uint32_t *)(b2 + off_sc);
+    sub.weight = b2 + off_wc;
+    sub.wtype = wc;
+    sub.rank = b2 + off_rc;
+    sub.rank_bytes = in.rank_bytes;
+    sub.n = m;
+    sub.validate = in.validate;
+    sub.seed = in.seed;
+    sub.ctx = c;
+    sub.incl = 1;
+    sub.err_ext = err;
+    sub.no_contract = 1;
+    st = run(sub, tuning, s);
+    if (st != LR_OK) return st;
+  }
+  prof.mark(PH_CHASE0);
+  LR_TRY(launch_lc_finish(in.succ, in.weight, in.wtype, n, in.rank, in.rank_bytes, tail16, hb, wpre, tpre,
+                          b2 + off_rc, s));
+  prof.mark(PH_FINAL);
+  prof.end();
+  return finish_call(c, err, in.sync, s);
+}
+
 lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   const bool ptrs = in.sptr != nullptr;
   lr_status st = LR_OK;
@@ -477,6 +579,12 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   const bool log0 = u.logmode && !ptrs && !extras && in.offsets == nullptr && in.wtype == 0 &&
                     in.rank_bytes == 4 && in.n > u.cutoff && in.n <= (1ull << 30);
   const bool t0ws = extras && in.term == nullptr;
+  if (u.contract != LR_CONTRACT_OFF && !in.no_contract && !ptrs && in.offsets == nullptr && !extras &&
+      in.ws == nullptr && in.ctx == nullptr && !capturing && in.max_lists <= 0 &&
+      in.n >= 16384 && in.n <= 0xFFFFFFFEull) {
+    const lr_status cs = run_contracted(in, tuning, c, u.contract == LR_CONTRACT_ON, s);
+    if (cs != LR_ERR_NOT_FOUND) return cs;
+  }
   const int grid = chase_grid_for(u, rec16_0, log0);
   const bool need_count = in.max_lists <= 0 && (in.ws == nullptr || in.count_in_ws) &&
                           (in.n > u.cutoff || ptrs);
@@ -497,7 +605,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     fixed = (char *)c->fixed;
   }
   LevelDesc *desc = (LevelDesc *)(fixed + p.off_desc);
-  uint32_t *err = (uint32_t *)(fixed + p.off_err);
+  uint32_t *err = in.err_ext ? in.err_ext : (uint32_t *)(fixed + p.off_err);
   uint32_t *hcount = (uint32_t *)(fixed + p.off_hcount);
   uint32_t *qctr = (uint32_t *)(fixed + p.off_q);
   uint64_t *bcnt = (uint64_t *)(fixed + p.off_bcnt);

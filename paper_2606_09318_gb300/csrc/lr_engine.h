@@ -10,7 +10,7 @@
 namespace lr {
 
 struct Tuning {
-  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, logmode, algo;
+  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, logmode, algo, contract;
 };
 
 struct Plan {
@@ -51,6 +51,10 @@ struct Ctx {
   size_t var_bytes = 0;
   void *hostpath = nullptr;
   size_t hostpath_bytes = 0;
+  void *contract = nullptr;         // tile-local contraction: bitmap, prefixes
+  size_t contract_bytes = 0;
+  void *contract2 = nullptr;        // and the contracted list
+  size_t contract2_bytes = 0;
   uint32_t *host_words = nullptr;   // [0] device error bits, [1] head count, [8..9] int64 scratch
   bool pending_status = false;
 };

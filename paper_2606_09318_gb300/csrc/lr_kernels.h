@@ -112,4 +112,24 @@ int chase_log_occupancy(int block);
 int chase_occupancy(bool rec16, int block);
 cudaError_t kernels_setup();
 
+// Tile-local contraction (lr_contract.cu).
+uint32_t lc_tiles(uint64_t n);
+uint32_t lc_tile_words();
+cudaError_t lc_setup();
+cudaError_t launch_lc_sample(const uint32_t *succ, uint32_t n, uint32_t samples, uint32_t *out,
+                             cudaStream_t s);
+// Solve every tile (distances to the local tails into rank, tails into
+// tail16, the local-head bitmap and counts), then the tile prefixes.
+cudaError_t launch_lc_solve(const uint32_t *succ, const void *weight, int wtype, uint32_t n, void *rank,
+                            int rank_bytes, uint16_t *tail16, uint32_t *hb, uint16_t *wpre, uint32_t *tcnt,
+                            uint32_t *tpre, uint32_t *err, cudaStream_t s);
+// The contracted list: one node per local head.
+cudaError_t launch_lc_nodes(const uint32_t *succ, const void *weight, int wtype, uint32_t n, const void *rank,
+                            int rank_bytes, const uint16_t *tail16, const uint32_t *hb, const uint16_t *wpre,
+                            const uint32_t *tpre, uint32_t *succ_c, void *w_c, uint32_t *err, cudaStream_t s);
+// Ranks of every element from the contracted ranks rc.
+cudaError_t launch_lc_finish(const uint32_t *succ, const void *weight, int wtype, uint32_t n, void *rank,
+                             int rank_bytes, const uint16_t *tail16, const uint32_t *hb, const uint16_t *wpre,
+                             const uint32_t *tpre, const void *rc, cudaStream_t s);
+
 }  // namespace lr
