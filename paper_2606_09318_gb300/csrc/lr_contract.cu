@@ -70,11 +70,12 @@ template <class VT>
 struct LcTile {
   uint32_t raw[kTile];       // succ of each element of the tile
   uint16_t nxt[kTile];       // local successor or kEnd16; then per sub-ruler: next sub-ruler
-  uint16_t sub[kTile];       // sub-ruler of the element; per sub-ruler: its local tail once known
+  uint16_t sub[kTile];       // predecessor marks; then the element's sub-ruler; per sub-ruler:
+                             // its local tail once known (kEnd16 between tiles)
   VT off[kTile];             // link weight; then offset from the sub-ruler; per sub-ruler: distance
   uint32_t pred[kTileWords]; // has-local-predecessor bitmap
-  uint16_t srl[kMaxSr];      // the sub-rulers (mode A)
-  uint32_t nheads, nsr, dense;
+  uint16_t srl[kMaxSr];      // dense tiles: heads whose id is not a multiple of kSub
+  uint32_t nheads, nlinks, nextra, dense;
 };
 
 template <class VT>
@@ -90,89 +91,125 @@ __device__ __forceinline__ bool lc_is_sr(const LcTile<VT> &S, uint32_t j) {
   return lc_head(S, j) || (S.dense && (j % kSub) == 0);
 }
 
-// Mark local predecessors without shared-memory atomics: every local link
-// stores its source into mark[target] (plain stores; with two predecessors
-// one store wins and the loser sees it); then one ballot per 32 elements
-// builds the has-local-predecessor bitmap.  mark[] must hold kEnd16 on
-// entry; returns error bits.  Call with the whole block.
-__device__ __forceinline__ uint32_t lc_mark_preds(const uint16_t *nxt, uint16_t *mark, uint32_t *pred,
-                                                  uint32_t len) {
-  for (uint32_t j = threadIdx.x; j < len; j += blockDim.x)
-    if (nxt[j] != kEnd16) mark[nxt[j]] = (uint16_t)j;
-  __syncthreads();
-  uint32_t bad = 0;
-  for (uint32_t j0 = 0; j0 < kTile; j0 += blockDim.x) {
-    const uint32_t j = j0 + threadIdx.x;
-    const bool in = j < len;
-    const bool has = in && mark[j] != kEnd16;
-    if (in && nxt[j] != kEnd16 && mark[nxt[j]] != j) bad |= kErrNotList;   // a second predecessor
-    const uint32_t word = __ballot_sync(0xFFFFFFFFu, has);
-    if ((threadIdx.x & 31u) == 0) pred[j >> 5] = word;
-  }
-  return bad;
+// One element of the load: succ, local link, weight; marks its target.
+template <int WT, class VT>
+__device__ __forceinline__ void lc_load1(LcTile<VT> &S, uint32_t j, uint32_t s, VT w, uint32_t t,
+                                         uint32_t base, uint32_t n, uint32_t &bad, uint32_t &links) {
+  const uint32_t i = base + j;
+  const bool local = s < n && s != i && (s >> kTileShift) == t;
+  if (s >= n) bad |= kErrRange;
+  S.nxt[j] = local ? (uint16_t)(s - base) : kEnd16;
+  S.off[j] = local ? w : (VT)0;
+  if (local) { S.sub[s - base] = (uint16_t)j; ++links; }
 }
 
 // Load tile `t` and find for every element its local tail and distance to
-// it.  Level 1: every sub-ruler walks to the next sub-ruler (or its local
-// tail), recording (sub-ruler, offset) in each element it passes.  Level 2
-// (dense tiles): pointer doubling over the at most kMaxSr sub-rulers gives
-// each its tail and distance.  In sparse tiles the sub-rulers are the heads
-// alone, whose walks already end at their tails.  Walks are bounded by the
-// tile length; an element no walk reaches lies on a cycle.
+// it.  sub[] must hold kEnd16 on entry.
+//   Marks: every local link stores its source into sub[target] (plain
+//   stores); one ballot per 32 elements turns them into the
+//   has-local-predecessor bitmap, and fewer marked targets than local links
+//   means an element with two predecessors.
+//   Level 1: every sub-ruler walks to the next sub-ruler (or its local
+//   tail), recording (sub-ruler, offset) in each element it passes.
+//   Level 2 (dense tiles): synchronous pointer doubling over the at most
+//   kMaxSr sub-rulers gives each its tail and distance.  In sparse tiles the
+//   sub-rulers are the heads alone, whose walks already end at their tails.
+// Walks are bounded by the tile length; an element no walk reaches lies on
+// a cycle.  Returns the tile length.
 template <int WT, class VT>
 __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *succ, const void *weight,
-                                  uint32_t n, uint32_t *err) {
+                                  uint32_t n, uint32_t *err, bool vec) {
   const uint32_t base = t << kTileShift;
   const uint32_t len = min(kTile, n - base);
   const uint32_t lane = threadIdx.x & 31u;
-  for (uint32_t j = threadIdx.x; j < kTile; j += blockDim.x) S.sub[j] = kEnd16;
-  if (threadIdx.x == 0) { S.nheads = 0; S.nsr = 0; }
-  uint32_t bad = 0;
-  for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
-    const uint32_t i = base + j;
-    const uint32_t s = __ldcs(succ + i);
-    S.raw[j] = s;
-    const bool local = s < n && s != i && (s >> kTileShift) == t;
-    if (s >= n) bad |= kErrRange;
-    S.nxt[j] = local ? (uint16_t)(s - base) : kEnd16;
-    S.off[j] = local ? (VT)lc_weight<WT>(weight, i) : (VT)0;
-  }
-  __syncthreads();
-  bad |= lc_mark_preds(S.nxt, S.sub, S.pred, len);
-  __syncthreads();
-  for (uint32_t j = threadIdx.x; j < kTile; j += blockDim.x) S.sub[j] = kEnd16;
-  if (threadIdx.x < kTileWords) {
-    const uint32_t w = threadIdx.x, lo = w * 32;
-    const uint32_t valid = lo >= len ? 0u : (len - lo >= 32 ? 0xFFFFFFFFu : ((1u << (len - lo)) - 1u));
-    const uint32_t h = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)__popc(~S.pred[w] & valid));
-    if (lane == 0 && h) atomicAdd(&S.nheads, h);
-  }
-  __syncthreads();
-  const bool dense = S.nheads + (len + kSub - 1) / kSub <= kMaxSr;
-  if (threadIdx.x == 0) S.dense = dense;
-  __syncthreads();
-  // level 1: in dense tiles the sub-rulers are first listed (one ballot and
-  // one atomic per warp), so that consecutive threads take consecutive walks
-  if (dense) {
-    for (uint32_t j0 = 0; j0 < len; j0 += blockDim.x) {
-      const uint32_t j = j0 + threadIdx.x;
-      const bool is_sr = j < len && lc_is_sr(S, j);
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, is_sr);
-      uint32_t pos = 0;
-      if (lane == 0 && m) pos = atomicAdd(&S.nsr, (uint32_t)__popc(m));
-      pos = __shfl_sync(0xFFFFFFFFu, pos, 0);
-      if (is_sr) S.srl[pos + __popc(m & ((1u << lane) - 1u))] = (uint16_t)j;
+  if (threadIdx.x == 0) { S.nheads = 0; S.nlinks = 0; S.nextra = 0; }
+  uint32_t bad = 0, links = 0;
+  // load, four elements per thread and step
+  for (uint32_t g = threadIdx.x; g * 4 < len; g += blockDim.x) {
+    const uint32_t j = g * 4;
+    if (vec && j + 4 <= len) {
+      const uint4 sv = __ldcs(reinterpret_cast<const uint4 *>(succ + base + j));
+      VT w0 = 1, w1 = 1, w2 = 1, w3 = 1;
+      if constexpr (WT == 1) {
+        const int4 q = __ldcs(reinterpret_cast<const int4 *>(reinterpret_cast<const int *>(weight) + base + j));
+        w0 = (VT)(int64_t)q.x; w1 = (VT)(int64_t)q.y; w2 = (VT)(int64_t)q.z; w3 = (VT)(int64_t)q.w;
+      } else if constexpr (WT == 2) {
+        const longlong2 *wp = reinterpret_cast<const longlong2 *>(reinterpret_cast<const long long *>(weight) + base + j);
+        const longlong2 q0 = __ldcs(wp), q1 = __ldcs(wp + 1);
+        w0 = (VT)q0.x; w1 = (VT)q0.y; w2 = (VT)q1.x; w3 = (VT)q1.y;
+      }
+      *reinterpret_cast<uint4 *>(&S.raw[j]) = sv;
+      lc_load1<WT, VT>(S, j + 0, sv.x, w0, t, base, n, bad, links);
+      lc_load1<WT, VT>(S, j + 1, sv.y, w1, t, base, n, bad, links);
+      lc_load1<WT, VT>(S, j + 2, sv.z, w2, t, base, n, bad, links);
+      lc_load1<WT, VT>(S, j + 3, sv.w, w3, t, base, n, bad, links);
+    } else {
+      for (uint32_t q = j; q < min(len, j + 4); ++q) {
+        const uint32_t sq = __ldcs(succ + base + q);
+        S.raw[q] = sq;
+        lc_load1<WT, VT>(S, q, sq, (VT)lc_weight<WT>(weight, base + q), t, base, n, bad, links);
+      }
     }
-    __syncthreads();
   }
-  const uint32_t nwalk = dense ? S.nsr : len;
-  for (uint32_t p = threadIdx.x; p < nwalk; p += blockDim.x) {
+  links = __reduce_add_sync(0xFFFFFFFFu, links);
+  if (lane == 0 && links) atomicAdd(&S.nlinks, links);
+  __syncthreads();
+  // the has-local-predecessor bitmap; marks are cleared as they are read
+  for (uint32_t j0 = 0; j0 < kTile; j0 += blockDim.x) {
+    const uint32_t j = j0 + threadIdx.x;
+    const bool has = j < len && S.sub[j] != kEnd16;
+    S.sub[j] = kEnd16;
+    const uint32_t word = __ballot_sync(0xFFFFFFFFu, has);
+    if (lane == 0) S.pred[j >> 5] = word;
+  }
+  __syncthreads();
+  // heads per tile; in dense tiles also the heads that are not multiples of kSub
+  if (threadIdx.x < 32) {
+    uint32_t hw[4], cnt = 0, extra = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t w = threadIdx.x * 4 + q, lo = w * 32;
+      const uint32_t valid = lo >= len ? 0u : (len - lo >= 32 ? 0xFFFFFFFFu : ((1u << (len - lo)) - 1u));
+      hw[q] = ~S.pred[w] & valid;
+      cnt += __popc(hw[q]);
+      extra += __popc(hw[q] & ~0x01010101u);           // bit b is a multiple of kSub = 8 iff b % 8 == 0
+    }
+    const uint32_t heads = __reduce_add_sync(0xFFFFFFFFu, cnt);
+    const uint32_t marked = len - heads;
+    if (marked < S.nlinks) bad |= kErrNotList;            // two links into one element
+    const bool dense = heads + (len + kSub - 1) / kSub <= kMaxSr;
+    if (dense) {
+      uint32_t incl = extra;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if ((int)lane >= d) incl += v;
+      }
+      uint32_t pos = incl - extra;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t bits = hw[q] & ~0x01010101u;
+        while (bits) {
+          const uint32_t b = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          S.srl[pos++] = (uint16_t)((threadIdx.x * 4 + q) * 32 + b);
+        }
+      }
+      if (lane == 31) S.nextra = incl;
+    }
+    if (lane == 0) { S.nheads = heads; S.dense = dense; }
+  }
+  __syncthreads();
+  const bool dense = S.dense;
+  const uint32_t nmul = (len + kSub - 1) / kSub;
+  const uint32_t nsr = dense ? nmul + S.nextra : len;
+  // level 1
+  for (uint32_t p = threadIdx.x; p < nsr; p += blockDim.x) {
     uint32_t j = p;
-    if (dense) j = S.srl[p];
+    if (dense) j = p < nmul ? p * kSub : S.srl[p - nmul];
     else if (!lc_head(S, j)) continue;
     uint32_t x = j, steps = 0;
     VT o = 0;
-    uint16_t nsr = kEnd16, tail = kEnd16;
+    uint16_t nx = kEnd16, tail = kEnd16;
     for (;;) {
       const VT wx = S.off[x];
       const uint16_t y = S.nxt[x];
@@ -180,28 +217,27 @@ __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *suc
       S.off[x] = o;
       if (y == kEnd16) { tail = (uint16_t)x; break; }
       o += wx;
-      if (dense && (y % kSub) == 0) { nsr = y; break; }
+      if (dense && (y % kSub) == 0) { nx = y; break; }
       x = y;
       if (++steps > len) { bad |= kErrCycle; break; }
     }
-    S.nxt[j] = nsr;                   // per sub-ruler: the next one (kEnd16: done)
+    S.nxt[j] = nx;                    // per sub-ruler: the next one (kEnd16: done)
     S.off[j] = o;                     // weight to it, or distance to the tail
     S.sub[j] = tail;                  // the tail, known once nxt is kEnd16
   }
   __syncthreads();
   // level 2: synchronous pointer doubling over the sub-rulers
   if (dense) {
-    const uint32_t ns = S.nsr;
     uint32_t rounds = 0;
-    while ((1u << rounds) < ns) ++rounds;
+    while ((1u << rounds) < nsr) ++rounds;
     for (uint32_t r = 0; r < rounds; ++r) {
       uint16_t tn[2], tt[2];
       VT tv[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const uint32_t p = threadIdx.x + e * kLcThreads;
-        if (p < ns) {
-          const uint32_t j = S.srl[p];
+        if (p < nsr) {
+          const uint32_t j = p < nmul ? p * kSub : S.srl[p - nmul];
           const uint16_t a = S.nxt[j];
           if (a != kEnd16) { tv[e] = S.off[j] + S.off[a]; tn[e] = S.nxt[a]; tt[e] = S.sub[a]; }
           else { tv[e] = S.off[j]; tn[e] = kEnd16; tt[e] = S.sub[j]; }
@@ -211,7 +247,10 @@ __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *suc
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         const uint32_t p = threadIdx.x + e * kLcThreads;
-        if (p < ns) { const uint32_t j = S.srl[p]; S.nxt[j] = tn[e]; S.off[j] = tv[e]; S.sub[j] = tt[e]; }
+        if (p < nsr) {
+          const uint32_t j = p < nmul ? p * kSub : S.srl[p - nmul];
+          S.nxt[j] = tn[e]; S.off[j] = tv[e]; S.sub[j] = tt[e];
+        }
       }
       __syncthreads();
     }
@@ -270,15 +309,17 @@ k_lc_scan(const uint32_t *__restrict__ tcnt, uint32_t ntiles, uint32_t *__restri
 // local-head bitmap, the head counts before each word of the tile and the
 // heads per tile go to hb, wpre and tcnt.
 template <int WT, class VT, class RT>
-__global__ void __launch_bounds__(kLcThreads)
+__global__ void __launch_bounds__(kLcThreads, WT == 0 ? 4 : 3)
 k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, uint32_t n,
            RT *__restrict__ rank, uint16_t *__restrict__ tail16, uint32_t *__restrict__ hb,
-           uint16_t *__restrict__ wpre, uint32_t *__restrict__ tcnt, uint32_t *__restrict__ err) {
+           uint16_t *__restrict__ wpre, uint32_t *__restrict__ tcnt, uint32_t *__restrict__ err, int vec) {
   extern __shared__ __align__(16) unsigned char lc_smem[];
   LcTile<VT> &S = *reinterpret_cast<LcTile<VT> *>(lc_smem);
   const uint32_t ntiles = (n + kTile - 1) >> kTileShift;
+  for (uint32_t j = threadIdx.x; j < kTile; j += blockDim.x) S.sub[j] = kEnd16;
+  __syncthreads();
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint32_t len = lc_tile_solve<WT, VT>(S, t, succ, weight, n, err);
+    const uint32_t len = lc_tile_solve<WT, VT>(S, t, succ, weight, n, err, vec != 0);
     const uint32_t base = t << kTileShift;
     bool cyc = false;
     for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
@@ -315,6 +356,8 @@ k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, u
       }
       if (threadIdx.x == 31) tcnt[t] = incl;
     }
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < kTile; j += blockDim.x) S.sub[j] = kEnd16;   // for the next tile
     __syncthreads();
   }
 }
@@ -435,9 +478,10 @@ cudaError_t launch_lc_solve(const uint32_t *succ, const void *weight, int wtype,
   const size_t sm = lc_smem_bytes(wtype != 0, rank_bytes);
   const int per_sm = wtype ? 3 : 4;
   const int grid = (int)std::min<uint32_t>(nt, (uint32_t)device_sm_count() * per_sm);
+  const int vec = ((uintptr_t)succ & 15u) == 0 && ((uintptr_t)weight & 15u) == 0;
 #define LC_SOLVE(W, V, R)                                                                          \
   k_lc_solve<W, V, R><<<grid, kLcThreads, sm, s>>>(succ, weight, n, reinterpret_cast<R *>(rank), tail16, \
-                                                   hb, wpre, tcnt, err)
+                                                   hb, wpre, tcnt, err, vec)
   if (wtype == 0) { if (rank_bytes == 4) LC_SOLVE(0, uint32_t, uint32_t); else LC_SOLVE(0, uint32_t, unsigned long long); }
   else if (wtype == 1) { if (rank_bytes == 4) LC_SOLVE(1, uint64_t, uint32_t); else LC_SOLVE(1, uint64_t, unsigned long long); }
   else { if (rank_bytes == 4) LC_SOLVE(2, uint64_t, uint32_t); else LC_SOLVE(2, uint64_t, unsigned long long); }
