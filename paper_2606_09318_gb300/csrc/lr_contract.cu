@@ -429,16 +429,40 @@ k_lc_tails(const uint32_t *__restrict__ succ, const void *__restrict__ weight, u
 }
 
 // Fix pass: rank[i] = dist(i -> t) + rank[t] for every element that is not
-// a tail (tails already hold their final rank).
+// a tail (tails already hold their final rank).  Four elements per thread
+// (a group never straddles a tile: tiles are multiples of 4).
+template <class RT>
+__device__ __forceinline__ RT lc_fix1(uint32_t i, uint16_t tl, RT r, const RT *rank) {
+  if (tl == kEnd16) return r;
+  const uint32_t ti = (i & ~(kTile - 1u)) + tl;
+  return ti == i ? r : (RT)(r + __ldcg(rank + ti));
+}
+
 template <class RT>
 __global__ void __launch_bounds__(256)
-k_lc_fix(uint32_t n, RT *__restrict__ rank, const uint16_t *__restrict__ tail16) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint16_t tl = __ldcs(tail16 + i);
-    if (tl == kEnd16) continue;
-    const uint32_t ti = (i & ~(kTile - 1u)) + tl;
-    if (ti == i) continue;
-    rank[i] = (RT)(__ldcs(rank + i) + __ldcg(rank + ti));
+k_lc_fix(uint32_t n, RT *__restrict__ rank, const uint16_t *__restrict__ tail16, int vec) {
+  const uint32_t groups = (n + 3) / 4;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
+    const uint32_t i = g * 4;
+    if (vec && i + 4 <= n) {
+      const uint2 tv = __ldcs(reinterpret_cast<const uint2 *>(tail16 + i));
+      const uint16_t t0 = (uint16_t)tv.x, t1 = (uint16_t)(tv.x >> 16), t2 = (uint16_t)tv.y, t3 = (uint16_t)(tv.y >> 16);
+      if constexpr (sizeof(RT) == 4) {
+        uint4 r = __ldcs(reinterpret_cast<const uint4 *>(rank + i));
+        r.x = lc_fix1<RT>(i, t0, r.x, rank); r.y = lc_fix1<RT>(i + 1, t1, r.y, rank);
+        r.z = lc_fix1<RT>(i + 2, t2, r.z, rank); r.w = lc_fix1<RT>(i + 3, t3, r.w, rank);
+        __stcs(reinterpret_cast<uint4 *>(rank + i), r);
+      } else {
+        ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2 *>(rank + i));
+        ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2 *>(rank + i + 2));
+        a.x = lc_fix1<RT>(i, t0, a.x, rank); a.y = lc_fix1<RT>(i + 1, t1, a.y, rank);
+        b.x = lc_fix1<RT>(i + 2, t2, b.x, rank); b.y = lc_fix1<RT>(i + 3, t3, b.y, rank);
+        __stcs(reinterpret_cast<ulonglong2 *>(rank + i), a);
+        __stcs(reinterpret_cast<ulonglong2 *>(rank + i + 2), b);
+      }
+    } else {
+      for (uint32_t q = i; q < min(n, i + 4); ++q) rank[q] = lc_fix1<RT>(q, tail16[q], rank[q], rank);
+    }
   }
 }
 
@@ -510,7 +534,7 @@ cudaError_t launch_lc_finish(const uint32_t *succ, const void *weight, int wtype
                              int rank_bytes, const uint16_t *tail16, const uint32_t *hb, const uint16_t *wpre,
                              const uint32_t *tpre, const void *rc, cudaStream_t s) {
   const int gw = stream_grid(((uint64_t)n + 31) / 32, 256);
-  const int ge = stream_grid(n, 256);
+  const int ge = stream_grid(((uint64_t)n + 3) / 4, 256);
 #define LC_TAILS(W, R)                                                                             \
   k_lc_tails<W, R><<<gw, 256, 0, s>>>(succ, weight, n, reinterpret_cast<R *>(rank), tail16, hb, wpre, tpre, \
                                       reinterpret_cast<const R *>(rc))
@@ -518,8 +542,9 @@ cudaError_t launch_lc_finish(const uint32_t *succ, const void *weight, int wtype
   else if (wtype == 1) { if (rank_bytes == 4) LC_TAILS(1, uint32_t); else LC_TAILS(1, unsigned long long); }
   else { if (rank_bytes == 4) LC_TAILS(2, uint32_t); else LC_TAILS(2, unsigned long long); }
 #undef LC_TAILS
-  if (rank_bytes == 4) k_lc_fix<uint32_t><<<ge, 256, 0, s>>>(n, reinterpret_cast<uint32_t *>(rank), tail16);
-  else k_lc_fix<unsigned long long><<<ge, 256, 0, s>>>(n, reinterpret_cast<unsigned long long *>(rank), tail16);
+  const int vec = ((uintptr_t)rank & 15u) == 0 && ((uintptr_t)tail16 & 7u) == 0;
+  if (rank_bytes == 4) k_lc_fix<uint32_t><<<ge, 256, 0, s>>>(n, reinterpret_cast<uint32_t *>(rank), tail16, vec);
+  else k_lc_fix<unsigned long long><<<ge, 256, 0, s>>>(n, reinterpret_cast<unsigned long long *>(rank), tail16, vec);
   count_launch(2);
   return cudaGetLastError();
 }
