@@ -83,8 +83,19 @@ typedef struct lr_tuning {
     uint32_t algorithm;  /* LR_ALGO_SRS (0, default) or LR_ALGO_WYLLIE            */
     uint32_t contract;   /* tile-local contraction: 0 auto (default),            */
                          /* LR_CONTRACT_OFF or LR_CONTRACT_ON                     */
-    uint32_t reserved[1];
+    uint32_t spawn;      /* 1: ruler spawning at level 0 (Section 2.2); 0 off    */
 } lr_tuning;
+
+/*
+ * Ruler spawning (Section 2.2): when a chasing thread's CTA has no queued
+ * ruler left, the thread claims an unvisited element of the CTA's slice of
+ * ids as a new ruler and chases from it, so that every thread keeps a wave
+ * until no unvisited element is left; waves that reach a spawned ruler stop
+ * there.  More rulers (about t ln(n/t) for t waves) in exchange for shorter
+ * segments.  Level 0 of the default algorithm, exchange chase only; not
+ * combined with extra outputs or the log path (ignored there).  Results are
+ * identical with and without.
+ */
 
 /*
  * Tile-local contraction (Section 2.3, restated for one GPU): before the
@@ -225,6 +236,18 @@ size_t lr_workspace_size(int64_t n_total, int32_t k, const lr_opts *opts);
  * non-NULL (and inclusive_tail) matters; outs == NULL is lr_workspace_size. */
 size_t lr_workspace_size_outputs(int64_t n_total, int32_t k, const lr_outputs *outs,
                                  const lr_opts *opts);
+
+/*
+ * Shape of the recursion of the last ruling-set call on `stream` (after it
+ * completes; waits for the stream): the sizes of the levels that ran, level
+ * 0 first (n), then the rulers of each level, down to the base case.
+ * Writes up to max_levels entries and returns how many levels ran (0 when
+ * the last call did not run the ruling set itself, e.g. pointer doubling or
+ * a contracted call; -1 on a CUDA error).  The descriptors live in the
+ * call's workspace: valid until the next call on the stream or until a
+ * caller-owned workspace is reused.
+ */
+int32_t lr_level_sizes(lr_stream stream, int64_t *sizes, int32_t max_levels);
 
 /*
  * Wait for `stream` and return (and clear) the status the device recorded

@@ -44,7 +44,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("f0_inv", ctypes.c_uint32), ("f_inv", ctypes.c_uint32), ("cutoff", ctypes.c_uint32),
                 ("chase_block", ctypes.c_uint32), ("chase_ctas", ctypes.c_uint32),
                 ("algorithm", ctypes.c_uint32), ("contract", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 1)]
+                ("spawn", ctypes.c_uint32)]
 
 
 ALGO_SRS, ALGO_WYLLIE = 0, 1
@@ -123,6 +123,7 @@ _SIGS = {
     "lr_rank_batch_outputs": (ctypes.c_int, [_V, _V, _V, _V, _I32, ctypes.POINTER(_Outputs),
                                              ctypes.POINTER(_Opts), _V]),
     "lr_get_device_status": (ctypes.c_int, [_V]),
+    "lr_level_sizes": (_I32, [_V, ctypes.POINTER(_I64), _I32]),
     "lr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lr_version": (ctypes.c_char_p, []),
     "lr_profile_enable": (ctypes.c_int, [_I32]),
@@ -396,6 +397,16 @@ def rank_host(succ, weight=None, out=None, rank_dtype=None, validate=False, seed
     code = fn(sp, wp, n, rp, ctypes.byref(o), _stream_handle(stream))
     _check(code, "lr_rank_host" if wait else "lr_rank_host_async")
     return out
+
+
+def level_sizes(stream=None):
+    """Sizes of the recursion levels of the last ruling-set call on `stream`
+    (waits for it): [n, rulers at level 1, ...]."""
+    arr = (_I64 * 16)()
+    cnt = load().lr_level_sizes(_stream_handle(stream), arr, 16)
+    if cnt < 0:
+        raise LRError(8, "lr_level_sizes")
+    return [int(x) for x in arr[:cnt]]
 
 
 def device_status(stream=None):

@@ -51,6 +51,7 @@ struct LevelDesc {
   uint64_t seed;     // static: permutation seed
   uint32_t rounds;   // static: pointer-doubling rounds of the fallback base
   uint32_t hsrc;     // where this level's heads come from: kHeadsBitmap or kHeadsList
+  uint32_t nraw;     // with spawning: ruler ids of the next level before compaction (else 0)
 };
 
 enum : uint32_t { kHeadsBitmap = 0, kHeadsList = 1 };
@@ -185,6 +186,36 @@ __device__ __forceinline__ Rec16 xchg_rec(Rec16 *p, uint32_t cid, uint64_t off) 
   r.tag = (uint32_t)(olo >> 32);
   r.w = ohi;
   return r;
+}
+
+// Ruler spawning (Section 2.2).  A spawner claims an unvisited element as a
+// new ruler c by exchanging in a claim mark, which no visited record can
+// equal: an 8-byte record {offset, id} never carries offset 0xFFFFFFFF (an
+// offset is below n <= 2^32 - 2); a 16-byte record carries successor word 0
+// once visited, and kClaimMark in a claim.
+constexpr uint32_t kClaimMark = 0xFFFFFFFFu;
+
+__device__ __forceinline__ Rec8 claim_rec(Rec8 *p, uint32_t cid) { return xchg_rec(p, cid, kClaimMark); }
+__device__ __forceinline__ Rec16 claim_rec(Rec16 *p, uint32_t cid) {
+  const unsigned long long nlo = ((unsigned long long)cid << 32) | kClaimMark, nhi = 0;
+  unsigned long long olo, ohi;
+  asm volatile("{\n\t.reg .b128 d, b;\n\tmov.b128 b, {%2, %3};\n\t"
+               "atom.global.exch.b128 d, [%4], b;\n\tmov.b128 {%0, %1}, d;\n\t}"
+               : "=l"(olo), "=l"(ohi) : "l"(nlo), "l"(nhi), "l"(p) : "memory");
+  Rec16 r;
+  r.succ = (uint32_t)olo;
+  r.tag = (uint32_t)(olo >> 32);
+  r.w = ohi;
+  return r;
+}
+__device__ __forceinline__ bool rec_is_claim(const Rec8 &r) { return r.hi != kUnvisited && r.lo == kClaimMark; }
+__device__ __forceinline__ bool rec_is_claim(const Rec16 &r) { return r.tag != kUnvisited && r.succ == kClaimMark; }
+// Put back a record exactly as it was (a spawner that lost its candidate).
+__device__ __forceinline__ void st_raw(Rec8 *p, const Rec8 &r) {
+  __stcg(reinterpret_cast<uint2 *>(p), make_uint2(r.lo, r.hi));
+}
+__device__ __forceinline__ void st_raw(Rec16 *p, const Rec16 &r) {
+  __stcg(reinterpret_cast<uint4 *>(p), make_uint4(r.succ, r.tag, (uint32_t)r.w, (uint32_t)(r.w >> 32)));
 }
 
 // The raw successor array read as a record (level 0 of the log path): no tag,

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -65,6 +66,7 @@ Tuning resolve_tuning_builtin(int64_t n, bool weighted) {
   u.logmode = 0;
   u.algo = LR_ALGO_SRS;
   u.contract = LR_CONTRACT_AUTO;
+  u.spawn = 0;
   return u;
 }
 
@@ -88,7 +90,9 @@ Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted, bool batch) 
   u.logmode = env_u32(env, "log", 0);
   u.algo = env_u32(env, "algo", LR_ALGO_SRS);
   u.contract = env_u32(env, "contract", u.contract);
+  u.spawn = env_u32(env, "spawn", u.spawn);
   if (t) {
+    if (t->spawn) u.spawn = t->spawn;
     if (t->algorithm) u.algo = t->algorithm;
     if (t->contract) u.contract = t->contract;
     if (t->f0_inv) u.f0_inv = t->f0_inv;
@@ -118,8 +122,18 @@ int chase_grid_for(const Tuning &u, bool rec16, bool log0) {
 }
 
 // Static plan for n elements and at most h lists.
+// Spawned rulers provided for at level 0: t waves leave about t ln(n/t)
+// rulers in all (Section 2.5 cites this for spawning); a few t more as slack.
+static uint32_t spawn_capacity(uint64_t n, uint64_t threads) {
+  if (threads == 0) threads = 1;
+  const double ratio = n > threads ? (double)n / (double)threads : 1.0;
+  const double want = (double)threads * (std::ceil(std::log(ratio)) + 4.0);
+  return (uint32_t)std::min<double>((double)n, want);
+}
+
 Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,
-               uint64_t seed, int chase_grid, bool force_srs, bool log0, bool term, bool t0ws) {
+               uint64_t seed, int chase_grid, bool force_srs, bool log0, bool term, bool t0ws,
+               bool spawn0) {
   Plan p;
   memset(&p, 0, sizeof(p));
   p.n = n;
@@ -133,10 +147,16 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
   p.cap[0] = (uint32_t)n;
   p.f_inv[0] = u.f0_inv;
   int L = 0;
+  const bool sp = spawn0 && (n > u.cutoff || force_srs);
+  p.spawn_cap = sp ? spawn_capacity(n, (uint64_t)chase_grid * u.block) : 0;
   if (n > u.cutoff || force_srs) {
     for (;;) {
       const uint64_t r = (p.cap[L] + p.f_inv[L] - 1) / p.f_inv[L];
-      const uint64_t nc = std::min<uint64_t>(p.cap[L], r + p.hcap);
+      uint64_t nc = std::min<uint64_t>(p.cap[L], r + p.hcap);
+      if (L == 0 && sp) {
+        p.raw_cap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, nc + p.spawn_cap);
+        nc = std::min<uint64_t>(p.cap[0], nc + p.spawn_cap);
+      }
       ++L;
       p.cap[L] = (uint32_t)nc;
       p.f_inv[L] = u.f_inv;
@@ -204,6 +224,15 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
     p.off_pd[1] = o; o = align_up(o + 4 * (size_t)p.cap[L]);
     p.off_pd[2] = o; o = align_up(o + 8 * (size_t)p.cap[L]);
     p.off_pd[3] = o; o = align_up(o + 8 * (size_t)p.cap[L]);
+  }
+  if (p.spawn_cap) {
+    const size_t words = (p.spawn_cap + 31) / 32;
+    p.off_sraw = o; o = align_up(o + 16 * (size_t)p.raw_cap);
+    p.off_srraw = o; o = align_up(o + (size_t)rank_bytes * p.raw_cap);
+    p.off_supre = o; o = align_up(o + 4 * words);
+    p.off_sctr = o; o = align_up(o + 16 + 4 * (size_t)chase_grid);
+    p.off_sused = o; o = align_up(o + 4 * words);
+    p.spawn_zero = o - p.off_sctr;                // counter, cursors, claimed bitmap
   }
   p.term = term;
   if (term) {
@@ -439,6 +468,7 @@ static bool wyllie_w16(const Inputs &in) { return in.wtype != 0; }
 
 // Whole-list pointer doubling (lr_wyllie.cu) on the same inputs and outputs.
 static lr_status run_wyllie(const Inputs &in, Ctx *c, cudaStream_t s) {
+  c->last_nlev = 0;
   const bool w16 = wyllie_w16(in);
   const WyPlan q = wyllie_plan(in.n, w16);
   char *base = nullptr;
@@ -504,6 +534,7 @@ static lr_status run_contracted(const Inputs &in, const lr_tuning *tuning, Ctx *
   }
   Profiler prof;
   prof.begin(s, (int64_t)in.n);
+  c->last_nlev = 0;
   uint32_t *hb = (uint32_t *)(b + off_hb);
   uint16_t *wpre = (uint16_t *)(b + off_wpre);
   uint32_t *tcnt = (uint32_t *)(b + off_tcnt);
@@ -579,6 +610,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   const bool log0 = u.logmode && !ptrs && !extras && in.offsets == nullptr && in.wtype == 0 &&
                     in.rank_bytes == 4 && in.n > u.cutoff && in.n <= (1ull << 30);
   const bool t0ws = extras && in.term == nullptr;
+  const bool spawn0 = u.spawn != 0 && u.xchg != 0 && !log0 && !extras && !ptrs;
   if (u.contract != LR_CONTRACT_OFF && !in.no_contract && !ptrs && in.offsets == nullptr && !extras &&
       in.ws == nullptr && in.ctx == nullptr && !capturing && in.max_lists <= 0 &&
       in.n >= 16384 && in.n <= 0xFFFFFFFEull) {
@@ -590,7 +622,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
                           (in.n > u.cutoff || ptrs);
   if (need_count && capturing) return LR_ERR_CAPTURE;
   uint64_t hb = in.max_lists > 0 ? (uint64_t)in.max_lists : in.n;
-  Plan p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws);
+  Plan p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws, spawn0);
 
   // fixed part (level 0)
   char *fixed = nullptr;
@@ -640,7 +672,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     }
     LR_TRY(cudaStreamSynchronize(s));
     hb = std::max<uint64_t>(1, c->host_words[1]);
-    p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws);
+    p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws, spawn0);
   }
   if (!in.ws) {
     st = ensure_buffer(&c->var, &c->var_bytes, p.var_bytes, s);
@@ -667,6 +699,16 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   ip.has_pd = p.has_pd;
   ip.hcap = p.hcap;
   LR_TRY(launch_init(desc, ip, s));
+  if (!in.ctx) { c->last_desc = desc; c->last_nlev = p.nlev; }
+  if (p.spawn_cap) LR_TRY(cudaMemsetAsync(var + p.off_sctr, 0, p.spawn_zero, s));
+  SpawnArgs spa;
+  memset(&spa, 0, sizeof(spa));
+  if (p.spawn_cap) {
+    spa.ctr = (uint32_t *)(var + p.off_sctr);
+    spa.cap = p.spawn_cap;
+    spa.used = (uint32_t *)(var + p.off_sused);
+    spa.cursor = (uint32_t *)(var + p.off_sctr + 16);
+  }
   uint32_t *hA0 = (uint32_t *)(var + p.off_hA);
   if (log0) LR_TRY(cudaMemsetAsync(var + p.off_hdr, 0xFF, (size_t)p.total_chunks * 8, s));
   if (log0 || sums0)
@@ -708,10 +750,17 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
       LR_TRY(launch_chase_log(desc, in.succ, work_of(1), ns, qctr, p.chase_grid, p.chase_block, err,
                               (uint32_t *)(var + p.off_log), (uint2 *)(var + p.off_hdr), p.per_cta,
                               p.total_chunks, (uint32_t *)(fixed + p.off_ovf), s));
-    else
+    else if (l == 0 && p.spawn_cap) {
+      // spawning: reduced records at uncompacted ids, then compacted into level 1
+      LR_TRY(launch_chase(desc, 0, work0, r16, var + p.off_sraw, ns, qctr, p.chase_grid, p.chase_block,
+                          err, (int)u.xchg, nullptr, nullptr, &spa, s));
+      LR_TRY(launch_spawn_compact(desc, 0, p.nlev, spa.ctr, spa.cap, spa.used, (uint32_t *)(var + p.off_supre),
+                                  var + p.off_sraw, work_of(1), p.raw_cap, p.cutoff, p.has_pd ? 1u : 0u,
+                                  err, s));
+    } else
       LR_TRY(launch_chase(desc, l, work_of(l), r16, work_of(l + 1), ns,
                           qctr + (size_t)l * p.chase_grid, p.chase_grid, p.chase_block, err,
-                          (int)u.xchg, tid_of(l), tid_of(l + 1), s));
+                          (int)u.xchg, tid_of(l), tid_of(l + 1), nullptr, s));
     prof.mark(l == 0 ? PH_CHASE0 : PH_CHASE);
   }
   LR_TRY(launch_base(desc, L, work_of(L), L > 0 || rec16_0, R_of(L), p.rank_bytes, p.cutoff, err,
@@ -735,7 +784,12 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     else if (l == 0 && ptrs)
       LR_TRY(launch_finalize_ptrs(desc, work0, rec16_0, R_of(1), in.rptr, p.rank_bytes, p.cap[0],
                                   in.offsets, in.k, err, s));
-    else
+    else if (l == 0 && p.spawn_cap) {
+      LR_TRY(launch_spawn_scatter(desc, 0, R_of(1), var + p.off_srraw, p.rank_bytes, spa.used,
+                                  (uint32_t *)(var + p.off_supre), p.raw_cap, s));
+      LR_TRY(launch_finalize(desc, 0, work0, rec16_0, var + p.off_srraw, R_of(0), p.rank_bytes, p.cap[0],
+                             err, nullptr, nullptr, nullptr, s));
+    } else
       LR_TRY(launch_finalize(desc, l, work_of(l), l > 0 || rec16_0, R_of(l + 1), R_of(l),
                              p.rank_bytes, p.cap[l], err, T_of(l + 1), T_of(l), tid_of(l), s));
   }
@@ -1031,13 +1085,32 @@ size_t lr_workspace_size_outputs(int64_t n_total, int32_t k, const lr_outputs *o
   const bool extras = outs && (outs->term || outs->prefix || outs->inclusive_tail);
   const bool log0 = u.logmode && !extras && k == 0 && opts->wtype == LR_NONE && opts->rtype == LR_I32 &&
                     (uint64_t)n_total > u.cutoff && n_total <= ((int64_t)1 << 30);
+  const bool spawn0 = u.spawn != 0 && u.xchg != 0 && !log0 && !extras;
   Plan p = make_plan((uint64_t)n_total, h, u, opts->wtype != LR_NONE,
                      opts->rtype == LR_I64 ? 8 : 4, opts->seed, 256 * 16, false, log0, extras,
-                     extras && !outs->term);
+                     extras && !outs->term, spawn0);
   return p.fixed_bytes + p.var_bytes;
 }
 
 lr_status lr_get_device_status(lr_stream stream) { return device_status((cudaStream_t)stream); }
+
+int32_t lr_level_sizes(lr_stream stream, int64_t *sizes, int32_t max_levels) {
+  lr_status st;
+  Ctx *c = get_ctx((cudaStream_t)stream, &st);
+  if (!c || !c->last_desc || c->last_nlev <= 0) return 0;
+  LevelDesc d[kMaxLevels + 1];
+  if (cudaMemcpyAsync(d, c->last_desc, sizeof(LevelDesc) * c->last_nlev, cudaMemcpyDeviceToHost,
+                      (cudaStream_t)stream) != cudaSuccess ||
+      cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+    return -1;
+  int32_t used = 0;
+  for (int l = 0; l < c->last_nlev; ++l) {
+    if (d[l].mode == kModeOff) break;
+    if (sizes && used < max_levels) sizes[used] = d[l].n;
+    ++used;
+  }
+  return used;
+}
 
 lr_status lr_profile_enable(int32_t on) {
   std::lock_guard<std::mutex> g(g_mu);

@@ -10,7 +10,7 @@
 namespace lr {
 
 struct Tuning {
-  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, logmode, algo, contract;
+  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, logmode, algo, contract, spawn;
 };
 
 struct Plan {
@@ -34,6 +34,9 @@ struct Plan {
   // variable part
   size_t off_work[kMaxLevels + 1], off_R[kMaxLevels + 1];
   size_t off_hA, off_hB, off_ns, off_pd[4];
+  uint32_t spawn_cap;               // ruler spawning at level 0: most spawned rulers (0: off)
+  uint32_t raw_cap;                 //   ids of level 1 before compaction
+  size_t off_sraw, off_sused, off_supre, off_sctr, off_srraw, spawn_zero;
   bool term;                        // terminal ids carried through the levels
   size_t off_T[kMaxLevels + 1], off_tid[kMaxLevels + 1], off_T0, off_hC, off_pdt[2];
   size_t off_log, off_hdr, off_pairs, off_pairsB, off_hist, off_histB;   // log path
@@ -57,6 +60,8 @@ struct Ctx {
   size_t contract2_bytes = 0;
   uint32_t *host_words = nullptr;   // [0] device error bits, [1] head count, [8..9] int64 scratch
   bool pending_status = false;
+  const LevelDesc *last_desc = nullptr;   // level descriptors of the last ruling-set call
+  int last_nlev = 0;
 };
 
 // Tuning of a call: the caller's fields, else LR_TUNING, else the autotuned
@@ -70,7 +75,7 @@ bool tuned_lookup(int64_t n, bool weighted, bool batch, lr_tuning *out);
 // level-0 terminal ids (when the caller does not receive them).
 Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,
                uint64_t seed, int chase_grid, bool force_srs, bool log0, bool term = false,
-               bool t0ws = false);
+               bool t0ws = false, bool spawn0 = false);
 int chase_grid_for(const Tuning &u, bool rec16, bool log0);
 Ctx *get_ctx(cudaStream_t stream, lr_status *st);
 // Forget the context of a stream that is about to be destroyed (waits for

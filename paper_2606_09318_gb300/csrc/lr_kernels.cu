@@ -21,6 +21,7 @@
 // Section 2.5; walking succ forward from each ruler makes both unnecessary).
 #include <atomic>
 #include <cstdio>
+#include <cstring>
 
 #include "lr_kernels.h"
 
@@ -61,6 +62,7 @@ __global__ void k_init(LevelDesc *desc, InitParams p) {
     x.seed = p.seed[l];
     x.rounds = p.pd_rounds;
     x.hsrc = l == 0 ? (uint32_t)kHeadsBitmap : (uint32_t)kHeadsList;
+    x.nraw = 0;
     desc[l] = x;
   }
 }
@@ -483,11 +485,19 @@ __device__ __forceinline__ Rec visit(Rec *p, uint32_t cid, uint64_t off) {
 // TERM: a ruler whose segment ends at a terminal y becomes a terminal of the
 // next level; it records y's original id (y itself at level 0, tid_cur[y]
 // deeper) in tid_next, so the terminal of every element can be carried back.
-template <class Rec, bool XCHG, bool TERM>
+//
+// SPAWN (Section 2.2, ruler spawning; exchange chase only): a thread whose
+// CTA has no queued ruler left claims an unvisited, unsampled element of its
+// CTA's slice of ids as a new ruler (one exchange writes the claim mark and
+// the thread's reserved id R + k), and chases from it.  A wave that meets a
+// claimed element stops there, its next ruler; a queued head that a spawner
+// claimed first becomes a zero-weight link to the spawned ruler.  Ids that
+// were reserved but never claimed leave holes, removed after the chase.
+template <class Rec, bool XCHG, bool TERM, bool SPAWN>
 __global__ void __launch_bounds__(512)
 k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__restrict__ next,
         const uint32_t *__restrict__ ns, uint32_t *__restrict__ qctr, uint32_t *__restrict__ err,
-        const uint32_t *__restrict__ tid_cur, uint32_t *__restrict__ tid_next) {
+        const uint32_t *__restrict__ tid_cur, uint32_t *__restrict__ tid_next, SpawnArgs sp) {
   const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
   const uint32_t n = d.n, r = d.r;
@@ -498,12 +508,54 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
   const uint32_t hi = (uint32_t)(R * (blockIdx.x + 1) / gridDim.x);
   uint32_t *q = qctr + blockIdx.x;
   uint32_t visited = 0, bad = 0;
+  uint32_t myid = kEnd;                                  // SPAWN: reserved, not yet claimed
+  const uint32_t slo = (uint32_t)((uint64_t)n * blockIdx.x / gridDim.x);
+  const uint32_t shi = (uint32_t)((uint64_t)n * (blockIdx.x + 1) / gridDim.x);
   uint64_t c64 = (uint64_t)lo + atomicAdd(q, 1u);
-  while (c64 < hi) {
-    const uint64_t cnext = (uint64_t)lo + atomicAdd(q, 1u);
-    const uint32_t c = (uint32_t)c64;
-    const uint32_t rho = c < r ? P.inv(c) : __ldcg(ns + (c - r));
-    Rec v = visit<XCHG>(work + rho, c, 0);
+  for (;;) {
+    uint32_t c, rho;
+    Rec v;
+    if (c64 < hi) {
+      const uint64_t cnext = (uint64_t)lo + atomicAdd(q, 1u);
+      c = (uint32_t)c64;
+      rho = c < r ? P.inv(c) : __ldcg(ns + (c - r));
+      v = visit<XCHG>(work + rho, c, 0);
+      c64 = cnext;
+      if constexpr (SPAWN) {
+        if (rec_is_claim(v)) {                           // a spawner took this head first
+          const uint32_t cs = rec_tag(v);
+          st_rec(work + rho, cs, 0);                     // it stays the spawned ruler's
+          __stcg(reinterpret_cast<uint4 *>(next + c), make_uint4(cs, kUnvisited, 0u, 0u));
+          continue;
+        }
+      }
+    } else if constexpr (SPAWN) {
+      bool got = false;
+      for (;;) {
+        if (myid == kEnd) {
+          const uint32_t k = atomicAdd(sp.ctr, 1u);
+          if (k >= sp.cap) break;                        // out of ids: the wave dies
+          myid = (uint32_t)R + k;
+        }
+        const uint32_t u = slo + atomicAdd(sp.cursor + blockIdx.x, 1u);
+        if (u >= shi) break;                             // nothing unvisited left here
+        if (P.fwd(u) < r) continue;                      // a sampled ruler: the queue chases it
+        if (rec_tag(ld_rec(work + u)) != kUnvisited) continue;
+        const Rec old = claim_rec(work + u, myid);
+        if (rec_tag(old) != kUnvisited) { st_raw(work + u, old); continue; }   // lost it: put it back
+        const uint32_t k = myid - (uint32_t)R;
+        atomicOr(sp.used + (k >> 5), 1u << (k & 31u));
+        c = myid;
+        rho = u;
+        v = old;
+        myid = kEnd;
+        got = true;
+        break;
+      }
+      if (!got) break;
+    } else {
+      break;
+    }
     uint64_t o = rec_weight(v, rho);
     uint32_t steps = 1, nxt = c;
     bad |= rec_tag(v) != kUnvisited;
@@ -519,6 +571,15 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
           break;
         }
         v = visit<XCHG>(work + y, c, o);
+        if constexpr (SPAWN) {
+          if (rec_is_claim(v)) {     // reached a spawned ruler
+            const uint32_t cs = rec_tag(v);
+            st_rec(work + y, cs, 0);
+            nxt = cs;
+            if (cs == c) bad |= 2u;  // its own: a cycle
+            break;
+          }
+        }
         ++steps;
         if (rec_tag(v) != kUnvisited) { bad |= 1u; break; }   // second predecessor
         o += rec_weight(v, y);
@@ -537,7 +598,6 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
       if (tend != kEnd) tid_next[c] = tid_cur ? __ldcg(tid_cur + tend) : tend;
     }
     visited += steps;
-    c64 = cnext;
   }
   if (bad & 1u) record_error(err, kErrNotList);
   if (bad & 2u) record_error(err, kErrCycle);
@@ -548,15 +608,24 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
 
 cudaError_t launch_chase(LevelDesc *desc, int lev, void *work, bool rec16, void *next_work,
                          const uint32_t *ns, uint32_t *qctr, int grid, int block, uint32_t *err,
-                         int xchg, const uint32_t *tid_cur, uint32_t *tid_next, cudaStream_t s) {
+                         int xchg, const uint32_t *tid_cur, uint32_t *tid_next, const SpawnArgs *spawn,
+                         cudaStream_t s) {
   Rec16 *nx = reinterpret_cast<Rec16 *>(next_work);
-#define LR_CHASE(REC, X, T)                                                                          k_chase<REC, X, T><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<REC *>(work), nx, ns, qctr,                                             err, tid_cur, tid_next)
-  if (tid_next) {
-    if (rec16) { if (xchg) LR_CHASE(Rec16, true, true); else LR_CHASE(Rec16, false, true); }
-    else { if (xchg) LR_CHASE(Rec8, true, true); else LR_CHASE(Rec8, false, true); }
+  SpawnArgs sp;
+  memset(&sp, 0, sizeof(sp));
+  if (spawn) sp = *spawn;
+#define LR_CHASE(REC, X, T, SP) \
+  k_chase<REC, X, T, SP><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<REC *>(work), nx, ns, qctr, err, \
+                                                tid_cur, tid_next, sp)
+  if (spawn) {
+    if (rec16) LR_CHASE(Rec16, true, false, true);
+    else LR_CHASE(Rec8, true, false, true);
+  } else if (tid_next) {
+    if (rec16) { if (xchg) LR_CHASE(Rec16, true, true, false); else LR_CHASE(Rec16, false, true, false); }
+    else { if (xchg) LR_CHASE(Rec8, true, true, false); else LR_CHASE(Rec8, false, true, false); }
   } else {
-    if (rec16) { if (xchg) LR_CHASE(Rec16, true, false); else LR_CHASE(Rec16, false, false); }
-    else { if (xchg) LR_CHASE(Rec8, true, false); else LR_CHASE(Rec8, false, false); }
+    if (rec16) { if (xchg) LR_CHASE(Rec16, true, false, false); else LR_CHASE(Rec16, false, false, false); }
+    else { if (xchg) LR_CHASE(Rec8, true, false, false); else LR_CHASE(Rec8, false, false, false); }
   }
 #undef LR_CHASE
   count_launch();
@@ -565,8 +634,8 @@ cudaError_t launch_chase(LevelDesc *desc, int lev, void *work, bool rec16, void 
 
 int chase_occupancy(bool rec16, int block) {
   int nb = 0;
-  if (rec16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chase<Rec16, false, false>, block, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chase<Rec8, false, false>, block, 0);
+  if (rec16) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chase<Rec16, false, false, false>, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_chase<Rec8, false, false, false>, block, 0);
   return nb > 0 ? nb : 1;
 }
 
@@ -599,7 +668,7 @@ k_finalize(const LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ 
            const uint32_t *__restrict__ tid_cur) {
   const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
-  const uint32_t n = d.n, nn = desc[lev + 1].n;
+  const uint32_t n = d.n, nn = d.nraw ? d.nraw : desc[lev + 1].n;
   uint32_t bad = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0 && d.visited != n) bad |= kErrCycle;
   const uint32_t ngroups = (uint32_t)(((uint64_t)n + 3u) / 4u);
@@ -713,6 +782,105 @@ cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec
     else { if (rank_bytes == 4) LR_FIN(Rec8, uint32_t, false); else LR_FIN(Rec8, unsigned long long, false); }
   }
 #undef LR_FIN
+  count_launch();
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- spawning: compaction
+// Spawned ruler ids R + k that were handed out but never claimed leave holes.
+// The next level is compacted: id c keeps c below R, and a claimed spawned
+// id R + k becomes R + (claimed spawned ids before it).  The ranks are
+// scattered back to the original ids before this level's propagation.
+__device__ __forceinline__ uint32_t spawn_map(uint32_t c, uint32_t R, const uint32_t *used,
+                                              const uint32_t *upre) {
+  if (c < R) return c;
+  const uint32_t k = c - R;
+  return R + __ldg(upre + (k >> 5)) + (uint32_t)__popc(__ldcg(used + (k >> 5)) & ((1u << (k & 31u)) - 1u));
+}
+
+// Prefix of the claimed-id bitmap (one CTA) and the next level's size and mode.
+__global__ void __launch_bounds__(1024)
+k_spawn_scan(LevelDesc *desc, int lev, int nlev, const uint32_t *__restrict__ ctr, uint32_t cap,
+             const uint32_t *__restrict__ used, uint32_t *__restrict__ upre, uint32_t cutoff,
+             uint32_t has_pd, uint32_t *__restrict__ err) {
+  __shared__ uint64_t sm[33];
+  LevelDesc &d = desc[lev];
+  if (d.mode != kModeSrs) return;
+  const uint32_t handed = min(*ctr, cap);
+  const uint32_t words = (handed + 31) / 32;
+  const uint32_t per = (words + blockDim.x - 1) / blockDim.x;
+  const uint32_t a = threadIdx.x * per, b = min(words, a + per);
+  uint64_t s = 0;
+  for (uint32_t w = a; w < b; ++w) s += __popc(used[w]);
+  uint64_t total;
+  uint64_t run = block_exclusive_scan(s, sm, &total);
+  for (uint32_t w = a; w < b; ++w) { upre[w] = (uint32_t)run; run += __popc(used[w]); }
+  if (threadIdx.x == 0) {
+    LevelDesc &e = desc[lev + 1];
+    const uint64_t R = (uint64_t)d.r + d.k;
+    const uint64_t n1 = R + total;
+    d.nraw = (uint32_t)(R + handed);
+    if (n1 > e.cap) { record_error(err, kErrCapacity); d.mode = kModeOff; return; }
+    uint32_t mode = kModeSrs;
+    if (n1 <= cutoff) mode = kModeBase;
+    else if (lev + 1 >= nlev - 1) { if (has_pd) mode = kModePd; else { record_error(err, kErrCapacity); d.mode = kModeOff; return; } }
+    e.n = (uint32_t)n1;
+    e.r = (uint32_t)((n1 + e.f_inv - 1) / e.f_inv);
+    e.mode = mode;
+  }
+}
+
+// The next level's records at compacted ids, successors remapped.
+__global__ void k_spawn_compact(const LevelDesc *__restrict__ desc, int lev, const Rec16 *__restrict__ raw,
+                                Rec16 *__restrict__ out, const uint32_t *__restrict__ used,
+                                const uint32_t *__restrict__ upre) {
+  const LevelDesc d = desc[lev];
+  if (d.mode != kModeSrs || d.nraw == 0) return;
+  const uint32_t R = d.r + d.k;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < d.nraw; c += gridDim.x * blockDim.x) {
+    if (c >= R && !((__ldcg(used + ((c - R) >> 5)) >> ((c - R) & 31u)) & 1u)) continue;   // a hole
+    const uint4 v = __ldcg(reinterpret_cast<const uint4 *>(raw + c));
+    const uint32_t s = v.x < d.nraw ? spawn_map(v.x, R, used, upre) : v.x;
+    __stcg(reinterpret_cast<uint4 *>(out + spawn_map(c, R, used, upre)), make_uint4(s, v.y, v.z, v.w));
+  }
+}
+
+// Ranks of the compacted next level back at the original ids.
+template <class RT>
+__global__ void k_spawn_scatter(const LevelDesc *__restrict__ desc, int lev, const RT *__restrict__ rc,
+                                RT *__restrict__ rraw, const uint32_t *__restrict__ used,
+                                const uint32_t *__restrict__ upre) {
+  const LevelDesc d = desc[lev];
+  if (d.mode != kModeSrs || d.nraw == 0) return;
+  const uint32_t R = d.r + d.k;
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < d.nraw; c += gridDim.x * blockDim.x) {
+    if (c >= R && !((__ldcg(used + ((c - R) >> 5)) >> ((c - R) & 31u)) & 1u)) continue;
+    rraw[c] = __ldcg(rc + spawn_map(c, R, used, upre));
+  }
+}
+
+cudaError_t launch_spawn_compact(LevelDesc *desc, int lev, int nlev, const uint32_t *ctr, uint32_t cap,
+                                 const uint32_t *used, uint32_t *upre, const void *raw, void *out,
+                                 uint32_t raw_cap, uint32_t cutoff, uint32_t has_pd, uint32_t *err,
+                                 cudaStream_t s) {
+  k_spawn_scan<<<1, 1024, 0, s>>>(desc, lev, nlev, ctr, cap, used, upre, cutoff, has_pd, err);
+  k_spawn_compact<<<stream_grid(raw_cap, 256), 256, 0, s>>>(desc, lev, reinterpret_cast<const Rec16 *>(raw),
+                                                           reinterpret_cast<Rec16 *>(out), used, upre);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spawn_scatter(LevelDesc *desc, int lev, const void *rc, void *rraw, int rank_bytes,
+                                 const uint32_t *used, const uint32_t *upre, uint32_t raw_cap,
+                                 cudaStream_t s) {
+  const int grid = stream_grid(raw_cap, 256);
+  if (rank_bytes == 4)
+    k_spawn_scatter<uint32_t><<<grid, 256, 0, s>>>(desc, lev, reinterpret_cast<const uint32_t *>(rc),
+                                                   reinterpret_cast<uint32_t *>(rraw), used, upre);
+  else
+    k_spawn_scatter<unsigned long long><<<grid, 256, 0, s>>>(
+        desc, lev, reinterpret_cast<const unsigned long long *>(rc),
+        reinterpret_cast<unsigned long long *>(rraw), used, upre);
   count_launch();
   return cudaGetLastError();
 }

@@ -59,9 +59,30 @@ cudaError_t launch_heads(LevelDesc *desc, int lev, int nlev, const uint32_t *bit
 // Terminal ids (all optional; null when the call does not ask for them):
 // tid_cur/tid_next hold the original id of each terminal of this/the next
 // level (written by the chase), tout/tnext the terminal of every element.
+// Ruler spawning at one level (k_chase with SPAWN): spawned ids are
+// R + k for k < cap, R = the level's initial rulers.
+struct SpawnArgs {
+  uint32_t *ctr;      // ids handed out so far
+  uint32_t cap;       // most spawned ids
+  uint32_t *used;     // bitmap: spawned id R + k became a ruler
+  uint32_t *cursor;   // per CTA: candidates examined in its slice of ids
+};
+
+// After a spawning chase at level lev: compact the next level's records
+// (raw -> out, raw_cap ids at most), set its size and mode; and, once it is
+// ranked, scatter its ranks back to the original ids.
+cudaError_t launch_spawn_compact(LevelDesc *desc, int lev, int nlev, const uint32_t *ctr, uint32_t cap,
+                                 const uint32_t *used, uint32_t *upre, const void *raw, void *out,
+                                 uint32_t raw_cap, uint32_t cutoff, uint32_t has_pd, uint32_t *err,
+                                 cudaStream_t s);
+cudaError_t launch_spawn_scatter(LevelDesc *desc, int lev, const void *rc, void *rraw, int rank_bytes,
+                                 const uint32_t *used, const uint32_t *upre, uint32_t raw_cap,
+                                 cudaStream_t s);
+
 cudaError_t launch_chase(LevelDesc *desc, int lev, void *work, bool rec16, void *next_work,
                          const uint32_t *ns, uint32_t *qctr, int grid, int block, uint32_t *err,
-                         int xchg, const uint32_t *tid_cur, uint32_t *tid_next, cudaStream_t s);
+                         int xchg, const uint32_t *tid_cur, uint32_t *tid_next, const SpawnArgs *spawn,
+                         cudaStream_t s);
 
 cudaError_t launch_base(LevelDesc *desc, int lev, const void *work, bool rec16, void *rout,
                         int rank_bytes, uint32_t cutoff, uint32_t *err, const uint32_t *tid,
