@@ -62,7 +62,7 @@ __device__ __forceinline__ bool lc_is_head(uint32_t x, const uint32_t *hb) {
   return (__ldcg(hb + (x >> 5)) >> (x & 31u)) & 1u;
 }
 
-constexpr uint32_t kSub = 8;           // every kSub-th local id is a sub-ruler (mode A)
+constexpr uint32_t kSubDefault = 8;    // every ksub-th local id is a sub-ruler (dense tiles)
 constexpr uint32_t kMaxSr = 2 * kLcThreads;   // sub-rulers ranked by pointer doubling
 
 // Shared-memory state of one tile.
@@ -74,8 +74,8 @@ struct LcTile {
                              // its local tail once known (kEnd16 between tiles)
   VT off[kTile];             // link weight; then offset from the sub-ruler; per sub-ruler: distance
   uint32_t pred[kTileWords]; // has-local-predecessor bitmap
-  uint16_t srl[kMaxSr];      // dense tiles: heads whose id is not a multiple of kSub
-  uint32_t nheads, nlinks, nextra, dense;
+  uint16_t srl[kMaxSr];      // dense tiles: heads whose id is not a multiple of ksub
+  uint32_t nheads, nlinks, nextra, dense, submask;
 };
 
 template <class VT>
@@ -84,11 +84,11 @@ __device__ __forceinline__ bool lc_head(const LcTile<VT> &S, uint32_t j) {
 }
 
 // Sub-rulers: the local heads, and in dense tiles (few heads, long local
-// sublists) also every kSub-th id.  A walk never enters a local head, so
+// sublists) also every ksub-th id.  A walk never enters a local head, so
 // "the next element is a sub-ruler" is an arithmetic test.
 template <class VT>
 __device__ __forceinline__ bool lc_is_sr(const LcTile<VT> &S, uint32_t j) {
-  return lc_head(S, j) || (S.dense && (j % kSub) == 0);
+  return lc_head(S, j) || (S.dense && (j & S.submask) == 0);
 }
 
 // One element of the load: succ, local link, weight; marks its target.
@@ -118,11 +118,14 @@ __device__ __forceinline__ void lc_load1(LcTile<VT> &S, uint32_t j, uint32_t s, 
 // a cycle.  Returns the tile length.
 template <int WT, class VT>
 __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *succ, const void *weight,
-                                  uint32_t n, uint32_t *err, bool vec) {
+                                  uint32_t n, uint32_t *err, bool vec, uint32_t ksub) {
   const uint32_t base = t << kTileShift;
   const uint32_t len = min(kTile, n - base);
   const uint32_t lane = threadIdx.x & 31u;
-  if (threadIdx.x == 0) { S.nheads = 0; S.nlinks = 0; S.nextra = 0; }
+  const uint32_t submask = ksub - 1u;
+  // the ids of one bitmap word that are multiples of ksub (2 <= ksub <= 32)
+  const uint32_t mulbits = ksub >= 32 ? 1u : (0xFFFFFFFFu / ((1u << ksub) - 1u));
+  if (threadIdx.x == 0) { S.nheads = 0; S.nlinks = 0; S.nextra = 0; S.submask = submask; }
   uint32_t bad = 0, links = 0;
   // load, four elements per thread and step
   for (uint32_t g = threadIdx.x; g * 4 < len; g += blockDim.x) {
@@ -163,7 +166,7 @@ __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *suc
     if (lane == 0) S.pred[j >> 5] = word;
   }
   __syncthreads();
-  // heads per tile; in dense tiles also the heads that are not multiples of kSub
+  // heads per tile; in dense tiles also the heads that are not multiples of ksub
   if (threadIdx.x < 32) {
     uint32_t hw[4], cnt = 0, extra = 0;
 #pragma unroll
@@ -172,12 +175,12 @@ __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *suc
       const uint32_t valid = lo >= len ? 0u : (len - lo >= 32 ? 0xFFFFFFFFu : ((1u << (len - lo)) - 1u));
       hw[q] = ~S.pred[w] & valid;
       cnt += __popc(hw[q]);
-      extra += __popc(hw[q] & ~0x01010101u);           // bit b is a multiple of kSub = 8 iff b % 8 == 0
+      extra += __popc(hw[q] & ~mulbits);              // heads off the ksub grid
     }
     const uint32_t heads = __reduce_add_sync(0xFFFFFFFFu, cnt);
     const uint32_t marked = len - heads;
     if (marked < S.nlinks) bad |= kErrNotList;            // two links into one element
-    const bool dense = heads + (len + kSub - 1) / kSub <= kMaxSr;
+    const bool dense = heads + (len + ksub - 1) / ksub <= kMaxSr;
     if (dense) {
       uint32_t incl = extra;
       for (int d = 1; d < 32; d <<= 1) {
@@ -187,7 +190,7 @@ __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *suc
       uint32_t pos = incl - extra;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        uint32_t bits = hw[q] & ~0x01010101u;
+        uint32_t bits = hw[q] & ~mulbits;
         while (bits) {
           const uint32_t b = __ffs(bits) - 1;
           bits &= bits - 1u;
@@ -200,12 +203,12 @@ __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *suc
   }
   __syncthreads();
   const bool dense = S.dense;
-  const uint32_t nmul = (len + kSub - 1) / kSub;
+  const uint32_t nmul = (len + ksub - 1) / ksub;
   const uint32_t nsr = dense ? nmul + S.nextra : len;
   // level 1
   for (uint32_t p = threadIdx.x; p < nsr; p += blockDim.x) {
     uint32_t j = p;
-    if (dense) j = p < nmul ? p * kSub : S.srl[p - nmul];
+    if (dense) j = p < nmul ? p * ksub : S.srl[p - nmul];
     else if (!lc_head(S, j)) continue;
     uint32_t x = j, steps = 0;
     VT o = 0;
@@ -217,7 +220,7 @@ __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *suc
       S.off[x] = o;
       if (y == kEnd16) { tail = (uint16_t)x; break; }
       o += wx;
-      if (dense && (y % kSub) == 0) { nx = y; break; }
+      if (dense && (y & submask) == 0) { nx = y; break; }
       x = y;
       if (++steps > len) { bad |= kErrCycle; break; }
     }
@@ -237,7 +240,7 @@ __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *suc
       for (int e = 0; e < 2; ++e) {
         const uint32_t p = threadIdx.x + e * kLcThreads;
         if (p < nsr) {
-          const uint32_t j = p < nmul ? p * kSub : S.srl[p - nmul];
+          const uint32_t j = p < nmul ? p * ksub : S.srl[p - nmul];
           const uint16_t a = S.nxt[j];
           if (a != kEnd16) { tv[e] = S.off[j] + S.off[a]; tn[e] = S.nxt[a]; tt[e] = S.sub[a]; }
           else { tv[e] = S.off[j]; tn[e] = kEnd16; tt[e] = S.sub[j]; }
@@ -248,7 +251,7 @@ __device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *suc
       for (int e = 0; e < 2; ++e) {
         const uint32_t p = threadIdx.x + e * kLcThreads;
         if (p < nsr) {
-          const uint32_t j = p < nmul ? p * kSub : S.srl[p - nmul];
+          const uint32_t j = p < nmul ? p * ksub : S.srl[p - nmul];
           S.nxt[j] = tn[e]; S.off[j] = tv[e]; S.sub[j] = tt[e];
         }
       }
@@ -312,14 +315,15 @@ template <int WT, class VT, class RT>
 __global__ void __launch_bounds__(kLcThreads, WT == 0 ? 4 : 3)
 k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, uint32_t n,
            RT *__restrict__ rank, uint16_t *__restrict__ tail16, uint32_t *__restrict__ hb,
-           uint16_t *__restrict__ wpre, uint32_t *__restrict__ tcnt, uint32_t *__restrict__ err, int vec) {
+           uint16_t *__restrict__ wpre, uint32_t *__restrict__ tcnt, uint32_t *__restrict__ err, int vec,
+           uint32_t ksub) {
   extern __shared__ __align__(16) unsigned char lc_smem[];
   LcTile<VT> &S = *reinterpret_cast<LcTile<VT> *>(lc_smem);
   const uint32_t ntiles = (n + kTile - 1) >> kTileShift;
   for (uint32_t j = threadIdx.x; j < kTile; j += blockDim.x) S.sub[j] = kEnd16;
   __syncthreads();
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint32_t len = lc_tile_solve<WT, VT>(S, t, succ, weight, n, err, vec != 0);
+    const uint32_t len = lc_tile_solve<WT, VT>(S, t, succ, weight, n, err, vec != 0, ksub);
     const uint32_t base = t << kTileShift;
     bool cyc = false;
     for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
@@ -497,7 +501,8 @@ cudaError_t lc_setup() {
 
 cudaError_t launch_lc_solve(const uint32_t *succ, const void *weight, int wtype, uint32_t n, void *rank,
                             int rank_bytes, uint16_t *tail16, uint32_t *hb, uint16_t *wpre, uint32_t *tcnt,
-                            uint32_t *tpre, uint32_t *err, cudaStream_t s) {
+                            uint32_t *tpre, uint32_t *err, uint32_t ksub, cudaStream_t s) {
+  if (ksub < 2 || ksub > 32 || (ksub & (ksub - 1))) ksub = kSubDefault;
   const uint32_t nt = lc_tiles(n);
   const size_t sm = lc_smem_bytes(wtype != 0, rank_bytes);
   const int per_sm = wtype ? 3 : 4;
@@ -505,7 +510,7 @@ cudaError_t launch_lc_solve(const uint32_t *succ, const void *weight, int wtype,
   const int vec = ((uintptr_t)succ & 15u) == 0 && ((uintptr_t)weight & 15u) == 0;
 #define LC_SOLVE(W, V, R)                                                                          \
   k_lc_solve<W, V, R><<<grid, kLcThreads, sm, s>>>(succ, weight, n, reinterpret_cast<R *>(rank), tail16, \
-                                                   hb, wpre, tcnt, err, vec)
+                                                   hb, wpre, tcnt, err, vec, ksub)
   if (wtype == 0) { if (rank_bytes == 4) LC_SOLVE(0, uint32_t, uint32_t); else LC_SOLVE(0, uint32_t, unsigned long long); }
   else if (wtype == 1) { if (rank_bytes == 4) LC_SOLVE(1, uint64_t, uint32_t); else LC_SOLVE(1, uint64_t, unsigned long long); }
   else { if (rank_bytes == 4) LC_SOLVE(2, uint64_t, uint32_t); else LC_SOLVE(2, uint64_t, unsigned long long); }
