@@ -103,11 +103,12 @@ typedef struct lr_tuning {
  * contracted in shared memory to one node, the ruling set ranks the list of
  * those nodes, and a final pass restores every element.  It pays when links
  * mostly stay inside tiles (locality and identity orders).  Auto (the
- * default) samples 16384 links first and contracts when at least half stay
- * inside their tile; it applies to single-instance calls that count their
- * lists anyway (max_lists == 0, no workspace, not during capture, no extra
- * outputs, n >= 16384).  LR_CONTRACT_ON skips the sample; LR_CONTRACT_OFF
- * never contracts.  Results are identical either way.
+ * default) lets the prep pass count the links that stay inside their tile
+ * and contracts when at least half do, decided at the wait that counts the
+ * lists; it applies to single-instance calls that count their lists anyway
+ * (max_lists == 0, no workspace, not during capture, no extra outputs,
+ * n >= 16384).  LR_CONTRACT_ON contracts without counting;
+ * LR_CONTRACT_OFF never contracts.  Results are identical either way.
  */
 #define LR_CONTRACT_AUTO 0u
 #define LR_CONTRACT_OFF 1u

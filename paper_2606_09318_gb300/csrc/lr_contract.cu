@@ -23,10 +23,11 @@
 // over the few sub-rulers: O(tile) work, unlike pointer doubling over the
 // whole tile's O(tile log tile).
 //
-// Passes: sample (decides whether contraction pays), count (head bitmap per
-// tile), scan (tile prefixes), build (contracted list), the ruling set on
-// the contracted list, final (ranks).  The count, build and final passes
-// stream succ (and weights) once each: about 16 B per element unweighted.
+// Passes: solve (every tile in shared memory: distances to the local tails,
+// the local-head bitmap), scan (tile prefixes), nodes (the contracted
+// list), the ruling set on the contracted list, tails and fix (the ranks).
+// Whether to contract is decided by the caller from the prep pass's count
+// of links that stay inside their tile.
 #include <algorithm>
 #include <cuda_runtime.h>
 
@@ -37,7 +38,7 @@ namespace lr {
 
 namespace {
 
-constexpr int kTileShift = 12;
+constexpr int kTileShift = kContractTileShift;
 constexpr uint32_t kTile = 1u << kTileShift;
 constexpr uint32_t kTileWords = kTile / 32;
 constexpr int kLcThreads = 512;
@@ -279,20 +280,6 @@ __device__ __forceinline__ uint16_t lc_elem(const LcTile<VT> &S, uint32_t j, VT 
 }
 }  // namespace
 
-// Fraction of sampled elements whose link stays inside its tile.
-__global__ void k_lc_sample(const uint32_t *__restrict__ succ, uint32_t n, uint32_t samples,
-                            uint32_t *__restrict__ out) {
-  uint32_t c = 0;
-  const uint64_t stride = n / samples;
-  for (uint32_t k = threadIdx.x; k < samples; k += blockDim.x) {
-    const uint32_t i = (uint32_t)(k * stride);
-    const uint32_t s = __ldg(succ + i);
-    c += s < n && s != i && (s >> kTileShift) == (i >> kTileShift);
-  }
-  for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xFFFFFFFFu, c, d);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, c);
-}
-
 // Exclusive prefix of the tile counts (one CTA); tpre[ntiles] = total.
 __global__ void __launch_bounds__(1024)
 k_lc_scan(const uint32_t *__restrict__ tcnt, uint32_t ntiles, uint32_t *__restrict__ tpre) {
@@ -477,13 +464,6 @@ size_t lc_smem_bytes(bool weighted, int rank_bytes) {
 
 uint32_t lc_tiles(uint64_t n) { return (uint32_t)((n + kTile - 1) >> kTileShift); }
 uint32_t lc_tile_words() { return kTileWords; }
-
-cudaError_t launch_lc_sample(const uint32_t *succ, uint32_t n, uint32_t samples, uint32_t *out,
-                             cudaStream_t s) {
-  k_lc_sample<<<1, 1024, 0, s>>>(succ, n, samples, out);
-  count_launch();
-  return cudaGetLastError();
-}
 
 cudaError_t lc_setup() {
   cudaError_t e = cudaSuccess;

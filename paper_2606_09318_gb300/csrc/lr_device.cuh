@@ -23,6 +23,7 @@ constexpr int kHeadBlocks = 512;               // CTAs of the head-selection ker
 constexpr int kHeadThreads = 256;
 constexpr int kBaseThreads = 1024;             // single-CTA base case
 constexpr uint32_t kMaxCutoff = 12288;         // largest base-case level (SMEM bound)
+constexpr int kContractTileShift = 12;         // tile-local contraction: tiles of 4096 ids
 
 // error bits recorded on the device (mapped to lr_status by the host)
 enum : uint32_t {

@@ -177,7 +177,7 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
   p.off_zero = o;
   p.off_err = o; o = align_up(o + 16);
   p.off_hcount = o; o = align_up(o + 16);
-  p.off_acc = o; o = align_up(o + 16);
+  p.off_acc = o; o = align_up(o + 32);        // sums of terminals, successors; local links
   p.off_ovf = o; o = align_up(o + 16);
   p.off_bctr = o; o = align_up(o + sizeof(uint32_t) * 256);
   p.off_q = o; o = align_up(o + sizeof(uint32_t) * (size_t)chase_grid * kMaxLevels);
@@ -490,7 +490,7 @@ static lr_status run_wyllie(const Inputs &in, Ctx *c, cudaStream_t s) {
   // without validation the scratch sums stand in for the bitmap, so the
   // pass issues no per-element atomics
   LR_TRY(launch_prep0(in.succ, in.weight, in.wtype, (uint32_t)in.n, A, bitmap, err, in.validate,
-                      in.offsets, in.k, in.validate ? nullptr : sums, s));
+                      in.offsets, in.k, in.validate ? nullptr : sums, nullptr, s));
   prof.mark(PH_PREP);
   LR_TRY(launch_wyllie(A, B, w16, (uint32_t)in.n, in.rank, in.rank_bytes, err, s));
   prof.mark(PH_BASE);
@@ -505,14 +505,13 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s);
 // form, through run() itself), restore every element.  Returns
 // LR_ERR_NOT_FOUND (nothing enqueued that writes outputs) when the exact
 // count shows that contraction would not shrink the list enough.
-static lr_status run_contracted(const Inputs &in, const lr_tuning *tuning, Ctx *c, bool decided,
+static lr_status run_contracted(const Inputs &in, const lr_tuning *tuning, Ctx *c, bool forced,
                                 cudaStream_t s) {
   const uint32_t n = (uint32_t)in.n;
   const uint32_t nt = lc_tiles(n);
   const size_t words = (size_t)nt * lc_tile_words();
   size_t o = 0;
   const size_t off_err = o; o = align_up(o + 16);
-  const size_t off_tmp = o; o = align_up(o + 16);
   const size_t off_hb = o; o = align_up(o + 4 * words);
   const size_t off_wpre = o; o = align_up(o + 2 * words);
   const size_t off_tcnt = o; o = align_up(o + 4 * (size_t)nt);
@@ -522,16 +521,7 @@ static lr_status run_contracted(const Inputs &in, const lr_tuning *tuning, Ctx *
   if (st != LR_OK) return st;
   char *b = (char *)c->contract;
   uint32_t *err = (uint32_t *)(b + off_err);
-  uint32_t *tmp = (uint32_t *)(b + off_tmp);
   LR_TRY(cudaMemsetAsync(b, 0, off_hb, s));
-  if (!decided) {
-    // sample: how many links stay inside their tile
-    const uint32_t samples = 16384;
-    LR_TRY(launch_lc_sample(in.succ, n, samples, tmp, s));
-    LR_TRY(cudaMemcpyAsync(c->host_words + 1, tmp, 4, cudaMemcpyDeviceToHost, s));
-    LR_TRY(cudaStreamSynchronize(s));
-    if (c->host_words[1] * 2 < samples) return LR_ERR_NOT_FOUND;
-  }
   Profiler prof;
   prof.begin(s, (int64_t)in.n);
   c->last_nlev = 0;
@@ -545,7 +535,7 @@ static lr_status run_contracted(const Inputs &in, const lr_tuning *tuning, Ctx *
   LR_TRY(cudaMemcpyAsync(c->host_words + 1, tpre + nt, 4, cudaMemcpyDeviceToHost, s));
   LR_TRY(cudaStreamSynchronize(s));
   const uint64_t m = c->host_words[1];
-  if (!decided && m * 5 > (uint64_t)n * 3) { prof.cancel(); return LR_ERR_NOT_FOUND; }
+  if (!forced && m * 5 > (uint64_t)n * 3) { prof.cancel(); return LR_ERR_NOT_FOUND; }
   // the contracted list: successors, weights (int32 unweighted: at most one
   // tile's links; int64 weighted), ranks in the caller's type
   const int wc = in.wtype == 0 ? 1 : 2;
@@ -611,12 +601,16 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
                     in.rank_bytes == 4 && in.n > u.cutoff && in.n <= (1ull << 30);
   const bool t0ws = extras && in.term == nullptr;
   const bool spawn0 = u.spawn != 0 && u.xchg != 0 && !log0 && !extras && !ptrs;
-  if (u.contract != LR_CONTRACT_OFF && !in.no_contract && !ptrs && in.offsets == nullptr && !extras &&
-      in.ws == nullptr && in.ctx == nullptr && !capturing && in.max_lists <= 0 &&
-      in.n >= 16384 && in.n <= 0xFFFFFFFEull) {
-    const lr_status cs = run_contracted(in, tuning, c, u.contract == LR_CONTRACT_ON, s);
+  // tile-local contraction: forced, or decided from the prep pass's count of
+  // links that stay inside their tile (read with the list count, no extra wait)
+  const bool contractible = u.contract != LR_CONTRACT_OFF && !in.no_contract && !ptrs &&
+                            in.offsets == nullptr && !extras && in.ws == nullptr && in.ctx == nullptr &&
+                            !capturing && in.max_lists <= 0 && in.n >= 16384 && in.n <= 0xFFFFFFFEull;
+  if (contractible && u.contract == LR_CONTRACT_ON) {
+    const lr_status cs = run_contracted(in, tuning, c, true, s);
     if (cs != LR_ERR_NOT_FOUND) return cs;
   }
+  const bool count_local = contractible && u.contract == LR_CONTRACT_AUTO && !log0;
   const int grid = chase_grid_for(u, rec16_0, log0);
   const bool need_count = in.max_lists <= 0 && (in.ws == nullptr || in.count_in_ws) &&
                           (in.n > u.cutoff || ptrs);
@@ -659,7 +653,8 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
                              in.validate, in.offsets, in.k, s));
   else
     LR_TRY(launch_prep0(in.succ, in.weight, in.wtype, (uint32_t)in.n, work0, bitmap, err,
-                        in.validate, in.offsets, in.k, sums0 ? acc : nullptr, s));
+                        in.validate, in.offsets, in.k, sums0 ? acc : nullptr, count_local ? acc + 2 : nullptr,
+                        s));
   if (need_count) {
     // count the lists (one wait), then size the recursion for exactly that many:
     // a single-instance pass counts terminals in its reduction, the batched
@@ -670,7 +665,19 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
       LR_TRY(launch_count_heads(bitmap, (uint32_t)in.n, hcount, s));
       LR_TRY(cudaMemcpyAsync(c->host_words + 1, hcount, 4, cudaMemcpyDeviceToHost, s));
     }
+    if (count_local)
+      LR_TRY(cudaMemcpyAsync(c->host_words + 2, acc + 2, 8, cudaMemcpyDeviceToHost, s));
     LR_TRY(cudaStreamSynchronize(s));
+    if (count_local) {
+      uint64_t local_links;
+      memcpy(&local_links, c->host_words + 2, 8);
+      if (local_links * 2 >= in.n) {           // at least half the links stay in their tile
+        prof.cancel();
+        const lr_status cs = run_contracted(in, tuning, c, false, s);
+        if (cs != LR_ERR_NOT_FOUND) return cs;
+        prof.begin(s, (int64_t)in.n);          // not contracted after all: carry on
+      }
+    }
     hb = std::max<uint64_t>(1, c->host_words[1]);
     p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws, spawn0);
   }

@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(256)
 k_prep0(const uint32_t *__restrict__ succ, const void *__restrict__ weight, uint32_t n,
         void *__restrict__ work, uint32_t *__restrict__ bitmap, uint32_t *__restrict__ err,
         int validate, int vec, const int64_t *__restrict__ offsets, int32_t k,
-        unsigned long long *__restrict__ sums) {
-  unsigned long long sT = 0, sS = 0;
+        unsigned long long *__restrict__ sums, unsigned long long *__restrict__ local) {
+  unsigned long long sT = 0, sS = 0, sL = 0;
   const uint32_t ngroups = (uint32_t)(((uint64_t)n + 3u) / 4u);
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
@@ -147,6 +147,7 @@ k_prep0(const uint32_t *__restrict__ succ, const void *__restrict__ weight, uint
     }
     for (uint32_t j = 0; j < cnt; ++j) {
       const uint32_t i = i0 + j;
+      if (local) sL += s[j] != i && (s[j] >> kContractTileShift) == (i >> kContractTileShift);
       if (s[j] != i) {
         if (sums) {
           sS += s[j];
@@ -193,11 +194,17 @@ k_prep0(const uint32_t *__restrict__ succ, const void *__restrict__ weight, uint
       if (sS) atomicAdd(sums + 1, sS);
     }
   }
+  if (local) {
+    // links that stay inside their contraction tile (decides whether to contract)
+    for (int d = 16; d > 0; d >>= 1) sL += __shfl_down_sync(0xFFFFFFFFu, sL, d);
+    if ((threadIdx.x & 31) == 0 && sL) atomicAdd(local, sL);
+  }
 }
 
 cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, uint32_t n,
                          void *work, uint32_t *bitmap, uint32_t *err, int validate,
-                         const int64_t *offsets, int32_t k, unsigned long long *sums, cudaStream_t s) {
+                         const int64_t *offsets, int32_t k, unsigned long long *sums,
+                         unsigned long long *local, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int block = 256;
   const int grid = stream_grid(((uint64_t)n + 3) / 4, block);
@@ -205,9 +212,9 @@ cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, ui
   if (wtype == 1) vec = vec && ((uintptr_t)weight & 15u) == 0;
   if (wtype == 2) vec = vec && ((uintptr_t)weight & 15u) == 0;
   switch (wtype) {
-    case 0: k_prep0<0><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k, sums); break;
-    case 1: k_prep0<1><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k, sums); break;
-    default: k_prep0<2><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k, sums); break;
+    case 0: k_prep0<0><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k, sums, local); break;
+    case 1: k_prep0<1><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k, sums, local); break;
+    default: k_prep0<2><<<grid, block, 0, s>>>(succ, weight, n, work, bitmap, err, validate, vec, offsets, k, sums, local); break;
   }
   count_launch();
   return cudaGetLastError();

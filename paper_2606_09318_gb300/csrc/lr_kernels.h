@@ -35,9 +35,11 @@ cudaError_t launch_init(LevelDesc *desc, const InitParams &p, cudaStream_t s);
 
 // Level-0 pass.  wtype 0/1/2 (none/i32/i64).  offsets != nullptr: batched
 // input with local successor ids (k instances).
+// local (optional): counts the links that stay inside their contraction tile.
 cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, uint32_t n,
                          void *work, uint32_t *bitmap, uint32_t *err, int validate,
-                         const int64_t *offsets, int32_t k, unsigned long long *sums, cudaStream_t s);
+                         const int64_t *offsets, int32_t k, unsigned long long *sums,
+                         unsigned long long *local, cudaStream_t s);
 
 cudaError_t launch_prep0_ptrs(const uint32_t *const *sptr, const void *const *wptr, int wtype,
                               uint32_t n, void *work, uint32_t *bitmap, uint32_t *err, int validate,
@@ -137,8 +139,6 @@ cudaError_t kernels_setup();
 uint32_t lc_tiles(uint64_t n);
 uint32_t lc_tile_words();
 cudaError_t lc_setup();
-cudaError_t launch_lc_sample(const uint32_t *succ, uint32_t n, uint32_t samples, uint32_t *out,
-                             cudaStream_t s);
 // Solve every tile (distances to the local tails into rank, tails into
 // tail16, the local-head bitmap and counts), then the tile prefixes.
 cudaError_t launch_lc_solve(const uint32_t *succ, const void *weight, int wtype, uint32_t n, void *rank,
