@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -350,11 +351,28 @@ struct ProfCall { std::vector<ProfMark> marks; int64_t n; int64_t launches; };
 static std::vector<ProfCall> g_prof_pending;
 static lr_profile g_prof_acc;
 
+// Per call: an NVTX range (always; free without an attached tool) whose
+// payload is n, NVTX marks at the phase boundaries, and, when profiling is
+// on, CUDA events at the same boundaries for lr_profile_read.
+static const char *const kPhaseNames[] = {"lr.prep", "lr.select", "lr.chase0", "lr.chase",
+                                          "lr.base", "lr.finalize"};
+
 struct Profiler {
   bool on = false;
+  bool ranged = false;
   ProfCall call;
   cudaStream_t s = nullptr;
   void begin(cudaStream_t st, int64_t n) {
+    nvtxEventAttributes_t a;
+    memset(&a, 0, sizeof(a));
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = "lr.call";
+    a.payloadType = NVTX_PAYLOAD_TYPE_INT64;
+    a.payload.llValue = n;
+    nvtxRangePushEx(&a);
+    ranged = true;
     on = g_prof && !stream_capturing(st);
     s = st;
     if (!on) return;
@@ -363,6 +381,7 @@ struct Profiler {
     mark(-1);
   }
   void mark(int phase) {
+    if (ranged && phase >= 0) nvtxMarkA(kPhaseNames[phase]);
     if (!on) return;
     ProfMark m;
     m.phase = phase;
@@ -371,18 +390,23 @@ struct Profiler {
     call.marks.push_back(m);
   }
   void end() {
+    if (ranged) { nvtxRangePop(); ranged = false; }
     if (!on) return;
+    on = false;
     call.launches = launch_count() - call.launches;
     std::lock_guard<std::mutex> g(g_mu);
     g_prof_pending.push_back(call);
   }
   // drop a call that turned out not to happen (its marks are not recorded)
   void cancel() {
+    if (ranged) { nvtxRangePop(); ranged = false; }
     if (!on) return;
     for (auto &m : call.marks) cudaEventDestroy(m.ev);
     call.marks.clear();
     on = false;
   }
+  // a call that returns early (an error) closes its range and drops its marks
+  ~Profiler() { cancel(); }
 };
 enum { PH_PREP = 0, PH_SELECT, PH_CHASE0, PH_CHASE, PH_BASE, PH_FINAL };
 

@@ -26,7 +26,6 @@ namespace lr {
 constexpr uint32_t kMark = 0x80000000u;    // log entry: a new segment of ruler (entry & ~kMark)
 constexpr uint32_t kLogEnd = 0xFFFFFFFFu;  // log entry: unused slot
 constexpr uint32_t kChunk = 32;            // entries per log chunk (128 bytes)
-constexpr int kBuckets = 256;
 
 // ---------------------------------------------------------------- heads by sums
 __global__ void __launch_bounds__(256)
