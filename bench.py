@@ -166,10 +166,17 @@ class ClockSampler:
 
 
 def kernel_source_hash():
+    """Hash of the source the level-0 chase kernel is built from: the device
+    header and the chase section of lr_kernels.cu."""
+    csrc = os.path.join(ROOT, "paper_2606_09318_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("lr_kernels.cu", "lr_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2606_09318_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    with open(os.path.join(csrc, "lr_device.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(csrc, "lr_kernels.cu"), "r") as fh:
+        text = fh.read()
+    a = text.index("// ---------------------------------------------------------------- chase")
+    b = text.index("// ---------------------------------------------------------------- finalize")
+    h.update(text[a:b].encode())
     return h.hexdigest()[:16]
 
 
