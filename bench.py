@@ -25,6 +25,7 @@ import argparse
 import hashlib
 import json
 import os
+import statistics
 import subprocess
 import sys
 import threading
@@ -251,18 +252,21 @@ def run_ours(args):
     lr.profile_enable(True)
     lr.profile_read(reset=True)
     launches0 = lr.kernel_launch_count()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # one event between consecutive steps: the whole region and every step's own time
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(lrk) as clk:
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for j in range(args.steps):
             step()
-        ev1.record(stream)
+            evs[j + 1].record(stream)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
+    ev0, ev1 = evs[0], evs[-1]
+    per_step = [evs[j].elapsed_time(evs[j + 1]) for j in range(args.steps)]
     launches = lr.kernel_launch_count() - launches0
     prof = lr.profile_read(reset=True)
     lr.profile_enable(False)
@@ -331,6 +335,9 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "step_ms": {"median": round(statistics.median(per_step), 4),
+                    "mean": round(statistics.fmean(per_step), 4),
+                    "min": round(min(per_step), 4), "max": round(max(per_step), 4)},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic: uniformly random-order single list (torch.randperm, seeded)",
         "config": {"workload": "single random-order list, n=2^28, unweighted, int32 ranks",
@@ -396,6 +403,44 @@ def run_reference(args):
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def run_reference_sweep(args):
+    """The oracle on the sizes and orders of the size sweep, one thread on the
+    host cores: random, locality (windows of 256) and identity order at
+    2^20, 2^24 and 2^28, and the random order at 2^30; unweighted, int32
+    ranks.  One JSON line per case (the best of --oracle-reps runs at
+    2^20 and 2^24, one run above), with the rank recurrence checked."""
+    ws, rk, _ = dist_env()
+    if rk != 0:
+        return
+    import numpy as np
+    import gen
+    import oracle
+    oracle.build()
+    cases = [(lg, kind) for lg in (int(x) for x in args.oracle_sizes.split(","))
+             for kind in ("random", "locality", "identity")]
+    if args.oracle_top:
+        cases.append((args.oracle_top, "random"))
+    for lg, kind in cases:
+        n = 1 << lg
+        succ = gen.list_of_order_kind(kind, n, gen.config_seed(2, lg))
+        reps = args.oracle_reps if lg <= 24 else 1
+        best = None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            r = oracle.rank(succ)
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        s64 = succ.astype(np.int64)
+        term = s64 == np.arange(n, dtype=np.int64)
+        ok = bool((r[~term].astype(np.int64) == r[s64[~term]].astype(np.int64) + 1).all()) \
+            and int(r[term].astype(np.int64).sum()) == 0 and int(term.sum()) == 1
+        print(json.dumps({"impl": "reference", "workload": "sweep", "kind": "oracle", "cores": 1,
+                          "n": n, "log2n": lg, "order": kind, "weights": "none -> int32 ranks",
+                          "runs": reps, "s": round(best, 4),
+                          "m_elem_s": round(n / best / 1e6, 3), "exact": ok}), flush=True)
+        del succ, r, s64, term
 
 
 def _device_random_order(m, g, dev):
@@ -740,6 +785,11 @@ def main():
                          "sweep: sizes and orders; pd: against whole-list pointer doubling")
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured requests")
     ap.add_argument("--sweep-sizes", default="24,26,28,30", help="sweep: log2 sizes")
+    ap.add_argument("--oracle-sizes", default="20,24,28",
+                    help="reference sweep: log2 sizes timed in all three orders")
+    ap.add_argument("--oracle-top", type=int, default=30,
+                    help="reference sweep: log2 size also timed in random order (0: none)")
+    ap.add_argument("--oracle-reps", type=int, default=3, help="reference sweep: runs at n <= 2^24")
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-streams", type=int, default=2)
     ap.add_argument("--load", type=float, default=0.8, help="serve: offered load / capacity guess")
@@ -748,7 +798,10 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload == "sweep":
+            run_reference_sweep(args)
+        else:
+            run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "serve":
