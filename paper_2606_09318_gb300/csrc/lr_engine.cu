@@ -209,13 +209,12 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
     p.shift = lg > 8 ? lg - 8 : 0;
     p.off_log = o; o = align_up(o + (size_t)p.total_chunks * 32 * 4);
     p.off_hdr = o; o = align_up(o + (size_t)p.total_chunks * 8);
-    uint32_t sB, na, kb, nw;
-    log_part_geometry((uint32_t)n, &sB, &na, &kb, &nw);
-    p.off_pairs = o; o = align_up(o + (size_t)n * 8);
-    p.off_pairsB = o; o = align_up(o + (sB ? (size_t)n * 8 : 0));
-    p.part_ctas = std::max(1, std::min(chase_grid, 152 * 8));
-    p.off_hist = o; o = align_up(o + (size_t)p.part_ctas * 256 * 4);
-    p.off_histB = o; o = align_up(o + (size_t)std::max<uint32_t>(1, na * kb) * 256 * 4);
+    p.lg = log_geometry((uint32_t)n);
+    p.off_pairs = o; o = align_up(o + (size_t)p.lg.na * p.lg.capA * 8);
+    p.off_pairsB = o; o = align_up(o + (size_t)p.lg.nw * p.lg.capB * 8);
+    p.off_cur = o;
+    p.cur_bytes = 4 * ((size_t)p.lg.na + p.lg.nbB);           // claimed slots per region
+    o = align_up(o + p.cur_bytes);
   }
   p.off_hA = o; o = align_up(o + 4 * (size_t)p.hcap);
   p.off_hB = o; o = align_up(o + 4 * (size_t)p.hcap);
@@ -741,7 +740,10 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     spa.cursor = (uint32_t *)(var + p.off_sctr + 16);
   }
   uint32_t *hA0 = (uint32_t *)(var + p.off_hA);
-  if (log0) LR_TRY(cudaMemsetAsync(var + p.off_hdr, 0xFF, (size_t)p.total_chunks * 8, s));
+  if (log0) {
+    LR_TRY(cudaMemsetAsync(var + p.off_hdr, 0xFF, (size_t)p.total_chunks * 8, s));
+    LR_TRY(cudaMemsetAsync(var + p.off_cur, 0, p.cur_bytes, s));
+  }
   if (log0 || sums0)
     LR_TRY(launch_heads0_log(desc, acc, hA0, in.succ, (uint32_t)in.n, bitmap, err, in.validate, s));
 
@@ -809,9 +811,8 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     if (l == 0 && log0)
       LR_TRY(launch_finalize_log(desc, (const uint32_t *)(var + p.off_log), (const uint2 *)(var + p.off_hdr),
                                  p.total_chunks, R_of(1), (uint2 *)(var + p.off_pairs),
-                                 (uint2 *)(var + p.off_pairsB), (uint32_t *)(var + p.off_hist),
-                                 (uint32_t *)(var + p.off_histB), p.part_ctas, (uint32_t *)in.rank,
-                                 (uint32_t)in.n, err, s));
+                                 (uint2 *)(var + p.off_pairsB), (uint32_t *)(var + p.off_cur),
+                                 (uint32_t *)(var + p.off_cur) + p.lg.na, p.lg, (uint32_t *)in.rank, err, s));
     else if (l == 0 && ptrs)
       LR_TRY(launch_finalize_ptrs(desc, work0, rec16_0, R_of(1), in.rptr, p.rank_bytes, p.cap[0],
                                   in.offsets, in.k, err, s));

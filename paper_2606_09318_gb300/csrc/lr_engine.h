@@ -6,6 +6,7 @@
 
 #include "lr.h"
 #include "lr_device.cuh"
+#include "lr_kernels.h"
 
 namespace lr {
 
@@ -39,9 +40,10 @@ struct Plan {
   size_t off_sraw, off_sused, off_supre, off_sctr, off_srraw, spawn_zero;
   bool term;                        // terminal ids carried through the levels
   size_t off_T[kMaxLevels + 1], off_tid[kMaxLevels + 1], off_T0, off_hC, off_pdt[2];
-  size_t off_log, off_hdr, off_pairs, off_pairsB, off_hist, off_histB;   // log path
+  size_t off_log, off_hdr, off_pairs, off_pairsB, off_cur;   // log path
   uint32_t per_cta, total_chunks, shift;
-  int part_ctas;
+  size_t cur_bytes;
+  LogGeom lg;
   size_t var_bytes;
 };
 

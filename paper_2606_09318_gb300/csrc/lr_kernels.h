@@ -124,11 +124,17 @@ cudaError_t launch_chase_log(LevelDesc *desc, const uint32_t *succ, void *next_w
                              uint32_t *qctr, int grid, int block, uint32_t *err, uint32_t *log,
                              uint2 *hdr, uint32_t per_cta, uint32_t total_chunks, uint32_t *ovf,
                              cudaStream_t s);
-cudaError_t launch_finalize_log(LevelDesc *desc, const uint32_t *log, const uint2 *hdr,
-                                uint32_t total_chunks, const void *r1, uint2 *pairsA, uint2 *pairsB,
-                                uint32_t *histA, uint32_t *histB, int ga, uint32_t *rank, uint32_t n,
-                                uint32_t *err, cudaStream_t s);
-void log_part_geometry(uint32_t n, uint32_t *sB, uint32_t *na, uint32_t *kb, uint32_t *nw);
+// Geometry of the log path's propagation (lr_log.cu): windows of 2^14 ranks;
+// level A partitions into na buckets of 2^shiftA ids (regions of capA pairs,
+// gridA CTAs, claims of claimA slots); with sB > 0, level B splits each
+// A-bucket into its 2^sB windows (kb CTAs per A-bucket, regions of capB).
+struct LogGeom {
+  uint32_t nw, sB, na, shiftA, gridA, claimA, capA, kb, claimB, capB, nbB;
+};
+LogGeom log_geometry(uint32_t n);
+cudaError_t launch_finalize_log(LevelDesc *desc, const uint32_t *log, const uint2 *hdr, uint32_t total_chunks,
+                                const void *r1, uint2 *pairsA, uint2 *pairsB, uint32_t *curA, uint32_t *curB,
+                                const LogGeom &g, uint32_t *rank, uint32_t *err, cudaStream_t s);
 cudaError_t log_setup();
 int chase_log_occupancy(int block);
 

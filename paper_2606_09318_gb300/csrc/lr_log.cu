@@ -270,32 +270,54 @@ int chase_log_occupancy(int block) {
 // log with its ruler c and offset o; its rank is R_1[c] - o and must land at
 // rank[y].  Writing 4-byte ranks at random y costs a DRAM access each on
 // GB300, so the pairs (y, rank) are first sorted by y into windows of
-// 2^kLgWin elements (a two-level radix partition whose writes are whole
-// 32-byte sectors), then each window is assembled in shared memory and
-// written out as whole lines.
+// 2^kLgWin elements (a radix partition, one level or two), then each window
+// is assembled in shared memory and written out as whole lines.
 //   level A: decode the log, partition by A-bucket (y >> (kLgWin + sB));
 //   level B: partition each A-bucket by window (only when there are more
 //            windows than one level can hold);
 //   scatter: one CTA per window.
-// Each pass is count / offsets / write, with no global atomics: the region
-// of every bucket is fixed (exactly its index range, for a valid list) and
-// the per-CTA offsets inside it come from a column scan of the counts.
+// No histogram pass: for a valid list a bucket receives exactly the elements
+// of its index range, so each bucket owns a region of that size plus slack,
+// and a CTA claims room in it with one global atomic per block of `claim`
+// slots.  Every store covers a whole 32-byte sector (four pairs): a CTA
+// carries fewer than four leftover pairs of a bucket into its next tile and,
+// at its end, fills the unused part of its last block with empty pairs
+// (y = kLogEnd), which the consumers skip.
 constexpr int kLgWin = 14;                 // 16384 ranks = 64 KiB of shared memory
 constexpr int kMaxBuckets = 256;
-constexpr int kPartThreads = 256;
+constexpr int kPartThreads = 512;
 constexpr int kIpt = 8;                    // items a thread holds per partition tile
 constexpr int kPartTile = kPartThreads * kIpt;
+constexpr int kSortCap = kPartTile + 6 * kMaxBuckets;   // runs padded to whole quads
 constexpr int kDecodeIlp = 4;              // chunks a warp decodes with their loads in flight
+constexpr uint32_t kDead = 0xFFFFFFFFu;    // bucket region overflowed (invalid input)
+constexpr int kScatterThreads = 512;
 
 struct PartSmem {
+  uint2 sorted[kSortCap];                  // this tile's pairs, bucket by bucket
   uint2 carry[kMaxBuckets * 4];            // < 4 leftover pairs per bucket
-  uint32_t ccnt[kMaxBuckets];
-  uint32_t gpos[kMaxBuckets];              // next global slot of each bucket
-  uint32_t tcnt[kMaxBuckets];
-  uint32_t toff[kMaxBuckets + 1];          // + total
-  uint32_t tcur[kMaxBuckets];
-  uint32_t fstart[kMaxBuckets + 1];        // first whole sector of each bucket in this tile
-  uint2 sorted[kPartTile];
+  uint32_t cnt[kMaxBuckets];               // this tile's pairs per bucket (reset once read)
+  uint32_t ccnt[kMaxBuckets];              // carried pairs per bucket
+  uint32_t pos[kMaxBuckets];               // next free slot of the bucket's current block
+  uint32_t left[kMaxBuckets];              // free slots left in it (a multiple of 4), or kDead
+  uint32_t tstart[kMaxBuckets];            // this tile: first slot of the bucket's run in `sorted`
+  uint32_t tcc[kMaxBuckets];               // this tile: carried pairs at the head of the run
+  uint32_t tm[kMaxBuckets];                // this tile: run length
+  uint32_t tpos[kMaxBuckets];              // this tile: the current block's free slot ...
+  uint32_t tleft[kMaxBuckets];             // ... and room, and the block claimed for the rest
+  uint32_t tnpos[kMaxBuckets];
+  uint32_t wsum[32];
+  uint16_t qb[kSortCap / 4];               // bucket of every quad of `sorted`
+};
+
+// Output of one partition: bucket b owns out[b * cap, (b + 1) * cap); cur[b]
+// counts the slots claimed in it.
+struct PartOut {
+  uint2 *out;
+  uint32_t *cur;
+  uint32_t cap;          // slots per region
+  uint32_t claim;        // slots per claim (a multiple of 4)
+  uint32_t nb;           // buckets (<= kMaxBuckets)
 };
 
 // Decode kDecodeIlp chunks of the log per warp: all header and entry loads
@@ -331,190 +353,151 @@ __device__ __forceinline__ void decode_ilp(const uint32_t *__restrict__ log, con
   }
 }
 
-// Whole-range decode (histogram pass): f(y) for every element.
-template <class F>
-__device__ __forceinline__ void decode_chunks(const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
-                                              uint32_t c0, uint32_t c1, uint32_t n, F &&f) {
-  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  for (uint32_t base = c0 + (uint32_t)warp * kDecodeIlp; base < c1; base += (uint32_t)nwarps * kDecodeIlp) {
-    uint2 it[kDecodeIlp];
-    uint32_t off[kDecodeIlp];
-    decode_ilp(log, hdr, base, c1, n, it, off);
+// Exclusive scan of v over the block's threads (all threads call it, at most
+// 32 warps); the total comes back through `total`.
+__device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t *wsum, uint32_t &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint32_t x = v;
 #pragma unroll
-    for (int j = 0; j < kDecodeIlp; ++j)
-      if (it[j].x != kLogEnd) f(it[j].x);
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+    if (lane >= d) x += y;
   }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  uint32_t t = lane < nwarps ? wsum[lane] : 0u;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, d);
+    if (lane >= d) t += y;
+  }
+  const uint32_t before = __shfl_sync(0xFFFFFFFFu, t, warp > 0 ? warp - 1 : 0);
+  total = __shfl_sync(0xFFFFFFFFu, t, 31);
+  __syncthreads();                                   // wsum may be reused after this
+  return (warp > 0 ? before : 0u) + x - v;
 }
 
-// Exclusive scan of nb (<= 256) shared-memory counts by warp 0; returns the
-// total through out[nb].
-__device__ __forceinline__ void warp0_scan(const uint32_t *in, uint32_t *out, int nb) {
-  const int lane = threadIdx.x & 31;
-  if ((threadIdx.x >> 5) != 0) return;
-  uint32_t run = 0;
-  for (int b0 = 0; b0 < nb; b0 += 32) {
-    const int b = b0 + lane;
-    const uint32_t v = b < nb ? in[b] : 0u;
-    uint32_t x = v;
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-      if (lane >= d) x += y;
+__device__ __forceinline__ void part_init(PartSmem &S, uint32_t nb) {
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+    S.cnt[b] = 0; S.ccnt[b] = 0; S.pos[b] = 0; S.left[b] = 0;
+  }
+  __syncthreads();
+}
+
+// One tile of register-held pairs (item[i].x != kLogEnd: a pair, bk[i] its
+// bucket) -> bucket runs in shared memory, laid out so that every aligned
+// quad of `sorted` is one quad of its bucket's output -> whole-sector stores.
+__device__ void part_tile(PartSmem &S, const PartOut &P, const uint2 (&item)[kIpt],
+                          const uint32_t (&bk)[kIpt], uint32_t &bad) {
+  const uint32_t tid = threadIdx.x, nb = P.nb;
+  uint32_t slot[kIpt];
+#pragma unroll
+  for (int i = 0; i < kIpt; ++i) slot[i] = item[i].x != kLogEnd ? atomicAdd(&S.cnt[bk[i]], 1u) : 0u;
+  __syncthreads();
+  uint32_t m = 0, alloc = 0;
+  if (tid < nb) {
+    m = S.ccnt[tid] + S.cnt[tid];
+    alloc = (m + 3u) & ~3u;
+  }
+  uint32_t total;
+  const uint32_t st = block_scan_excl(alloc, S.wsum, total);
+  if (tid < nb) {
+    const uint32_t b = tid, cc = S.ccnt[b], full = m & ~3u;
+    uint32_t p = S.pos[b], l = S.left[b], np = 0;
+    S.cnt[b] = 0;
+    S.tstart[b] = st;
+    S.tcc[b] = cc;
+    S.tm[b] = m;
+    if (l != kDead && full > l) {                   // claim room for what the block lacks
+      const uint32_t x = full - l;
+      const uint32_t c = (x + P.claim - 1u) / P.claim * P.claim;
+      const uint32_t o = atomicAdd(P.cur + b, c);
+      if ((uint64_t)o + c > P.cap) {
+        bad |= kErrNotList;                          // more pairs than the bucket's range holds
+        l = kDead;
+      } else {
+        np = o;
+        S.pos[b] = o + x;
+        S.left[b] = c - x;
+      }
+    } else if (l != kDead) {
+      S.pos[b] = p + full;
+      S.left[b] = l - full;
     }
-    if (b < nb) out[b] = run + x - v;
-    run += __shfl_sync(0xFFFFFFFFu, x, 31);
+    if (l == kDead) S.left[b] = kDead;
+    S.tpos[b] = p;
+    S.tleft[b] = l;
+    S.tnpos[b] = np;
+    S.ccnt[b] = m - full;
+    for (uint32_t k = 0; k < cc; ++k) S.sorted[st + k] = S.carry[b * 4 + k];
+    for (uint32_t q = st / 4; q < (st + alloc) / 4; ++q) S.qb[q] = (uint16_t)b;
   }
-  if (lane == 0) out[nb] = run;
-}
-
-// One tile of register-held items (item[i] valid when item[i].x != kLogEnd,
-// bk[i] its bucket) -> sorted by bucket in shared memory -> whole-sector
-// stores.  gpos/ccnt/carry persist across tiles: each bucket's output
-// continues its carry, so every store but a bucket's first (unaligned) head
-// and its final tail covers a whole 32-byte sector, one thread per sector.
-// lim: size of `out`; positions past it (only possible for an invalid list,
-// which the count scan reports) are dropped.
-__device__ void part_emit_tile(PartSmem &S, int nb, const uint2 (&item)[kIpt], const uint32_t (&bk)[kIpt],
-                               uint2 *__restrict__ out, uint32_t lim, uint32_t &bad) {
-  const int tid = threadIdx.x;
+  __syncthreads();
 #pragma unroll
   for (int i = 0; i < kIpt; ++i)
-    if (item[i].x != kLogEnd) atomicAdd(&S.tcnt[bk[i]], 1u);
+    if (item[i].x != kLogEnd) S.sorted[S.tstart[bk[i]] + S.tcc[bk[i]] + slot[i]] = item[i];
   __syncthreads();
-  warp0_scan(S.tcnt, S.toff, nb);
+  const uint32_t nq = total / 4;
+  for (uint32_t q = tid; q < nq; q += blockDim.x) {
+    const uint32_t b = S.qb[q];
+    const uint32_t k = 4 * q - S.tstart[b], rm = S.tm[b];
+    if (k + 4 <= rm) {
+      const uint32_t l = S.tleft[b];
+      if (l == kDead) continue;
+      const uint32_t dst = k < l ? S.tpos[b] + k : S.tnpos[b] + (k - l);
+      const uint4 *src = reinterpret_cast<const uint4 *>(S.sorted + 4 * q);
+      const uint4 u = src[0], v = src[1];
+      st_sector(P.out + (size_t)b * P.cap + dst, u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w);
+    } else {
+      for (uint32_t j = k; j < rm; ++j) S.carry[b * 4 + (j - k)] = S.sorted[4 * q + (j - k)];
+    }
+  }
   __syncthreads();
+}
+
+// End of a CTA's input: the carried pairs of each bucket, padded with empty
+// pairs, and empty pairs in the rest of its last block.
+__device__ void part_flush(PartSmem &S, const PartOut &P, uint32_t &bad) {
+  for (uint32_t b = threadIdx.x; b < P.nb; b += blockDim.x) {
+    uint32_t l = S.left[b], p = S.pos[b];
+    const uint32_t r = S.ccnt[b];
+    if (l == kDead || (r == 0 && l == 0)) continue;
+    if (l == 0) {
+      const uint32_t o = atomicAdd(P.cur + b, P.claim);
+      if ((uint64_t)o + P.claim > P.cap) {
+        bad |= kErrNotList;
+        continue;
+      }
+      p = o;
+      l = P.claim;
+    }
+    uint2 *dst = P.out + (size_t)b * P.cap + p;
+    if (r > 0) {
+      uint2 q[4];
 #pragma unroll
-  for (int i = 0; i < kIpt; ++i)
-    if (item[i].x != kLogEnd) S.sorted[S.toff[bk[i]] + atomicAdd(&S.tcur[bk[i]], 1u)] = item[i];
-  __syncthreads();                                   // placement done before tcur is reused
-  // per bucket: pairs up to the next sector boundary (h), whole sectors (f)
-  for (int b = tid; b < nb; b += blockDim.x) {
-    const uint32_t m = S.ccnt[b] + S.tcnt[b], g = S.gpos[b];
-    const uint32_t h = min(m, (4u - (g & 3u)) & 3u);
-    S.tcur[b] = (m - h) / 4u;                        // reuse: whole sectors of bucket b
-  }
-  __syncthreads();
-  warp0_scan(S.tcur, S.fstart, nb);
-  __syncthreads();
-  auto seq = [&](int b, uint32_t k) -> uint2 {
-    const uint32_t c = S.ccnt[b];
-    return k < c ? S.carry[b * 4 + k] : S.sorted[S.toff[b] + k - c];
-  };
-  const uint32_t nsec = S.fstart[nb];
-  for (uint32_t sct = tid; sct < nsec; sct += blockDim.x) {
-    int lo = 0, hi = nb;                              // bucket: last b with fstart[b] <= sct
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (S.fstart[mid] <= sct) lo = mid; else hi = mid;
+      for (uint32_t k = 0; k < 4; ++k) q[k] = k < r ? S.carry[b * 4 + k] : make_uint2(kLogEnd, 0u);
+      st_sector(dst, q[0].x, q[0].y, q[1].x, q[1].y, q[2].x, q[2].y, q[3].x, q[3].y);
+      dst += 4;
+      l -= 4;
     }
-    const int b = lo;
-    const uint32_t g = S.gpos[b];
-    const uint32_t h = min(S.ccnt[b] + S.tcnt[b], (4u - (g & 3u)) & 3u);
-    const uint32_t k = h + 4u * (sct - S.fstart[b]);
-    const uint2 a = seq(b, k), bb = seq(b, k + 1), cc = seq(b, k + 2), dd = seq(b, k + 3);
-    if ((uint64_t)g + k + 3 < lim) st_sector(out + g + k, a.x, a.y, bb.x, bb.y, cc.x, cc.y, dd.x, dd.y);
-    else bad |= kErrNotList;
-  }
-  __syncthreads();                                   // sector writers done with carry/gpos/ccnt
-  // heads and new carries: one thread per bucket (reads before it writes)
-  for (int b = tid; b < nb; b += blockDim.x) {
-    const uint32_t m = S.ccnt[b] + S.tcnt[b], g = S.gpos[b];
-    const uint32_t h = min(m, (4u - (g & 3u)) & 3u);
-    for (uint32_t k = 0; k < h; ++k)
-      if ((uint64_t)g + k < lim) out[g + k] = seq(b, k);
-    const uint32_t used = h + 4u * ((m - h) / 4u), rest = m - used;
-    const uint2 k0 = rest > 0 ? seq(b, used) : make_uint2(0u, 0u);
-    const uint2 k1 = rest > 1 ? seq(b, used + 1) : make_uint2(0u, 0u);
-    const uint2 k2 = rest > 2 ? seq(b, used + 2) : make_uint2(0u, 0u);
-    if (rest > 0) S.carry[b * 4 + 0] = k0;
-    if (rest > 1) S.carry[b * 4 + 1] = k1;
-    if (rest > 2) S.carry[b * 4 + 2] = k2;
-    S.gpos[b] = g + used;
-    S.ccnt[b] = rest;
-    S.tcnt[b] = 0;
-    S.tcur[b] = 0;
-  }
-  __syncthreads();
-}
-
-__device__ void part_flush(PartSmem &S, int nb, uint2 *__restrict__ out, uint32_t lim) {
-  const int tid = threadIdx.x;
-  for (int b = tid; b < nb; b += blockDim.x)
-    for (uint32_t k = 0; k < S.ccnt[b]; ++k)
-      if ((uint64_t)S.gpos[b] + k < lim) out[S.gpos[b] + k] = S.carry[b * 4 + k];
-}
-
-__device__ void part_init(PartSmem &S, int nb, const uint32_t *__restrict__ offs) {
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    S.ccnt[b] = 0; S.tcnt[b] = 0; S.tcur[b] = 0;
-    S.gpos[b] = offs[b];
-  }
-  __syncthreads();
-}
-
-struct PartGeom {
-  uint32_t n;
-  uint32_t sB;          // level-B bits (windows per A-bucket = 2^sB)
-  uint32_t na;          // A-buckets
-  uint32_t kb;          // level-B CTAs per A-bucket
-  uint32_t nw;          // windows
-};
-
-__device__ __forceinline__ uint32_t bucket_a(uint32_t y, const PartGeom &G) { return y >> (kLgWin + G.sB); }
-__device__ __forceinline__ uint32_t bucket_b(uint32_t y, const PartGeom &G) {
-  return (y >> kLgWin) & ((1u << G.sB) - 1u);
-}
-
-// ---- level A
-__global__ void __launch_bounds__(kPartThreads)
-k_la_hist(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
-          uint32_t total_chunks, uint32_t *__restrict__ hist, PartGeom G) {
-  __shared__ uint32_t sh[kMaxBuckets];
-  if (desc[0].mode != kModeSrs) return;
-  for (int b = threadIdx.x; b < kMaxBuckets; b += blockDim.x) sh[b] = 0;
-  __syncthreads();
-  const uint32_t c0 = (uint32_t)((uint64_t)total_chunks * blockIdx.x / gridDim.x);
-  const uint32_t c1 = (uint32_t)((uint64_t)total_chunks * (blockIdx.x + 1) / gridDim.x);
-  decode_chunks(log, hdr, c0, c1, G.n, [&](uint32_t y) { atomicAdd(&sh[bucket_a(y, G)], 1u); });
-  __syncthreads();
-  for (int b = threadIdx.x; b < (int)G.na; b += blockDim.x) hist[(size_t)blockIdx.x * G.na + b] = sh[b];
-}
-
-// Column scan: counts[cta][bucket] -> start slot of each CTA's run inside the
-// bucket; bucket b's region starts at base(b).  shift: log2 of a bucket's
-// index span.  groups > 1: CTAs come in groups (level B: one group per
-// A-bucket, buckets are that group's windows).
-__global__ void k_part_scan(const LevelDesc *__restrict__ desc, uint32_t *__restrict__ hist, int nctas_per_group,
-                            int nbuckets, uint32_t shift, uint32_t n, uint32_t *__restrict__ err) {
-  if (desc[0].mode != kModeSrs) return;
-  const int group = blockIdx.x;
-  for (int b = threadIdx.x; b < nbuckets; b += blockDim.x) {
-    const uint64_t bucket = (uint64_t)group * nbuckets + b;
-    const uint64_t base = bucket << shift;
-    uint64_t run = base;
-    for (int k = 0; k < nctas_per_group; ++k) {
-      uint32_t *h = hist + ((size_t)group * nctas_per_group + k) * nbuckets + b;
-      const uint32_t v = *h;
-      *h = (uint32_t)run;
-      run += v;
-    }
-    const uint64_t end = base + (1ull << shift);
-    if (base < n && run > (end < n ? end : (uint64_t)n)) record_error(err, kErrNotList);
+    for (; l > 0; l -= 4, dst += 4) st_sector(dst, kLogEnd, 0u, kLogEnd, 0u, kLogEnd, 0u, kLogEnd, 0u);
   }
 }
 
-__global__ void __launch_bounds__(kPartThreads)
-k_la_write(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
-           uint32_t total_chunks, const uint32_t *__restrict__ offs, const uint32_t *__restrict__ r1,
-           uint2 *__restrict__ out, PartGeom G, uint32_t *__restrict__ err) {
+// ---- level A: decode the log, rank = R_1[ruler] - offset, partition by y >> shift
+__global__ void __launch_bounds__(kPartThreads, 2)
+k_part_log(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
+           uint32_t total_chunks, const uint32_t *__restrict__ r1, PartOut P, uint32_t shift,
+           uint32_t *__restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_part[];
   PartSmem &S = *reinterpret_cast<PartSmem *>(smem_part);
   const LevelDesc d = desc[0];
   if (d.mode != kModeSrs) return;
-  const uint32_t nn = desc[1].n;
-  part_init(S, G.na, offs + (size_t)blockIdx.x * G.na);
+  const uint32_t n = d.n, nn = desc[1].n;
+  part_init(S, P.nb);
   const uint32_t c0 = (uint32_t)((uint64_t)total_chunks * blockIdx.x / gridDim.x);
   const uint32_t c1 = (uint32_t)((uint64_t)total_chunks * (blockIdx.x + 1) / gridDim.x);
-  // a tile: every warp decodes 2 x kDecodeIlp chunks, each lane keeps its
+  // a tile: every warp decodes 2 x kDecodeIlp chunks; each lane keeps its
   // (at most one per chunk) elements in registers
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const uint32_t per_tile = (uint32_t)nwarps * 2 * kDecodeIlp;
@@ -526,99 +509,97 @@ k_la_write(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log,
     for (int r = 0; r < 2; ++r) {
       uint2 it[kDecodeIlp];
       uint32_t of[kDecodeIlp];
-      decode_ilp(log, hdr, t0 + ((uint32_t)r * nwarps + warp) * kDecodeIlp, c1, G.n, it, of);
+      decode_ilp(log, hdr, t0 + ((uint32_t)r * nwarps + warp) * kDecodeIlp, c1, n, it, of);
 #pragma unroll
       for (int j = 0; j < kDecodeIlp; ++j) { item[r * kDecodeIlp + j] = it[j]; off[r * kDecodeIlp + j] = of[j]; }
     }
 #pragma unroll
-    for (int i = 0; i < kIpt; ++i) {                // rank = R_1[ruler] - offset
+    for (int i = 0; i < kIpt; ++i) {
+      bk[i] = 0;
       if (item[i].x == kLogEnd) continue;
       const uint32_t c = item[i].y;
       uint32_t val = 0;
       if (c < nn) val = __ldcg(r1 + c) - off[i];
       else bad |= kErrInternal;
       item[i].y = val;
-      bk[i] = bucket_a(item[i].x, G);
+      bk[i] = item[i].x >> shift;
     }
-    part_emit_tile(S, G.na, item, bk, out, G.n, bad);
+    part_tile(S, P, item, bk, bad);
   }
-  part_flush(S, G.na, out, G.n);
+  part_flush(S, P, bad);
   if (bad) record_error(err, bad);
 }
 
-// ---- level B: CTA (a, i) handles part i of A-bucket a's region
-__device__ __forceinline__ void lb_range(const PartGeom &G, uint32_t &p0, uint32_t &p1) {
-  const uint32_t a = blockIdx.x / G.kb, i = blockIdx.x % G.kb;
-  const uint64_t s0 = (uint64_t)a << (kLgWin + G.sB);
-  const uint64_t e0 = s0 + (1ull << (kLgWin + G.sB));
-  const uint64_t s = s0 < G.n ? s0 : G.n, e = e0 < G.n ? e0 : G.n;
-  p0 = (uint32_t)(s + (e - s) * i / G.kb);
-  p1 = (uint32_t)(s + (e - s) * (i + 1) / G.kb);
-}
-
-__global__ void __launch_bounds__(kPartThreads)
-k_lb_hist(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, uint32_t *__restrict__ hist, PartGeom G) {
-  __shared__ uint32_t sh[kMaxBuckets];
-  if (desc[0].mode != kModeSrs) return;
-  const uint32_t nbk = 1u << G.sB;
-  for (int b = threadIdx.x; b < (int)nbk; b += blockDim.x) sh[b] = 0;
-  __syncthreads();
-  uint32_t p0, p1;
-  lb_range(G, p0, p1);
-  for (uint32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    const uint32_t y = __ldcs(&in[p].x);
-    if (y < G.n) atomicAdd(&sh[bucket_b(y, G)], 1u);
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < (int)nbk; b += blockDim.x) hist[(size_t)blockIdx.x * nbk + b] = sh[b];
-}
-
-__global__ void __launch_bounds__(kPartThreads)
-k_lb_write(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, const uint32_t *__restrict__ offs,
-           uint2 *__restrict__ out, PartGeom G, uint32_t *__restrict__ err) {
+// ---- level B: CTA (a, i) partitions part i of A-bucket a's region by window
+__global__ void __launch_bounds__(kPartThreads, 2)
+k_part_win(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, const uint32_t *__restrict__ cur_in,
+           uint32_t cap_in, uint32_t kb, uint32_t sB, PartOut P, uint32_t *__restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_part[];
   PartSmem &S = *reinterpret_cast<PartSmem *>(smem_part);
   if (desc[0].mode != kModeSrs) return;
-  const uint32_t nbk = 1u << G.sB;
-  part_init(S, nbk, offs + (size_t)blockIdx.x * nbk);
-  uint32_t p0, p1;
-  lb_range(G, p0, p1);
+  const uint32_t a = blockIdx.x / kb, i = blockIdx.x % kb;
+  const uint32_t len = min(__ldcg(cur_in + a), cap_in);
+  const uint32_t p0 = (uint32_t)((uint64_t)len * i / kb), p1 = (uint32_t)((uint64_t)len * (i + 1) / kb);
+  const uint2 *src = in + (size_t)a * cap_in;
+  PartOut Q = P;
+  Q.out = P.out + ((size_t)a << sB) * P.cap;
+  Q.cur = P.cur + ((size_t)a << sB);
+  part_init(S, Q.nb);
+  const uint32_t wmask = (1u << sB) - 1u;
   uint32_t bad = 0;
   for (uint32_t t0 = p0; t0 < p1; t0 += kPartTile) {
     uint2 item[kIpt];
     uint32_t bk[kIpt];
 #pragma unroll
-    for (int i = 0; i < kIpt; ++i) {
-      const uint32_t p = t0 + (uint32_t)i * blockDim.x + threadIdx.x;
-      item[i] = p < p1 ? __ldcs(in + p) : make_uint2(kLogEnd, 0u);
-      if (item[i].x != kLogEnd && item[i].x >= G.n) { bad |= kErrInternal; item[i].x = kLogEnd; }
-      bk[i] = item[i].x != kLogEnd ? bucket_b(item[i].x, G) : 0u;
+    for (int j = 0; j < kIpt; ++j) {
+      const uint32_t p = t0 + (uint32_t)j * blockDim.x + threadIdx.x;
+      item[j] = p < p1 ? __ldcs(src + p) : make_uint2(kLogEnd, 0u);
+      bk[j] = 0;
+      if (item[j].x == kLogEnd) continue;
+      if ((item[j].x >> (kLgWin + sB)) != a) {       // not this bucket's: never for pairs written above
+        bad |= kErrInternal;
+        item[j].x = kLogEnd;
+        continue;
+      }
+      bk[j] = (item[j].x >> kLgWin) & wmask;
     }
-    part_emit_tile(S, nbk, item, bk, out, G.n, bad);
+    part_tile(S, Q, item, bk, bad);
   }
-  part_flush(S, nbk, out, G.n);
+  part_flush(S, Q, bad);
   if (bad) record_error(err, bad);
 }
 
 // ---- scatter: one CTA per window of 2^kLgWin ranks assembled in shared memory
-__global__ void __launch_bounds__(256)
-k_win_scatter(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, uint32_t *__restrict__ rank,
-              uint32_t *__restrict__ err) {
+__global__ void __launch_bounds__(kScatterThreads)
+k_win_scatter(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, const uint32_t *__restrict__ cur,
+              uint32_t cap, uint32_t *__restrict__ rank, uint32_t *__restrict__ err) {
   extern __shared__ __align__(16) uint32_t win[];
+  uint32_t *s_count = win + (1u << kLgWin);
   const LevelDesc d = desc[0];
   if (d.mode != kModeSrs) return;
   const uint32_t n = d.n;
   const uint64_t w0 = (uint64_t)blockIdx.x << kLgWin;
   if (w0 >= n) return;
   const uint32_t len = (uint32_t)min((uint64_t)1 << kLgWin, (uint64_t)n - w0);
-  uint32_t bad = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0 && d.visited != n) bad |= d.visited > n ? kErrNotList : kErrCycle;
-  for (uint32_t p = threadIdx.x; p < len; p += blockDim.x) {
-    const uint2 v = __ldcs(in + w0 + p);
-    const uint64_t loc = (uint64_t)v.x - w0;
-    if (loc < len) win[loc] = v.y; else bad |= kErrInternal;
-  }
+  if (threadIdx.x == 0) *s_count = 0;
   __syncthreads();
+  uint32_t bad = 0, got = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && d.visited != n) bad |= d.visited > n ? kErrNotList : kErrCycle;
+  const uint32_t m = min(__ldcg(cur + blockIdx.x), cap);
+  const uint2 *src = in + (size_t)blockIdx.x * cap;
+  for (uint32_t p = threadIdx.x; p < m; p += blockDim.x) {
+    const uint2 v = __ldcs(src + p);
+    if (v.x == kLogEnd) continue;
+    const uint64_t loc = (uint64_t)v.x - w0;
+    if (loc < len) { win[loc] = v.y; ++got; } else bad |= kErrInternal;
+  }
+  for (int dd = 16; dd > 0; dd >>= 1) got += __shfl_down_sync(0xFFFFFFFFu, got, dd);
+  if ((threadIdx.x & 31) == 0 && got) atomicAdd(s_count, got);
+  __syncthreads();
+  // a window that did not receive each of its elements exactly once: some
+  // element was reached twice (and, as the chase visited n in all, another
+  // never), which only a list with in-degree > 1 produces
+  if (threadIdx.x == 0 && *s_count != len && d.visited == n) bad |= kErrNotList;
   uint32_t *dst = rank + w0;
   if ((len & 3u) == 0 && ((uintptr_t)dst & 15u) == 0) {
     for (uint32_t q = threadIdx.x; q < len / 4; q += blockDim.x)
@@ -630,49 +611,80 @@ k_win_scatter(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, 
 }
 
 // Host side: geometry and launch sequence.
-void log_part_geometry(uint32_t n, uint32_t *sB, uint32_t *na, uint32_t *kb, uint32_t *nw) {
-  const uint32_t w = (uint32_t)(((uint64_t)n + (1u << kLgWin) - 1) >> kLgWin);
-  uint32_t lg = 0;
-  while ((1ull << lg) < w) ++lg;
-  *sB = lg > 8 ? lg - 8 : 0;
-  *na = (w + (1u << *sB) - 1) >> *sB;
-  *kb = *sB ? std::max<uint32_t>(1, 1024 / *na) : 0;
-  *nw = w;
+static size_t part_smem() { return sizeof(PartSmem); }
+static size_t scatter_smem() { return (4u << kLgWin) + 16; }
+
+// Resident CTAs of the level-A kernel on the current device.  The workspace
+// size depends on it, so it is computed the same way whether or not the
+// device setup ran before (it sets the shared-memory attribute itself).
+static int part_resident_ctas() {
+  static int cached[64] = {0};
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev]) return cached[dev];
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+  if (cudaFuncSetAttribute(k_part_log, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem()) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_part_log, kPartThreads, part_smem()) != cudaSuccess ||
+      per <= 0)
+    per = 1;
+  cached[dev] = per * sms;
+  return cached[dev];
 }
 
-static size_t part_smem() { return sizeof(PartSmem); }
+LogGeom log_geometry(uint32_t n) {
+  LogGeom g;
+  g.nw = (uint32_t)(((uint64_t)n + (1u << kLgWin) - 1) >> kLgWin);
+  uint32_t lg = 0;
+  while ((1ull << lg) < g.nw) ++lg;
+  g.sB = lg > 8 ? lg - 8 : 0;
+  g.na = (g.nw + (1u << g.sB) - 1) >> g.sB;
+  g.shiftA = kLgWin + g.sB;
+  const uint64_t chunks_per_cta = 32;                       // a few tiles each at least
+  const uint64_t want = ((uint64_t)n / 32 + chunks_per_cta - 1) / chunks_per_cta;
+  g.gridA = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(part_resident_ctas(), want));
+  g.claimA = g.sB ? 32 : 8;
+  g.capA = (1u << g.shiftA) + g.gridA * g.claimA;
+  g.kb = g.sB ? std::max<uint32_t>(1, 2048 / g.na) : 0;
+  g.claimB = 16;
+  g.capB = g.sB ? (1u << kLgWin) + g.kb * g.claimB : 0;
+  g.nbB = g.sB ? (g.na << g.sB) : 0;
+  return g;
+}
 
 cudaError_t log_setup() {
-  cudaError_t e = cudaFuncSetAttribute(k_la_write, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem());
+  cudaError_t e = cudaFuncSetAttribute(k_part_log, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_lb_write, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem());
+  e = cudaFuncSetAttribute(k_part_win, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)part_smem());
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_win_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(4u << kLgWin));
+  return cudaFuncSetAttribute(k_win_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem());
 }
 
-cudaError_t launch_finalize_log(LevelDesc *desc, const uint32_t *log, const uint2 *hdr,
-                                uint32_t total_chunks, const void *r1, uint2 *pairsA, uint2 *pairsB,
-                                uint32_t *histA, uint32_t *histB, int ga, uint32_t *rank, uint32_t n,
-                                uint32_t *err, cudaStream_t s) {
-  PartGeom G;
-  G.n = n;
-  log_part_geometry(n, &G.sB, &G.na, &G.kb, &G.nw);
-  const uint32_t shiftA = kLgWin + G.sB;
-  k_la_hist<<<ga, kPartThreads, 0, s>>>(desc, log, hdr, total_chunks, histA, G);
-  k_part_scan<<<1, 256, 0, s>>>(desc, histA, ga, (int)G.na, shiftA, n, err);
-  k_la_write<<<ga, kPartThreads, part_smem(), s>>>(desc, log, hdr, total_chunks, histA,
-                                                   reinterpret_cast<const uint32_t *>(r1), pairsA, G, err);
-  const uint2 *final_pairs = pairsA;
-  int launches = 4;
-  if (G.sB > 0) {
-    const int gb = (int)(G.na * G.kb);
-    k_lb_hist<<<gb, kPartThreads, 0, s>>>(desc, pairsA, histB, G);
-    k_part_scan<<<G.na, 256, 0, s>>>(desc, histB, (int)G.kb, 1 << G.sB, kLgWin, n, err);
-    k_lb_write<<<gb, kPartThreads, part_smem(), s>>>(desc, pairsA, histB, pairsB, G, err);
-    final_pairs = pairsB;
-    launches += 3;
+cudaError_t launch_finalize_log(LevelDesc *desc, const uint32_t *log, const uint2 *hdr, uint32_t total_chunks,
+                                const void *r1, uint2 *pairsA, uint2 *pairsB, uint32_t *curA, uint32_t *curB,
+                                const LogGeom &g, uint32_t *rank, uint32_t *err, cudaStream_t s) {
+  PartOut A;
+  A.out = pairsA;
+  A.cur = curA;
+  A.cap = g.capA;
+  A.claim = g.claimA;
+  A.nb = g.na;
+  k_part_log<<<g.gridA, kPartThreads, part_smem(), s>>>(desc, log, hdr, total_chunks,
+                                                        reinterpret_cast<const uint32_t *>(r1), A, g.shiftA, err);
+  int launches = 2;
+  if (g.sB > 0) {
+    PartOut B;
+    B.out = pairsB;
+    B.cur = curB;
+    B.cap = g.capB;
+    B.claim = g.claimB;
+    B.nb = 1u << g.sB;
+    k_part_win<<<g.na * g.kb, kPartThreads, part_smem(), s>>>(desc, pairsA, curA, g.capA, g.kb, g.sB, B, err);
+    k_win_scatter<<<g.nw, kScatterThreads, scatter_smem(), s>>>(desc, pairsB, curB, g.capB, rank, err);
+    launches = 3;
+  } else {
+    k_win_scatter<<<g.nw, kScatterThreads, scatter_smem(), s>>>(desc, pairsA, curA, g.capA, rank, err);
   }
-  k_win_scatter<<<G.nw, 256, 4u << kLgWin, s>>>(desc, final_pairs, rank, err);
   count_launch(launches);
   return cudaGetLastError();
 }

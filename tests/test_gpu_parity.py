@@ -194,6 +194,52 @@ def test_level0_paths(path, monkeypatch):
     check_equal(gen.random_list(300_000, 4), rank_dtype=np.int64)
 
 
+@pytest.mark.parametrize("n", [(1 << 22) + 12345, (1 << 24) + 3])
+def test_log_path_two_level_partition(n, monkeypatch):
+    """The log path past 256 windows of 2^14 ranks: a level-A partition into
+    A-buckets, then level B into windows (1 and 3 window bits)."""
+    monkeypatch.setenv("LR_TUNING", "log=1")
+    check_equal(gen.random_list(n, 48))
+    check_equal(gen.locality_list(n, 49))
+    succ, _ = gen.forest(n, 50, n_long=8, long_len=n // 16, mean_short=64)
+    check_equal(succ)
+
+
+def _status_of(succ, **kw):
+    try:
+        lr.rank(dev(succ), **kw)
+        return "LR_OK"
+    except lr.LRError as e:
+        return e.name
+
+
+@pytest.mark.parametrize("n", [300_007, (1 << 22) + 5])
+def test_log_path_errors(n, monkeypatch):
+    """Invalid lists on the log path report an error; the stream still works."""
+    monkeypatch.setenv("LR_TUNING", "log=1")
+    succ = gen.random_list(n, 51).astype(np.int64)
+    hp = np.zeros(n, dtype=bool)
+    hp[succ[succ != np.arange(n)]] = True
+    head = int(np.flatnonzero(~hp)[0])
+    tail = int(np.flatnonzero(succ == np.arange(n))[0])
+    bad = succ.copy()
+    bad[n // 3] = n + 7
+    assert _status_of(bad.astype(np.uint32)) == "LR_ERR_OUT_OF_RANGE"
+    closed = succ.copy()
+    closed[tail] = head
+    assert _status_of(closed.astype(np.uint32)) == "LR_ERR_CYCLE"
+    rho = succ.copy()
+    rho[tail] = succ[succ[head]]
+    assert _status_of(rho.astype(np.uint32)) != "LR_OK"
+    two = succ.copy()
+    a = int(succ[head])
+    b = int(succ[a])
+    two[a] = int(succ[b])                      # b becomes a second head; succ[b] has two predecessors
+    assert oracle.rank_status(two.astype(np.uint32))[0] == oracle.NOT_A_LIST
+    assert _status_of(two.astype(np.uint32)) != "LR_OK"
+    check_equal(succ.astype(np.uint32))
+
+
 def test_host_async_two_streams():
     """lr_rank_host_async: calls alternate between two streams; each result is exact."""
     n = (1 << 20) + 3
