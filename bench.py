@@ -36,7 +36,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "G list elements ranked/s at n=2^28 (1 GB300) and % of random-sector HBM roofline"
 UNIT = "G elem/s"
-BYTES_PER_ELEM_CHASE = 64          # one 32 B sector read + one 32 B sector write-back
+BYTES_PER_ELEM_CHASE = 64          # exchange form: one 32 B sector read + one 32 B sector write-back
+BYTES_PER_ELEM_CHASE_LOG = 36      # log form: one 32 B sector gathered + one 4 B log entry written
+# the level-0 chase kernel of each form: name, source file and the section of it
+# the kernel is built from (with the device header), committed traffic record
+CHASE0 = {
+    "exchange": ("k_chase<Rec8> (level-0 ruler chasing, exchange form)", "lr_kernels.cu",
+                 "// ---------------------------------------------------------------- chase",
+                 "// ---------------------------------------------------------------- finalize",
+                 "chase0_traffic.json", BYTES_PER_ELEM_CHASE),
+    "log": ("k_chase_log (level-0 ruler chasing, log form)", "lr_log.cu",
+            "// ---------------------------------------------------------------- log writer",
+            "// ---------------------------------------------------------------- propagation",
+            "chase0_log_traffic.json", BYTES_PER_ELEM_CHASE_LOG),
+}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -115,6 +128,12 @@ class ClockSampler:
                  "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # start timing only once nvidia-smi has initialised and sampled: its
+            # start-up would otherwise overlap the first timed steps
+            t_end = time.time() + 3.0
+            while not self.rows and time.time() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.warm = len(self.rows)
         except Exception:
             self.proc = None
         return self
@@ -135,7 +154,8 @@ class ClockSampler:
         import statistics
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        rows = self.rows[getattr(self, "warm", 0):] or self.rows   # samples of the timed region
+        for r in rows:
             try:
                 sm.append(float(r[0]))
                 mx.append(float(r[1]))
@@ -166,31 +186,30 @@ class ClockSampler:
             return {}
 
 
-def kernel_source_hash():
-    """Hash of the source the level-0 chase kernel is built from: the device
-    header and the chase section of lr_kernels.cu."""
+def kernel_source_hash(form="exchange"):
+    """Hash of the source a level-0 chase kernel is built from: the device
+    header and the kernel's section of its file."""
+    _, fname, start, end, _, _ = CHASE0[form]
     csrc = os.path.join(ROOT, "paper_2606_09318_gb300", "csrc")
     h = hashlib.sha256()
     with open(os.path.join(csrc, "lr_device.cuh"), "rb") as fh:
         h.update(fh.read())
-    with open(os.path.join(csrc, "lr_kernels.cu"), "r") as fh:
+    with open(os.path.join(csrc, fname), "r") as fh:
         text = fh.read()
-    a = text.index("// ---------------------------------------------------------------- chase")
-    b = text.index("// ---------------------------------------------------------------- finalize")
-    h.update(text[a:b].encode())
+    h.update(text[text.index(start):text.index(end)].encode())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(n):
+def ncu_traffic(n, form="exchange"):
     """DRAM bytes per level-0 chase launch from the committed ncu summary,
     scaled to n elements, or None if the kernel changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "chase0_traffic.json")
+    path = os.path.join(ROOT, "profiles", CHASE0[form][4])
     try:
         with open(path) as f:
             d = json.load(f)
     except Exception:
         return None
-    if d.get("kernel_hash") != kernel_source_hash():
+    if d.get("kernel_hash") != kernel_source_hash(form):
         return None
     return float(d["dram_bytes_per_elem"]) * n
 
@@ -328,7 +347,9 @@ def run_ours(args):
 
     hbm, src = measured_peaks()
     chase_ms = prof["ms_chase0"] / max(1, prof["chase0_launches"])
-    achieved = BYTES_PER_ELEM_CHASE * n / (chase_ms * 1e-3) / 1e9
+    form = "log" if prof["chase0_log_launches"] == prof["chase0_launches"] > 0 else "exchange"
+    kname, _, _, _, _, kbytes = CHASE0[form]
+    achieved = kbytes * n / (chase_ms * 1e-3) / 1e9
     value = ws * n / (ms * 1e-3) / 1e9
     sector_roof = hbm / BYTES_PER_ELEM_CHASE            # G elem/s
     steps_prof = max(1, prof["calls"])
@@ -341,19 +362,23 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic: uniformly random-order single list (torch.randperm, seeded)",
         "config": {"workload": "single random-order list, n=2^28, unweighted, int32 ranks",
-                   "n": n, "l2_policy": "inputs larger than L2 (1 GiB succ + 2 GiB records)",
+                   "n": n, "chase0_form": form,
+                   "l2_policy": "inputs larger than L2 (1 GiB succ + 1 GiB log, or 2 GiB records)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "k_chase<Rec8> (level-0 ruler chasing)",
+        "roofline": {"bound": "hbm", "kernel": kname,
                      "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "peak_source": src,
-                     "traffic": ncu_traffic(n), "algorithmic_bytes": BYTES_PER_ELEM_CHASE * n,
+                     "traffic": ncu_traffic(n, form), "algorithmic_bytes": kbytes * n,
                      "ms_per_launch": round(chase_ms, 4),
+                     # the chase's own ceiling: dependent random gathers (log form)
+                     # or gathers with an atomic exchange (exchange form)
                      "random_access_ceiling": None if probe is None else {
                          "gather_g_per_s": round(probe["gather_gsteps"], 2),
                          "gather_exchange_g_per_s": round(probe["gather_xchg_gsteps"], 2),
                          "copy_gbs": round(probe["copy_gbs"], 1),
-                         "chase_frac_of_exchange_ceiling": round(
-                             n / (chase_ms * 1e-3) / 1e9 / probe["gather_xchg_gsteps"], 4)}},
+                         "chase_frac_of_ceiling": round(
+                             n / (chase_ms * 1e-3) / 1e9 /
+                             probe["gather_gsteps" if form == "log" else "gather_xchg_gsteps"], 4)}},
         "pipeline": {"random_sector_roofline_gelem_s": round(sector_roof, 2),
                      "frac": round(value / ws / sector_roof, 4),
                      "phases_ms_per_step": {k[3:]: round(prof[k] / steps_prof, 4) for k in

@@ -84,7 +84,30 @@ typedef struct lr_tuning {
     uint32_t contract;   /* tile-local contraction: 0 auto (default),            */
                          /* LR_CONTRACT_OFF or LR_CONTRACT_ON                     */
     uint32_t spawn;      /* 1: ruler spawning at level 0 (Section 2.2); 0 off    */
+    uint32_t chase0;     /* level-0 chase form: 0 auto (default),                */
+                         /* LR_CHASE0_EXCHANGE or LR_CHASE0_LOG                   */
 } lr_tuning;
+
+/*
+ * Level-0 chase form of the default algorithm (Algorithm 1's ruler chasing
+ * and ruler propagation at the first level).  Both give identical results.
+ *  - LR_CHASE0_EXCHANGE: the prep pass packs every element into a record;
+ *    the chase swaps (ruler, offset) into each record with one atomic
+ *    exchange, and propagation streams the records.  On GB300 that is two
+ *    random DRAM accesses per element (the gather and the later write-back).
+ *  - LR_CHASE0_LOG: the chase only gathers succ[] and appends each element
+ *    it reaches to a per-thread log; propagation radix-partitions the log by
+ *    element id into windows of 16384 ranks and assembles each window in
+ *    shared memory.  One random access per element plus streaming passes.
+ *    Unweighted lists with int32 ranks and n <= 2^30 only (the exchange
+ *    form is used otherwise).
+ * Auto (0) takes the log form for single-instance unweighted int32 calls
+ * with n >= 2^25 and no extra outputs or spawning, where it is faster on
+ * GB300, and the exchange form otherwise.
+ */
+#define LR_CHASE0_AUTO 0u
+#define LR_CHASE0_EXCHANGE 1u
+#define LR_CHASE0_LOG 2u
 
 /*
  * Ruler spawning (Section 2.2): when a chasing thread's CTA has no queued
@@ -304,6 +327,7 @@ typedef struct lr_profile {
     int64_t chase0_launches;
     int64_t kernel_launches;
     int64_t elements;    /* elements ranked (sum of n)                           */
+    int64_t chase0_log_launches; /* of chase0_launches: the log form            */
 } lr_profile;
 
 lr_status lr_profile_enable(int32_t on);

@@ -44,11 +44,12 @@ class Tuning(ctypes.Structure):
     _fields_ = [("f0_inv", ctypes.c_uint32), ("f_inv", ctypes.c_uint32), ("cutoff", ctypes.c_uint32),
                 ("chase_block", ctypes.c_uint32), ("chase_ctas", ctypes.c_uint32),
                 ("algorithm", ctypes.c_uint32), ("contract", ctypes.c_uint32),
-                ("spawn", ctypes.c_uint32)]
+                ("spawn", ctypes.c_uint32), ("chase0", ctypes.c_uint32)]
 
 
 ALGO_SRS, ALGO_WYLLIE = 0, 1
 CONTRACT_AUTO, CONTRACT_OFF, CONTRACT_ON = 0, 1, 2
+CHASE0_AUTO, CHASE0_EXCHANGE, CHASE0_LOG = 0, 1, 2
 
 
 class _Opts(ctypes.Structure):
@@ -73,7 +74,8 @@ class _Profile(ctypes.Structure):
                 ("ms_chase0", ctypes.c_double), ("ms_chase_rest", ctypes.c_double),
                 ("ms_base", ctypes.c_double), ("ms_finalize", ctypes.c_double),
                 ("calls", ctypes.c_int64), ("chase0_launches", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("elements", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("elements", ctypes.c_int64),
+                ("chase0_log_launches", ctypes.c_int64)]
 
 
 class _ServerConfig(ctypes.Structure):

@@ -64,7 +64,7 @@ Tuning resolve_tuning_builtin(int64_t n, bool weighted) {
   u.block = 256;
   u.ctas = 0;
   u.xchg = 1;
-  u.logmode = 0;
+  u.chase0 = LR_CHASE0_AUTO;
   u.algo = LR_ALGO_SRS;
   u.contract = LR_CONTRACT_AUTO;
   u.spawn = 0;
@@ -88,12 +88,14 @@ Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted, bool batch) 
   u.block = env_u32(env, "block", u.block);
   u.ctas = env_u32(env, "ctas", u.ctas);
   u.xchg = env_u32(env, "xchg", 1);
-  u.logmode = env_u32(env, "log", 0);
+  const uint32_t env_log = env_u32(env, "log", 2);      // log=1 / log=0: force a level-0 form
+  if (env_log < 2) u.chase0 = env_log ? LR_CHASE0_LOG : LR_CHASE0_EXCHANGE;
   u.algo = env_u32(env, "algo", LR_ALGO_SRS);
   u.contract = env_u32(env, "contract", u.contract);
   u.spawn = env_u32(env, "spawn", u.spawn);
   if (t) {
     if (t->spawn) u.spawn = t->spawn;
+    if (t->chase0) u.chase0 = t->chase0;
     if (t->algorithm) u.algo = t->algorithm;
     if (t->contract) u.contract = t->contract;
     if (t->f0_inv) u.f0_inv = t->f0_inv;
@@ -107,6 +109,18 @@ Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted, bool batch) 
   u.cutoff = std::min<uint32_t>(std::max<uint32_t>(u.cutoff, 64), kMaxCutoff);
   if (u.block != 128 && u.block != 256 && u.block != 512) u.block = 256;
   return u;
+}
+
+// Level-0 chase form: the log form (lr_log.cu) needs an unweighted single
+// instance with int32 ranks and n <= 2^30; auto takes it from 2^25 on, where
+// its one random access per element beats the exchange form's two, unless
+// spawning (an exchange-form feature) was asked for.
+constexpr uint64_t kLogAutoMin = 1ull << 25;
+static bool use_log0(const Tuning &u, uint64_t n, bool weighted, int rank_bytes, bool extras, bool multi) {
+  if (weighted || rank_bytes != 4 || extras || multi || n <= u.cutoff || n > (1ull << 30) || !u.xchg)
+    return false;
+  if (u.chase0 == LR_CHASE0_LOG) return true;
+  return u.chase0 == LR_CHASE0_AUTO && n >= kLogAutoMin && !u.spawn;
 }
 
 static uint32_t ceil_log2(uint64_t x) {
@@ -346,7 +360,7 @@ lr_status ensure_buffer(void **buf, size_t *cur, size_t want, cudaStream_t s) {
 // ---------------------------------------------------------------- profiling
 static bool g_prof = false;
 struct ProfMark { cudaEvent_t ev; int phase; };  // phase of the interval ending here
-struct ProfCall { std::vector<ProfMark> marks; int64_t n; int64_t launches; };
+struct ProfCall { std::vector<ProfMark> marks; int64_t n; int64_t launches; bool log0 = false; };
 static std::vector<ProfCall> g_prof_pending;
 static lr_profile g_prof_acc;
 
@@ -620,8 +634,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   const bool rec16_0 = in.wtype != 0;
   const bool extras = in.term != nullptr || in.prefix != nullptr || in.incl != 0;
   if (extras && ptrs) return LR_ERR_INVALID_ARGUMENT;
-  const bool log0 = u.logmode && !ptrs && !extras && in.offsets == nullptr && in.wtype == 0 &&
-                    in.rank_bytes == 4 && in.n > u.cutoff && in.n <= (1ull << 30);
+  const bool log0 = use_log0(u, in.n, in.wtype != 0, in.rank_bytes, extras, ptrs || in.offsets != nullptr);
   const bool t0ws = extras && in.term == nullptr;
   const bool spawn0 = u.spawn != 0 && u.xchg != 0 && !log0 && !extras && !ptrs;
   // tile-local contraction: forced, or decided from the prep pass's count of
@@ -633,7 +646,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     const lr_status cs = run_contracted(in, tuning, c, true, s);
     if (cs != LR_ERR_NOT_FOUND) return cs;
   }
-  const bool count_local = contractible && u.contract == LR_CONTRACT_AUTO && !log0;
+  const bool count_local = contractible && u.contract == LR_CONTRACT_AUTO;
   const int grid = chase_grid_for(u, rec16_0, log0);
   const bool need_count = in.max_lists <= 0 && (in.ws == nullptr || in.count_in_ws) &&
                           (in.n > u.cutoff || ptrs);
@@ -670,7 +683,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   LR_TRY(cudaMemsetAsync(fixed + p.off_zero, 0, p.zero_bytes, s));
   LR_TRY(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * ((in.n + 31) / 32), s));
   if (log0)
-    LR_TRY(launch_sum0(in.succ, (uint32_t)in.n, acc, err, s));
+    LR_TRY(launch_sum0(in.succ, (uint32_t)in.n, acc, count_local ? acc + 2 : nullptr, err, s));
   else if (ptrs)
     LR_TRY(launch_prep0_ptrs(in.sptr, in.wptr, in.wtype, (uint32_t)in.n, work0, bitmap, err,
                              in.validate, in.offsets, in.k, s));
@@ -794,6 +807,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
       LR_TRY(launch_chase(desc, l, work_of(l), r16, work_of(l + 1), ns,
                           qctr + (size_t)l * p.chase_grid, p.chase_grid, p.chase_block, err,
                           (int)u.xchg, tid_of(l), tid_of(l + 1), nullptr, s));
+    if (l == 0) prof.call.log0 = log0;
     prof.mark(l == 0 ? PH_CHASE0 : PH_CHASE);
   }
   LR_TRY(launch_base(desc, L, work_of(L), L > 0 || rec16_0, R_of(L), p.rank_bytes, p.cutoff, err,
@@ -1115,8 +1129,8 @@ size_t lr_workspace_size_outputs(int64_t n_total, int32_t k, const lr_outputs *o
   }
   const uint64_t h = opts->max_lists > 0 ? (uint64_t)opts->max_lists : (uint64_t)n_total;
   const bool extras = outs && (outs->term || outs->prefix || outs->inclusive_tail);
-  const bool log0 = u.logmode && !extras && k == 0 && opts->wtype == LR_NONE && opts->rtype == LR_I32 &&
-                    (uint64_t)n_total > u.cutoff && n_total <= ((int64_t)1 << 30);
+  const bool log0 = use_log0(u, (uint64_t)n_total, opts->wtype != LR_NONE, opts->rtype == LR_I64 ? 8 : 4,
+                             extras, k != 0);
   const bool spawn0 = u.spawn != 0 && u.xchg != 0 && !log0 && !extras;
   Plan p = make_plan((uint64_t)n_total, h, u, opts->wtype != LR_NONE,
                      opts->rtype == LR_I64 ? 8 : 4, opts->seed, 256 * 16, false, log0, extras,
@@ -1164,7 +1178,11 @@ lr_status lr_profile_read(lr_profile *out, int32_t reset) {
       switch (call.marks[i].phase) {
         case PH_PREP: g_prof_acc.ms_prep += ms; break;
         case PH_SELECT: g_prof_acc.ms_select += ms; break;
-        case PH_CHASE0: g_prof_acc.ms_chase0 += ms; g_prof_acc.chase0_launches += 1; break;
+        case PH_CHASE0:
+          g_prof_acc.ms_chase0 += ms;
+          g_prof_acc.chase0_launches += 1;
+          g_prof_acc.chase0_log_launches += call.log0 ? 1 : 0;
+          break;
         case PH_CHASE: g_prof_acc.ms_chase_rest += ms; break;
         case PH_BASE: g_prof_acc.ms_base += ms; break;
         case PH_FINAL: g_prof_acc.ms_finalize += ms; break;

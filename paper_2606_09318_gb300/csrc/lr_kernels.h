@@ -115,8 +115,8 @@ cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec
                             const uint32_t *tid_cur, cudaStream_t s);
 
 // Log path (unweighted level 0, see lr_log.cu).
-cudaError_t launch_sum0(const uint32_t *succ, uint32_t n, unsigned long long *acc, uint32_t *err,
-                        cudaStream_t s);
+cudaError_t launch_sum0(const uint32_t *succ, uint32_t n, unsigned long long *acc, unsigned long long *local,
+                        uint32_t *err, cudaStream_t s);
 cudaError_t launch_heads0_log(LevelDesc *desc, const unsigned long long *acc, uint32_t *hlist0,
                               const uint32_t *succ, uint32_t n, uint32_t *bitmap, uint32_t *err,
                               int validate, cudaStream_t s);

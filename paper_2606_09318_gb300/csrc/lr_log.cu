@@ -28,10 +28,13 @@ constexpr uint32_t kLogEnd = 0xFFFFFFFFu;  // log entry: unused slot
 constexpr uint32_t kChunk = 32;            // entries per log chunk (128 bytes)
 
 // ---------------------------------------------------------------- heads by sums
+// (local: also count the links that stay inside their 4096-id tile, for the
+// contraction decision)
 __global__ void __launch_bounds__(256)
 k_sum0(const uint32_t *__restrict__ succ, uint32_t n, unsigned long long *__restrict__ acc,
-       uint32_t *__restrict__ err, int vec) {
+       unsigned long long *__restrict__ local, uint32_t *__restrict__ err, int vec) {
   unsigned long long S = 0, T = 0;
+  uint32_t loc = 0;
   uint32_t bad = 0;
   const uint32_t ngroups = (uint32_t)(((uint64_t)n + 3u) / 4u);
   for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
@@ -49,25 +52,30 @@ k_sum0(const uint32_t *__restrict__ succ, uint32_t n, unsigned long long *__rest
       if (j >= cnt) break;
       if (s[j] >= n) bad = 1;
       else if (s[j] == i0 + j) T += 1;
-      else S += s[j];
+      else {
+        S += s[j];
+        loc += (s[j] >> kContractTileShift) == ((i0 + j) >> kContractTileShift);
+      }
     }
   }
   for (int d = 16; d > 0; d >>= 1) {
     S += __shfl_down_sync(0xFFFFFFFFu, S, d);
     T += __shfl_down_sync(0xFFFFFFFFu, T, d);
+    loc += __shfl_down_sync(0xFFFFFFFFu, loc, d);
   }
   if ((threadIdx.x & 31) == 0) {
     if (T) atomicAdd(acc + 0, T);
     if (S) atomicAdd(acc + 1, S);
+    if (local && loc) atomicAdd(local, (unsigned long long)loc);
   }
   if (bad) record_error(err, kErrRange);
 }
 
-cudaError_t launch_sum0(const uint32_t *succ, uint32_t n, unsigned long long *acc, uint32_t *err,
-                        cudaStream_t s) {
+cudaError_t launch_sum0(const uint32_t *succ, uint32_t n, unsigned long long *acc, unsigned long long *local,
+                        uint32_t *err, cudaStream_t s) {
   const int block = 256;
   const int vec = ((uintptr_t)succ & 15u) == 0;
-  k_sum0<<<stream_grid(((uint64_t)n + 3) / 4, block), block, 0, s>>>(succ, n, acc, err, vec);
+  k_sum0<<<stream_grid(((uint64_t)n + 3) / 4, block), block, 0, s>>>(succ, n, acc, local, err, vec);
   count_launch();
   return cudaGetLastError();
 }
@@ -300,12 +308,11 @@ struct PartSmem {
   uint32_t ccnt[kMaxBuckets];              // carried pairs per bucket
   uint32_t pos[kMaxBuckets];               // next free slot of the bucket's current block
   uint32_t left[kMaxBuckets];              // free slots left in it (a multiple of 4), or kDead
-  uint32_t tstart[kMaxBuckets];            // this tile: first slot of the bucket's run in `sorted`
-  uint32_t tcc[kMaxBuckets];               // this tile: carried pairs at the head of the run
-  uint32_t tm[kMaxBuckets];                // this tile: run length
-  uint32_t tpos[kMaxBuckets];              // this tile: the current block's free slot ...
-  uint32_t tleft[kMaxBuckets];             // ... and room, and the block claimed for the rest
-  uint32_t tnpos[kMaxBuckets];
+  // this tile, per bucket: {first slot of its run in `sorted` | run length
+  // << 16, room left in the current block, its free slot, the block claimed
+  // for the rest}, and where the tile's own pairs start (after the carried)
+  uint4 tile[kMaxBuckets];
+  uint32_t tbase[kMaxBuckets];
   uint32_t wsum[32];
   uint16_t qb[kSortCap / 4];               // bucket of every quad of `sorted`
 };
@@ -351,6 +358,16 @@ __device__ __forceinline__ void decode_ilp(const uint32_t *__restrict__ log, con
     const uint32_t o = below ? (uint32_t)(lane - m - 1) : h[j].y + (uint32_t)lane;
     if (e[j] != kLogEnd && !(e[j] & kMark) && e[j] < n) { out[j] = make_uint2(e[j], c); off[j] = o; }
   }
+}
+
+// Bulk prefetch of [p, p + bytes) into L2, shrunk inward to 16-byte
+// boundaries (a hint: the next tile's input, fetched while this one is
+// partitioned).
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
+  const uintptr_t a = ((uintptr_t)p + 15u) & ~(uintptr_t)15u;
+  const uintptr_t e = ((uintptr_t)p + bytes) & ~(uintptr_t)15u;
+  if (e > a)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(a), "r"((uint32_t)(e - a)) : "memory");
 }
 
 // Exclusive scan of v over the block's threads (all threads call it, at most
@@ -405,9 +422,6 @@ __device__ void part_tile(PartSmem &S, const PartOut &P, const uint2 (&item)[kIp
     const uint32_t b = tid, cc = S.ccnt[b], full = m & ~3u;
     uint32_t p = S.pos[b], l = S.left[b], np = 0;
     S.cnt[b] = 0;
-    S.tstart[b] = st;
-    S.tcc[b] = cc;
-    S.tm[b] = m;
     if (l != kDead && full > l) {                   // claim room for what the block lacks
       const uint32_t x = full - l;
       const uint32_t c = (x + P.claim - 1u) / P.claim * P.claim;
@@ -425,9 +439,8 @@ __device__ void part_tile(PartSmem &S, const PartOut &P, const uint2 (&item)[kIp
       S.left[b] = l - full;
     }
     if (l == kDead) S.left[b] = kDead;
-    S.tpos[b] = p;
-    S.tleft[b] = l;
-    S.tnpos[b] = np;
+    S.tile[b] = make_uint4(st | (m << 16), l, p, np);
+    S.tbase[b] = st + cc;
     S.ccnt[b] = m - full;
     for (uint32_t k = 0; k < cc; ++k) S.sorted[st + k] = S.carry[b * 4 + k];
     for (uint32_t q = st / 4; q < (st + alloc) / 4; ++q) S.qb[q] = (uint16_t)b;
@@ -435,16 +448,17 @@ __device__ void part_tile(PartSmem &S, const PartOut &P, const uint2 (&item)[kIp
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kIpt; ++i)
-    if (item[i].x != kLogEnd) S.sorted[S.tstart[bk[i]] + S.tcc[bk[i]] + slot[i]] = item[i];
+    if (item[i].x != kLogEnd) S.sorted[S.tbase[bk[i]] + slot[i]] = item[i];
   __syncthreads();
   const uint32_t nq = total / 4;
   for (uint32_t q = tid; q < nq; q += blockDim.x) {
     const uint32_t b = S.qb[q];
-    const uint32_t k = 4 * q - S.tstart[b], rm = S.tm[b];
+    const uint4 t = S.tile[b];
+    const uint32_t k = 4 * q - (t.x & 0xFFFFu), rm = t.x >> 16;
     if (k + 4 <= rm) {
-      const uint32_t l = S.tleft[b];
+      const uint32_t l = t.y;
       if (l == kDead) continue;
-      const uint32_t dst = k < l ? S.tpos[b] + k : S.tnpos[b] + (k - l);
+      const uint32_t dst = k < l ? t.z + k : t.w + (k - l);
       const uint4 *src = reinterpret_cast<const uint4 *>(S.sorted + 4 * q);
       const uint4 u = src[0], v = src[1];
       st_sector(P.out + (size_t)b * P.cap + dst, u.x, u.y, u.z, u.w, v.x, v.y, v.z, v.w);
@@ -503,6 +517,11 @@ k_part_log(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log,
   const uint32_t per_tile = (uint32_t)nwarps * 2 * kDecodeIlp;
   uint32_t bad = 0;
   for (uint32_t t0 = c0; t0 < c1; t0 += per_tile) {
+    if (threadIdx.x == 0 && t0 + per_tile < c1) {
+      const uint32_t nx = t0 + per_tile, ne = min(c1, nx + per_tile);
+      prefetch_l2(log + (size_t)nx * kChunk, (size_t)(ne - nx) * kChunk * 4);
+      prefetch_l2(hdr + nx, (size_t)(ne - nx) * 8);
+    }
     uint2 item[kIpt];
     uint32_t off[kIpt], bk[kIpt];
 #pragma unroll
@@ -548,6 +567,10 @@ k_part_win(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, con
   const uint32_t wmask = (1u << sB) - 1u;
   uint32_t bad = 0;
   for (uint32_t t0 = p0; t0 < p1; t0 += kPartTile) {
+    if (threadIdx.x == 0 && t0 + kPartTile < p1) {
+      const uint32_t nx = t0 + kPartTile, ne = min(p1, nx + kPartTile);
+      prefetch_l2(src + nx, (size_t)(ne - nx) * 8);
+    }
     uint2 item[kIpt];
     uint32_t bk[kIpt];
 #pragma unroll
@@ -585,13 +608,21 @@ k_win_scatter(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, 
   __syncthreads();
   uint32_t bad = 0, got = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0 && d.visited != n) bad |= d.visited > n ? kErrNotList : kErrCycle;
-  const uint32_t m = min(__ldcg(cur + blockIdx.x), cap);
-  const uint2 *src = in + (size_t)blockIdx.x * cap;
-  for (uint32_t p = threadIdx.x; p < m; p += blockDim.x) {
-    const uint2 v = __ldcs(src + p);
-    if (v.x == kLogEnd) continue;
-    const uint64_t loc = (uint64_t)v.x - w0;
-    if (loc < len) { win[loc] = v.y; ++got; } else bad |= kErrInternal;
+  // a region holds whole quads of pairs (claims are multiples of four), 32-byte aligned
+  const uint32_t nq = min(__ldcg(cur + blockIdx.x), cap) / 4;
+  const uint4 *src = reinterpret_cast<const uint4 *>(in + (size_t)blockIdx.x * cap);
+  auto put = [&](uint32_t y, uint32_t v) {
+    if (y == kLogEnd) return;
+    const uint64_t loc = (uint64_t)y - w0;
+    if (loc < len) { win[loc] = v; ++got; } else bad |= kErrInternal;
+  };
+  for (uint32_t q = threadIdx.x; q < nq; q += 2 * blockDim.x) {
+    const uint32_t q2 = q + blockDim.x;
+    const uint4 a = __ldcs(src + 2 * q), b = __ldcs(src + 2 * q + 1);
+    uint4 c = make_uint4(kLogEnd, 0u, kLogEnd, 0u), e = c;
+    if (q2 < nq) { c = __ldcs(src + 2 * q2); e = __ldcs(src + 2 * q2 + 1); }
+    put(a.x, a.y); put(a.z, a.w); put(b.x, b.y); put(b.z, b.w);
+    put(c.x, c.y); put(c.z, c.w); put(e.x, e.y); put(e.z, e.w);
   }
   for (int dd = 16; dd > 0; dd >>= 1) got += __shfl_down_sync(0xFFFFFFFFu, got, dd);
   if ((threadIdx.x & 31) == 0 && got) atomicAdd(s_count, got);

@@ -205,6 +205,43 @@ def test_log_path_two_level_partition(n, monkeypatch):
     check_equal(succ)
 
 
+def test_chase0_auto_and_forced():
+    """The level-0 chase form: auto takes the log form for large unweighted
+    single lists and the exchange form otherwise; either can be forced; the
+    ranks are the same."""
+    def form(succ, **kw):
+        lr.profile_enable(True)
+        lr.profile_read(reset=True)
+        got = lr.rank(dev(succ), **kw)
+        prof = lr.profile_read(reset=True)
+        lr.profile_enable(False)
+        assert prof["chase0_launches"] == 1
+        return got, "log" if prof["chase0_log_launches"] == 1 else "exchange"
+    big = gen.random_list((1 << 25) + 17, 52)
+    want = oracle.rank(big)
+    for t, expect in ((None, "log"), (lr.Tuning(chase0=lr.CHASE0_EXCHANGE), "exchange"),
+                      (lr.Tuning(spawn=1), "exchange")):
+        got, f = form(big, tuning=t)
+        assert f == expect
+        np.testing.assert_array_equal(host(got), want)
+    got, f = form(big, rank_dtype=torch.int64)
+    assert f == "exchange"
+    np.testing.assert_array_equal(host(got), want.astype(np.int64))
+    small = gen.random_list((1 << 20) + 5, 53)
+    assert form(small)[1] == "exchange"
+    got, f = form(small, tuning=lr.Tuning(chase0=lr.CHASE0_LOG))
+    assert f == "log"
+    np.testing.assert_array_equal(host(got), oracle.rank(small))
+    # a locality order is contracted before either form is chosen
+    loc = gen.locality_list((1 << 25) + 3, 54)
+    lr.profile_enable(True)
+    lr.profile_read(reset=True)
+    np.testing.assert_array_equal(host(lr.rank(dev(loc))), oracle.rank(loc))
+    prof = lr.profile_read(reset=True)
+    lr.profile_enable(False)
+    assert prof["chase0_log_launches"] == 0
+
+
 def _status_of(succ, **kw):
     try:
         lr.rank(dev(succ), **kw)
