@@ -194,10 +194,11 @@ def test_level0_paths(path, monkeypatch):
     check_equal(gen.random_list(300_000, 4), rank_dtype=np.int64)
 
 
-@pytest.mark.parametrize("n", [(1 << 22) + 12345, (1 << 24) + 3])
+@pytest.mark.parametrize("n", [1 << 22, (1 << 22) + 12345, (1 << 24) + 3])
 def test_log_path_two_level_partition(n, monkeypatch):
-    """The log path past 256 windows of 2^14 ranks: a level-A partition into
-    A-buckets, then level B into windows (1 and 3 window bits)."""
+    """The log path at 256 windows of 2^14 ranks (the most one partition level
+    holds) and past it: a level-A partition into A-buckets, then level B into
+    windows (1 and 3 window bits)."""
     monkeypatch.setenv("LR_TUNING", "log=1")
     check_equal(gen.random_list(n, 48))
     check_equal(gen.locality_list(n, 49))
