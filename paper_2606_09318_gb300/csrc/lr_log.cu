@@ -351,11 +351,13 @@ __device__ __forceinline__ void decode_ilp(const uint32_t *__restrict__ log, con
     if (h[j].y == kLogEnd) continue;               // chunk never allocated (warp-uniform)
     const bool mark = e[j] != kLogEnd && (e[j] & kMark);
     const uint32_t mm = __ballot_sync(0xFFFFFFFFu, mark);
-    const uint32_t below = mm & ((2u << lane) - 1u);
-    const int m = below ? 31 - __clz(below) : 0;
-    const uint32_t em = __shfl_sync(0xFFFFFFFFu, e[j], m);
-    const uint32_t c = below ? (em & ~kMark) : h[j].x;
-    const uint32_t o = below ? (uint32_t)(lane - m - 1) : h[j].y + (uint32_t)lane;
+    uint32_t c = h[j].x, o = h[j].y + (uint32_t)lane;
+    if (mm) {                                      // warp-uniform: the chunk starts a segment
+      const uint32_t below = mm & ((2u << lane) - 1u);
+      const int m = below ? 31 - __clz(below) : 0;
+      const uint32_t em = __shfl_sync(0xFFFFFFFFu, e[j], m);
+      if (below) { c = em & ~kMark; o = (uint32_t)(lane - m - 1); }
+    }
     if (e[j] != kLogEnd && !(e[j] & kMark) && e[j] < n) { out[j] = make_uint2(e[j], c); off[j] = o; }
   }
 }
@@ -404,8 +406,11 @@ __device__ __forceinline__ void part_init(PartSmem &S, uint32_t nb) {
 // One tile of register-held pairs (item[i].x != kLogEnd: a pair, bk[i] its
 // bucket) -> bucket runs in shared memory, laid out so that every aligned
 // quad of `sorted` is one quad of its bucket's output -> whole-sector stores.
+// The stored value is item[i].y - sub[i]: the caller may pass item[i].y
+// straight from a load still in flight, which is first used when the pair
+// is placed, after the tile's counting, scan and claims.
 __device__ void part_tile(PartSmem &S, const PartOut &P, const uint2 (&item)[kIpt],
-                          const uint32_t (&bk)[kIpt], uint32_t &bad) {
+                          const uint32_t (&sub)[kIpt], const uint32_t (&bk)[kIpt], uint32_t &bad) {
   const uint32_t tid = threadIdx.x, nb = P.nb;
   uint32_t slot[kIpt];
 #pragma unroll
@@ -448,7 +453,7 @@ __device__ void part_tile(PartSmem &S, const PartOut &P, const uint2 (&item)[kIp
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kIpt; ++i)
-    if (item[i].x != kLogEnd) S.sorted[S.tbase[bk[i]] + slot[i]] = item[i];
+    if (item[i].x != kLogEnd) S.sorted[S.tbase[bk[i]] + slot[i]] = make_uint2(item[i].x, item[i].y - sub[i]);
   __syncthreads();
   const uint32_t nq = total / 4;
   for (uint32_t q = tid; q < nq; q += blockDim.x) {
@@ -533,17 +538,15 @@ k_part_log(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log,
       for (int j = 0; j < kDecodeIlp; ++j) { item[r * kDecodeIlp + j] = it[j]; off[r * kDecodeIlp + j] = of[j]; }
     }
 #pragma unroll
-    for (int i = 0; i < kIpt; ++i) {
-      bk[i] = 0;
-      if (item[i].x == kLogEnd) continue;
+    for (int i = 0; i < kIpt; ++i) {             // issue the R_1 gathers first
       const uint32_t c = item[i].y;
-      uint32_t val = 0;
-      if (c < nn) val = __ldcg(r1 + c) - off[i];
-      else bad |= kErrInternal;
-      item[i].y = val;
-      bk[i] = item[i].x >> shift;
+      const bool ok = item[i].x != kLogEnd && c < nn;
+      if (item[i].x != kLogEnd && c >= nn) bad |= kErrInternal;
+      item[i].y = ok ? __ldcg(r1 + c) : 0u;
     }
-    part_tile(S, P, item, bk, bad);
+#pragma unroll
+    for (int i = 0; i < kIpt; ++i) bk[i] = item[i].x != kLogEnd ? item[i].x >> shift : 0u;
+    part_tile(S, P, item, off, bk, bad);
   }
   part_flush(S, P, bad);
   if (bad) record_error(err, bad);
@@ -586,7 +589,8 @@ k_part_win(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, con
       }
       bk[j] = (item[j].x >> kLgWin) & wmask;
     }
-    part_tile(S, Q, item, bk, bad);
+    const uint32_t zero[kIpt] = {0, 0, 0, 0, 0, 0, 0, 0};
+    part_tile(S, Q, item, zero, bk, bad);
   }
   part_flush(S, Q, bad);
   if (bad) record_error(err, bad);
