@@ -373,7 +373,8 @@ __device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
 }
 
 // Exclusive scan of v over the block's threads (all threads call it, at most
-// 32 warps); the total comes back through `total`.
+// 32 warps); the total comes back through `total`.  `wsum` may be written
+// again only after another barrier of the block.
 __device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t *wsum, uint32_t &total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   uint32_t x = v;
@@ -392,7 +393,6 @@ __device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t *wsum, 
   }
   const uint32_t before = __shfl_sync(0xFFFFFFFFu, t, warp > 0 ? warp - 1 : 0);
   total = __shfl_sync(0xFFFFFFFFu, t, 31);
-  __syncthreads();                                   // wsum may be reused after this
   return (warp > 0 ? before : 0u) + x - v;
 }
 
@@ -471,12 +471,16 @@ __device__ void part_tile(PartSmem &S, const PartOut &P, const uint2 (&item)[kIp
       for (uint32_t j = k; j < rm; ++j) S.carry[b * 4 + (j - k)] = S.sorted[4 * q + (j - k)];
     }
   }
-  __syncthreads();
+  // no barrier here: the next tile only counts (S.cnt, which this step does
+  // not touch) before its first barrier, and everything this step reads or
+  // writes is next written or read after that barrier (part_flush is preceded
+  // by one of its own)
 }
 
 // End of a CTA's input: the carried pairs of each bucket, padded with empty
 // pairs, and empty pairs in the rest of its last block.
 __device__ void part_flush(PartSmem &S, const PartOut &P, uint32_t &bad) {
+  __syncthreads();                                   // the last tile's carries are written
   for (uint32_t b = threadIdx.x; b < P.nb; b += blockDim.x) {
     uint32_t l = S.left[b], p = S.pos[b];
     const uint32_t r = S.ccnt[b];
