@@ -243,6 +243,28 @@ def test_chase0_auto_and_forced():
     assert prof["chase0_log_launches"] == 0
 
 
+@pytest.mark.parametrize("path,n", [
+    ("log=1,f0=2", (1 << 20) + 3),            # a ruler at every other element: marks everywhere
+    ("log=1,f0=65536", (1 << 22) + 1),        # segments of ~65536: mark-free chunks, long walks,
+                                              # and a last window of one element after 256 full ones
+    ("log=1", 12289),                         # just above the base case
+    ("log=1,f0=3,f=2", 100_003),
+])
+def test_log_path_ruler_densities(path, n, monkeypatch):
+    monkeypatch.setenv("LR_TUNING", path)
+    check_equal(gen.random_list(n, 55))
+    check_equal(gen.locality_list(n, 56))
+
+
+@pytest.mark.parametrize("mean_short", [1, 2])
+def test_log_path_forest_of_tiny_lists(mean_short, monkeypatch):
+    """Mostly singletons and pairs: the heads come from the bitmap, most
+    rulers are heads, and many segments are a single element."""
+    monkeypatch.setenv("LR_TUNING", "log=1")
+    succ, _ = gen.forest(1 << 21, 57 + mean_short, n_long=2, long_len=1 << 16, mean_short=mean_short)
+    check_equal(succ)
+
+
 def _status_of(succ, **kw):
     try:
         lr.rank(dev(succ), **kw)
