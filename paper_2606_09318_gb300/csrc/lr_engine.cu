@@ -193,7 +193,7 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
   p.off_err = o; o = align_up(o + 16);
   p.off_hcount = o; o = align_up(o + 16);
   p.off_acc = o; o = align_up(o + 32);        // sums of terminals, successors; local links
-  p.off_ovf = o; o = align_up(o + 16);
+  p.off_logctr = o; o = align_up(o + 16);
   p.off_bctr = o; o = align_up(o + sizeof(uint32_t) * 256);
   p.off_q = o; o = align_up(o + sizeof(uint32_t) * (size_t)chase_grid * kMaxLevels);
   p.off_bcnt = o; o = align_up(o + sizeof(uint64_t) * kHeadBlocks);
@@ -209,14 +209,13 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
   }
   if (log0) {
     // log entries: every element once plus one mark per ruler, in 32-entry
-    // chunks; each thread may leave one chunk partly filled.  6 % slack per
-    // CTA region plus an overflow pool of the same size.
+    // chunks handed out from one counter; each thread leaves at most one
+    // chunk partly filled, and each CTA at most the rest of one window of
+    // kLogWindow chunks, however long the segments are
     const uint64_t rulers = (n + p.f_inv[0] - 1) / p.f_inv[0] + p.hcap;
     const uint64_t need = (n + rulers + 31) / 32;
     const uint64_t threads = (uint64_t)chase_grid * u.block;
-    const uint64_t main = need + need * 6 / 100 + threads + chase_grid;
-    p.per_cta = (uint32_t)((main + chase_grid - 1) / chase_grid);
-    const uint64_t total = (uint64_t)p.per_cta * chase_grid + need * 6 / 100 + 4096;
+    const uint64_t total = need + threads + (uint64_t)chase_grid * kLogWindow + 4096;
     p.total_chunks = (uint32_t)std::min<uint64_t>(total, 0xFFFFFFF0ull);
     uint32_t lg = 0;
     while ((1ull << lg) < n) ++lg;
@@ -794,8 +793,8 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     prof.mark(PH_SELECT);
     if (l == 0 && log0)
       LR_TRY(launch_chase_log(desc, in.succ, work_of(1), ns, qctr, p.chase_grid, p.chase_block, err,
-                              (uint32_t *)(var + p.off_log), (uint2 *)(var + p.off_hdr), p.per_cta,
-                              p.total_chunks, (uint32_t *)(fixed + p.off_ovf), s));
+                              (uint32_t *)(var + p.off_log), (uint2 *)(var + p.off_hdr),
+                              p.total_chunks, (uint32_t *)(fixed + p.off_logctr), s));
     else if (l == 0 && p.spawn_cap) {
       // spawning: reduced records at uncompacted ids, then compacted into level 1
       LR_TRY(launch_chase(desc, 0, work0, r16, var + p.off_sraw, ns, qctr, p.chase_grid, p.chase_block,
@@ -824,7 +823,8 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   for (int l = L - 1; l >= 0; --l) {
     if (l == 0 && log0)
       LR_TRY(launch_finalize_log(desc, (const uint32_t *)(var + p.off_log), (const uint2 *)(var + p.off_hdr),
-                                 p.total_chunks, R_of(1), (uint2 *)(var + p.off_pairs),
+                                 p.total_chunks, (const uint32_t *)(fixed + p.off_logctr), R_of(1),
+                                 (uint2 *)(var + p.off_pairs),
                                  (uint2 *)(var + p.off_pairsB), (uint32_t *)(var + p.off_cur),
                                  (uint32_t *)(var + p.off_cur) + p.lg.na, p.lg, (uint32_t *)in.rank, err, s));
     else if (l == 0 && ptrs)

@@ -29,7 +29,7 @@ struct Plan {
   int rank_bytes;
   int chase_grid, chase_block;
   // fixed part (does not depend on the list bound)
-  size_t off_desc, off_zero, zero_bytes, off_err, off_hcount, off_acc, off_ovf, off_bctr, off_q,
+  size_t off_desc, off_zero, zero_bytes, off_err, off_hcount, off_acc, off_logctr, off_bctr, off_q,
       off_bcnt, off_bitmap;
   size_t fixed_bytes;
   // variable part
@@ -41,7 +41,7 @@ struct Plan {
   bool term;                        // terminal ids carried through the levels
   size_t off_T[kMaxLevels + 1], off_tid[kMaxLevels + 1], off_T0, off_hC, off_pdt[2];
   size_t off_log, off_hdr, off_pairs, off_pairsB, off_cur;   // log path
-  uint32_t per_cta, total_chunks, shift;
+  uint32_t total_chunks, shift;
   size_t cur_bytes;
   LogGeom lg;
   size_t var_bytes;

@@ -114,7 +114,9 @@ cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec
                             uint32_t *err, const uint32_t *tnext, uint32_t *tout,
                             const uint32_t *tid_cur, cudaStream_t s);
 
-// Log path (unweighted level 0, see lr_log.cu).
+// Log path (unweighted level 0, see lr_log.cu).  The log's chunks go to the
+// chasing CTAs in windows of kLogWindow chunks.
+constexpr uint32_t kLogWindow = 32;
 cudaError_t launch_sum0(const uint32_t *succ, uint32_t n, unsigned long long *acc, unsigned long long *local,
                         uint32_t *err, cudaStream_t s);
 cudaError_t launch_heads0_log(LevelDesc *desc, const unsigned long long *acc, uint32_t *hlist0,
@@ -122,8 +124,7 @@ cudaError_t launch_heads0_log(LevelDesc *desc, const unsigned long long *acc, ui
                               int validate, cudaStream_t s);
 cudaError_t launch_chase_log(LevelDesc *desc, const uint32_t *succ, void *next_work, const uint32_t *ns,
                              uint32_t *qctr, int grid, int block, uint32_t *err, uint32_t *log,
-                             uint2 *hdr, uint32_t per_cta, uint32_t total_chunks, uint32_t *ovf,
-                             cudaStream_t s);
+                             uint2 *hdr, uint32_t total_chunks, uint32_t *ctr, cudaStream_t s);
 // Geometry of the log path's propagation (lr_log.cu): windows of 2^14 ranks;
 // level A partitions into na buckets of 2^shiftA ids (regions of capA pairs,
 // gridA CTAs, claims of claimA slots); with sB > 0, level B splits each
@@ -133,8 +134,9 @@ struct LogGeom {
 };
 LogGeom log_geometry(uint32_t n);
 cudaError_t launch_finalize_log(LevelDesc *desc, const uint32_t *log, const uint2 *hdr, uint32_t total_chunks,
-                                const void *r1, uint2 *pairsA, uint2 *pairsB, uint32_t *curA, uint32_t *curB,
-                                const LogGeom &g, uint32_t *rank, uint32_t *err, cudaStream_t s);
+                                const uint32_t *chunk_ctr, const void *r1, uint2 *pairsA, uint2 *pairsB,
+                                uint32_t *curA, uint32_t *curB, const LogGeom &g, uint32_t *rank, uint32_t *err,
+                                cudaStream_t s);
 cudaError_t log_setup();
 int chase_log_occupancy(int block);
 

@@ -123,13 +123,15 @@ cudaError_t launch_heads0_log(LevelDesc *desc, const unsigned long long *acc, ui
 }
 
 // ---------------------------------------------------------------- log writer
+// Chunks are handed out from one global counter, to each CTA in windows of
+// kLogWindow consecutive chunks (one global atomic per window), so that the
+// used chunks are exactly [0, *ctr) whatever the segments' lengths, apart
+// from the unused rest of each CTA's last window (headers kLogEnd).
 struct LogCfg {
   uint32_t *log;          // chunks of kChunk entries
   uint2 *hdr;             // per chunk: (ruler, offset) of its first entry, or (kLogEnd, 0)
-  uint32_t per_cta;       // chunks reserved for each CTA
-  uint32_t main_chunks;   // per_cta * grid
-  uint32_t total_chunks;  // main + overflow pool
-  uint32_t *ovf;          // overflow pool cursor
+  uint32_t total_chunks;  // capacity
+  uint32_t *ctr;          // chunks handed out (zeroed per call)
 };
 
 // Entries are buffered eight at a time (a register shift buffer) and stored
@@ -145,21 +147,32 @@ struct LogWriter {
     slot = kChunk; nb = 0; ok = true; chunk = 0; gc = kLogEnd; go = 0;
     b0 = b1 = b2 = b3 = b4 = b5 = b6 = b7 = kLogEnd;
   }
-  __device__ bool alloc(const LogCfg &L, uint32_t *s_used) {
-    const uint32_t i = atomicAdd(s_used, 1u);
-    uint64_t id = (uint64_t)blockIdx.x * L.per_cta + i;
-    if (i >= L.per_cta || id >= L.main_chunks) {
-      id = (uint64_t)L.main_chunks + atomicAdd(L.ovf, 1u);
-      if (id >= L.total_chunks) { ok = false; return false; }
+  // s_win: the CTA's window, (end << 32) | next, in global chunk ids.  The
+  // thread that draws next == end takes a new window from the global
+  // counter; threads that draw past the end meanwhile take one chunk each
+  // from the global counter.  Nobody waits.
+  __device__ bool alloc(const LogCfg &L, unsigned long long *s_win) {
+    const unsigned long long w = atomicAdd(s_win, 1ull);
+    const uint32_t next = (uint32_t)w, end = (uint32_t)(w >> 32);
+    uint64_t id;
+    if (next < end) {
+      id = next;
+    } else if (next == end) {
+      id = atomicAdd(L.ctr, kLogWindow);
+      if (id + kLogWindow <= L.total_chunks)
+        atomicExch(s_win, ((unsigned long long)(id + kLogWindow) << 32) | (id + 1));
+    } else {
+      id = atomicAdd(L.ctr, 1u);
     }
+    if (id >= L.total_chunks) { ok = false; return false; }
     chunk = (uint32_t)id;
     slot = 0;
     L.hdr[chunk] = make_uint2(gc, go);
     return true;
   }
-  __device__ void flush(const LogCfg &L, uint32_t *s_used) {
+  __device__ void flush(const LogCfg &L, unsigned long long *s_win) {
     nb = 0;
-    if (!ok || (slot == kChunk && !alloc(L, s_used))) return;
+    if (!ok || (slot == kChunk && !alloc(L, s_win))) return;
     st_sector(L.log + (size_t)chunk * kChunk + slot, b0, b1, b2, b3, b4, b5, b6, b7);
     slot += 8;
   }
@@ -167,16 +180,16 @@ struct LogWriter {
     b0 = b1; b1 = b2; b2 = b3; b3 = b4; b4 = b5; b5 = b6; b6 = b7; b7 = v;
   }
   // v: the entry; (c, o): its ruler and offset when v is an element
-  __device__ __forceinline__ void put(const LogCfg &L, uint32_t *s_used, uint32_t v, uint32_t c,
+  __device__ __forceinline__ void put(const LogCfg &L, unsigned long long *s_win, uint32_t v, uint32_t c,
                                       uint32_t o) {
     if (nb == 0) { gc = c; go = o; }
     shift_in(v);
-    if (++nb == 8) flush(L, s_used);
+    if (++nb == 8) flush(L, s_win);
   }
-  __device__ void finish(const LogCfg &L, uint32_t *s_used) {
+  __device__ void finish(const LogCfg &L, unsigned long long *s_win) {
     if (nb > 0) {
       while (nb < 8) { shift_in(kLogEnd); ++nb; }
-      flush(L, s_used);
+      flush(L, s_win);
     }
     if (ok && slot < kChunk) {
       for (; slot < kChunk; slot += 8)
@@ -194,8 +207,8 @@ __global__ void __launch_bounds__(512)
 k_chase_log(LevelDesc *__restrict__ desc, const uint32_t *__restrict__ succ, Rec16 *__restrict__ next,
             const uint32_t *__restrict__ ns, uint32_t *__restrict__ qctr, uint32_t *__restrict__ err,
             LogCfg L) {
-  __shared__ uint32_t s_used;
-  if (threadIdx.x == 0) s_used = 0;
+  __shared__ unsigned long long s_win;
+  if (threadIdx.x == 0) s_win = 0;
   __syncthreads();
   const LevelDesc d = desc[0];
   if (d.mode != kModeSrs) return;
@@ -214,11 +227,11 @@ k_chase_log(LevelDesc *__restrict__ desc, const uint32_t *__restrict__ succ, Rec
     const uint64_t cnext = (uint64_t)lo + atomicAdd(q, 1u);
     const uint32_t c = (uint32_t)c64;
     const uint32_t rho = c < r ? P.inv(c) : __ldcg(ns + (c - r));
-    W.put(L, &s_used, kMark | c, kLogEnd, 0);
+    W.put(L, &s_win, kMark | c, kLogEnd, 0);
     uint32_t x = rho, o = 0, nxt = c;
     for (;;) {
       const uint32_t s = __ldcg(succ + x);
-      W.put(L, &s_used, x, c, o);
+      W.put(L, &s_win, x, c, o);
       ++visited;
       if (s >= n) { bad |= 8u; break; }
       if (s == x) break;                       // terminal: segment length o links
@@ -240,7 +253,7 @@ k_chase_log(LevelDesc *__restrict__ desc, const uint32_t *__restrict__ succ, Rec
     __stcg(reinterpret_cast<uint4 *>(next + c), make_uint4(nxt, kUnvisited, o, 0u));
     c64 = cnext;
   }
-  W.finish(L, &s_used);
+  W.finish(L, &s_win);
   if (!W.ok) bad |= 16u;
   if (bad & 1u) record_error(err, kErrNotList);
   if (bad & 2u) record_error(err, kErrCycle);
@@ -253,15 +266,12 @@ k_chase_log(LevelDesc *__restrict__ desc, const uint32_t *__restrict__ succ, Rec
 
 cudaError_t launch_chase_log(LevelDesc *desc, const uint32_t *succ, void *next_work, const uint32_t *ns,
                              uint32_t *qctr, int grid, int block, uint32_t *err, uint32_t *log,
-                             uint2 *hdr, uint32_t per_cta, uint32_t total_chunks, uint32_t *ovf,
-                             cudaStream_t s) {
+                             uint2 *hdr, uint32_t total_chunks, uint32_t *ctr, cudaStream_t s) {
   LogCfg L;
   L.log = log;
   L.hdr = hdr;
-  L.per_cta = per_cta;
-  L.main_chunks = per_cta * (uint32_t)grid;
   L.total_chunks = total_chunks;
-  L.ovf = ovf;
+  L.ctr = ctr;
   k_chase_log<<<grid, block, 0, s>>>(desc, succ, reinterpret_cast<Rec16 *>(next_work), ns, qctr, err, L);
   count_launch();
   return cudaGetLastError();
@@ -510,16 +520,17 @@ __device__ void part_flush(PartSmem &S, const PartOut &P, uint32_t &bad) {
 // ---- level A: decode the log, rank = R_1[ruler] - offset, partition by y >> shift
 __global__ void __launch_bounds__(kPartThreads, 2)
 k_part_log(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log, const uint2 *__restrict__ hdr,
-           uint32_t total_chunks, const uint32_t *__restrict__ r1, PartOut P, uint32_t shift,
-           uint32_t *__restrict__ err) {
+           uint32_t total_chunks, const uint32_t *__restrict__ chunk_ctr, const uint32_t *__restrict__ r1,
+           PartOut P, uint32_t shift, uint32_t *__restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem_part[];
   PartSmem &S = *reinterpret_cast<PartSmem *>(smem_part);
   const LevelDesc d = desc[0];
   if (d.mode != kModeSrs) return;
   const uint32_t n = d.n, nn = desc[1].n;
   part_init(S, P.nb);
-  const uint32_t c0 = (uint32_t)((uint64_t)total_chunks * blockIdx.x / gridDim.x);
-  const uint32_t c1 = (uint32_t)((uint64_t)total_chunks * (blockIdx.x + 1) / gridDim.x);
+  const uint32_t used = min(__ldcg(chunk_ctr), total_chunks);       // chunks the chase handed out
+  const uint32_t c0 = (uint32_t)((uint64_t)used * blockIdx.x / gridDim.x);
+  const uint32_t c1 = (uint32_t)((uint64_t)used * (blockIdx.x + 1) / gridDim.x);
   // a tile: every warp decodes 2 x kDecodeIlp chunks; each lane keeps its
   // (at most one per chunk) elements in registers
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -700,15 +711,16 @@ cudaError_t log_setup() {
 }
 
 cudaError_t launch_finalize_log(LevelDesc *desc, const uint32_t *log, const uint2 *hdr, uint32_t total_chunks,
-                                const void *r1, uint2 *pairsA, uint2 *pairsB, uint32_t *curA, uint32_t *curB,
-                                const LogGeom &g, uint32_t *rank, uint32_t *err, cudaStream_t s) {
+                                const uint32_t *chunk_ctr, const void *r1, uint2 *pairsA, uint2 *pairsB,
+                                uint32_t *curA, uint32_t *curB, const LogGeom &g, uint32_t *rank, uint32_t *err,
+                                cudaStream_t s) {
   PartOut A;
   A.out = pairsA;
   A.cur = curA;
   A.cap = g.capA;
   A.claim = g.claimA;
   A.nb = g.na;
-  k_part_log<<<g.gridA, kPartThreads, part_smem(), s>>>(desc, log, hdr, total_chunks,
+  k_part_log<<<g.gridA, kPartThreads, part_smem(), s>>>(desc, log, hdr, total_chunks, chunk_ctr,
                                                         reinterpret_cast<const uint32_t *>(r1), A, g.shiftA, err);
   int launches = 2;
   if (g.sB > 0) {
