@@ -111,3 +111,38 @@ def test_pipeline_argument_errors():
     for bad in (dict(depth=1), dict(depth=5), dict(max_lists=-1)):
         with pytest.raises(lr.LRError):
             lr.Pipeline(1000, **bad)
+
+
+def test_pipeline_log_form_sizes():
+    """Lists of 2^25 and more take the log form at level 0 (auto): through the
+    pipeline's own workspace, sized by lr_workspace_size, in every slot, next
+    to smaller lists ranked with the exchange form."""
+    big = (1 << 25) + 1
+    lists = [gen.random_list(big, 70), gen.random_list(100_003, 71), gen.random_list(big - 64, 72),
+             gen.forest(big, 73, n_long=4, long_len=1 << 20, mean_short=64)[0]]
+    pipe = lr.Pipeline(big, depth=2, max_lists=0)
+    outs = [pipe.submit(pinned(s)) for s in lists]
+    pipe.wait()
+    for s, o in zip(lists, outs):
+        np.testing.assert_array_equal(o.numpy(), oracle.rank(s))
+    pipe.close()
+
+
+def test_log_form_exact_workspace_and_host_buffers():
+    """A caller workspace of exactly lr_workspace_size bytes suffices for the
+    log form; the host-buffer entry point takes it too."""
+    n = (1 << 25) + 1
+    succ = gen.random_list(n, 74)
+    want = oracle.rank(succ)
+    ws_bytes = lr.workspace_size(n, max_lists=1)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    d = torch.from_numpy(succ.view(np.int32)).cuda()
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    lr.rank_ex(d, out=out, max_lists=1, workspace=ws)
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+    small = torch.empty(ws_bytes // 2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lr.LRError):
+        lr.rank_ex(d, out=out, max_lists=1, workspace=small)
+    host = np.empty(n, dtype=np.int32)
+    lr.rank_host(succ, out=host, max_lists=1)
+    np.testing.assert_array_equal(host, want)
