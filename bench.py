@@ -636,7 +636,8 @@ def run_serve(args):
         results[mode] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
                          "p99_ms": round(float(np.percentile(lat, 99)), 3),
                          "elements_per_s": round(elems / ((t_last - t_first) * 1e-3), 1),
-                         "batches": int(st["batches"]), "requests": int(args.requests)}
+                         "batches": int(st["batches"]), "ranked_alone": int(st["ranked_alone"]),
+                         "requests": int(args.requests)}
     print(json.dumps({
         "workload": "serve", "metric": "served G list elements/s and p50/p99 latency",
         "value": round(results["batched"]["elements_per_s"] / 1e9, 4), "unit": UNIT,

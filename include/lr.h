@@ -359,6 +359,10 @@ int64_t lr_kernel_launch_count(void);
  * Continuous batching: requests of mixed sizes are admitted while their
  * device footprint fits the memory budget, grouped as they arrive into
  * batched launches on one of n_streams streams, and completed individually.
+ * A request of at least alone_min_n elements is a batch of its own, and a
+ * batch of one request is ranked through the single-list path (as lr_rank_ex
+ * ranks it, with its tile-local contraction and level-0 form); smaller
+ * requests are ranked together as one forest.
  */
 typedef struct lr_server lr_server;
 
@@ -368,7 +372,11 @@ typedef struct lr_server_config {
     int32_t max_batch;       /* most requests per launch (default 256)               */
     int64_t max_batch_elems; /* most elements per launch (default 2^28)              */
     int32_t device;          /* CUDA device ordinal (default 0)                      */
-    int32_t plain;           /* 1: launch every request alone (baseline mode)        */
+    int32_t plain;           /* 1: rank every request alone through the single-list  */
+                             /* path, as lr_rank_ex does (baseline mode)             */
+    int64_t alone_min_n;     /* a request of at least this many elements is ranked   */
+                             /* alone, never batched with others; 0 = default 2^20,  */
+                             /* < 0 = batch requests of any size                     */
 } lr_server_config;
 
 void lr_server_config_default(lr_server_config *c);
@@ -396,6 +404,9 @@ typedef struct lr_server_stats {
     double p50_ms, p99_ms, mean_ms;   /* submit -> done                            */
     double elements_per_s;            /* completed elements / busy wall time        */
     size_t peak_resident_bytes;
+    int64_t ranked_alone;             /* batches of one request (ranked through the */
+                                      /* single-list path; all of them in plain     */
+                                      /* mode)                                      */
 } lr_server_stats;
 
 lr_status lr_server_create(const lr_server_config *cfg, lr_server **out);

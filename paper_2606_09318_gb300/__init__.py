@@ -81,7 +81,7 @@ class _Profile(ctypes.Structure):
 class _ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("n_streams", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("max_batch_elems", ctypes.c_int64),
-                ("device", ctypes.c_int32), ("plain", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("plain", ctypes.c_int32), ("alone_min_n", ctypes.c_int64)]
 
 
 class _Request(ctypes.Structure):
@@ -99,7 +99,8 @@ class _Result(ctypes.Structure):
 class _ServerStats(ctypes.Structure):
     _fields_ = [("completed", ctypes.c_int64), ("elements", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
-                ("elements_per_s", ctypes.c_double), ("peak_resident_bytes", ctypes.c_size_t)]
+                ("elements_per_s", ctypes.c_double), ("peak_resident_bytes", ctypes.c_size_t),
+                ("ranked_alone", ctypes.c_int64)]
 
 
 class _ProbeResult(ctypes.Structure):
@@ -593,12 +594,13 @@ class Server:
     """Continuous-batching ranking server (lr_server_* of the C ABI)."""
 
     def __init__(self, budget_bytes=40_000_000_000, n_streams=2, max_batch=256,
-                 max_batch_elems=1 << 28, device=0, plain=False):
+                 max_batch_elems=1 << 28, device=0, plain=False, alone_min_n=0):
         lib = load()
         c = _ServerConfig()
         lib.lr_server_config_default(ctypes.byref(c))
         c.budget_bytes, c.n_streams, c.max_batch = int(budget_bytes), int(n_streams), int(max_batch)
         c.max_batch_elems, c.device, c.plain = int(max_batch_elems), int(device), 1 if plain else 0
+        c.alone_min_n = int(alone_min_n)
         h = ctypes.c_void_p()
         _check(lib.lr_server_create(ctypes.byref(c), ctypes.byref(h)), "lr_server_create")
         self._h = h

@@ -865,6 +865,21 @@ lr_status run_fixed_scratch(const uint32_t *succ, int64_t n, int32_t *rank, void
   return run(in, nullptr, s);
 }
 
+lr_status run_single(const uint32_t *succ, const void *weight, int wtype, void *rank, int rank_bytes,
+                     int64_t n, uint64_t seed, cudaStream_t s) {
+  Inputs in;
+  memset(&in, 0, sizeof(in));
+  in.succ = succ;
+  in.weight = weight;
+  in.wtype = wtype;
+  in.rank = rank;
+  in.rank_bytes = rank_bytes;
+  in.n = (uint64_t)n;
+  in.seed = seed;
+  in.sync = 1;
+  return run(in, nullptr, s);
+}
+
 lr_status run_ptr_batch(const int64_t *offsets, int32_t k, int64_t n_total,
                         const uint32_t *const *sptr, const void *const *wptr, void *const *rptr,
                         int wtype, int rank_bytes, uint64_t seed, cudaStream_t s) {

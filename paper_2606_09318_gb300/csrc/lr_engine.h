@@ -94,6 +94,11 @@ lr_status run_fixed_scratch(const uint32_t *succ, int64_t n, int32_t *rank, void
                             size_t scratch_bytes, Ctx *ctx, cudaStream_t s);
 // Kernel attributes (shared-memory limits) for the current device, once.
 lr_status setup_device_once();
+// One list in device memory, ranked on its own (the single-instance path,
+// with its automatic choices: tile-local contraction, the level-0 form);
+// waits for the result and returns the status.
+lr_status run_single(const uint32_t *succ, const void *weight, int wtype, void *rank, int rank_bytes,
+                     int64_t n, uint64_t seed, cudaStream_t s);
 // Rank k instances given by per-instance device pointers (tables in device
 // memory); waits for the result and returns the status.
 lr_status run_ptr_batch(const int64_t *offsets, int32_t k, int64_t n_total,

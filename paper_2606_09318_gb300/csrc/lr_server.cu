@@ -11,6 +11,13 @@
 // so work from different batches overlaps on the device.  If a batch reports
 // a data error, its requests are re-ranked one by one so every request gets
 // its own status.
+//
+// A request of at least alone_min_n elements is a batch of its own: it gains
+// nothing from batching, the single-list path takes the size-dependent
+// choices the batched form does not (tile-local contraction of Section 2.3,
+// the level-0 form), and smaller requests do not wait for it in a batch.
+// Every batch of one request is ranked through the single-list path, as
+// lr_rank_ex would rank it; in plain mode every batch holds one request.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,6 +48,8 @@ struct Req {
 
 size_t wbytes(lr_dtype t) { return t == LR_I32 ? 4 : (t == LR_I64 ? 8 : 0); }
 
+constexpr int64_t kAloneMinDefault = (int64_t)1 << 20;
+
 // Device bytes a request holds while it is resident: its own buffers when
 // the server copies them, plus an estimate of its share of the ranking
 // workspace (records, bitmap, reduced levels).
@@ -65,7 +74,7 @@ struct lr_server {
   std::vector<std::thread> workers;
   Clock::time_point t0;
   std::vector<double> lat;
-  int64_t completed = 0, elements = 0, batches = 0;
+  int64_t completed = 0, elements = 0, batches = 0, ranked_alone = 0;
   double first_submit = -1, last_done = 0;
 
   double now_ms() const {
@@ -94,26 +103,45 @@ void lr_server::worker(int idx) {
   void **dw = ds + maxb;
   void **dr = dw + maxb;
   uint64_t seed = 0x5e71e + (uint64_t)idx;
+  const int64_t alone_min = cfg.alone_min_n == 0 ? kAloneMinDefault : cfg.alone_min_n;
 
-  auto run_tables = [&](std::vector<Req *> &b) -> lr_status {
+  // the request's arrays on the device: the caller's, or the staged copies
+  auto dsucc_of = [](Req *q) { return q->r.on_device ? q->r.succ : (const uint32_t *)q->dsucc; };
+  auto dw_of = [](Req *q) { return q->r.on_device ? q->r.weight : (const void *)q->dw; };
+  auto drank_of = [](Req *q) { return q->r.on_device ? q->r.rank : q->drank; };
+
+  // offsets and pointer tables of b, uploaded on s; returns the element total
+  auto fill_tables = [&](std::vector<Req *> &b) -> int64_t {
     const int k = (int)b.size();
     int64_t tot = 0;
     for (int j = 0; j < k; ++j) {
       hoff[j] = tot;
       tot += b[j]->r.n;
-      hs[j] = b[j]->r.on_device ? (void *)b[j]->r.succ : b[j]->dsucc;
-      hw[j] = b[j]->r.on_device ? (void *)b[j]->r.weight : b[j]->dw;
-      hr[j] = b[j]->r.on_device ? b[j]->r.rank : b[j]->drank;
+      hs[j] = (void *)dsucc_of(b[j]);
+      hw[j] = (void *)dw_of(b[j]);
+      hr[j] = drank_of(b[j]);
     }
     hoff[k] = tot;
     cudaMemcpyAsync(doff, hoff, 8 * (size_t)(k + 1), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(ds, hs, 8 * (size_t)k, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dw, hw, 8 * (size_t)k, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dr, hr, 8 * (size_t)k, cudaMemcpyHostToDevice, s);
+    return tot;
+  };
+
+  auto run_tables = [&](std::vector<Req *> &b) -> lr_status {
+    const int k = (int)b.size();
+    const int64_t tot = fill_tables(b);
     if (tot == 0) return LR_OK;
     return lr::run_ptr_batch(doff, k, tot, (const uint32_t *const *)ds, (const void *const *)dw,
                              (void *const *)dr, (int)b[0]->r.wtype, b[0]->r.rtype == LR_I32 ? 4 : 8,
                              seed++, s);
+  };
+
+  // one request through the single-list path (waits for its status)
+  auto run_alone = [&](Req *q) -> lr_status {
+    return lr::run_single(dsucc_of(q), dw_of(q), (int)q->r.wtype, drank_of(q), q->r.rtype == LR_I32 ? 4 : 8,
+                          q->r.n, seed++, s);
   };
 
   for (;;) {
@@ -128,7 +156,9 @@ void lr_server::worker(int idx) {
       const double t = now_ms();
       while (!pending.empty() && (int)batch.size() < maxb) {
         Req *q = pending.front();
+        const bool own = cfg.plain || (alone_min >= 0 && q->r.n >= alone_min);
         if (!batch.empty()) {
+          if (own) break;   // a large request starts a batch of its own
           if (q->r.wtype != batch[0]->r.wtype || q->r.rtype != batch[0]->r.rtype) break;
           if (elems + q->r.n > cfg.max_batch_elems) break;
         }
@@ -139,7 +169,7 @@ void lr_server::worker(int idx) {
         q->res.t_admit_ms = t;
         batch.push_back(q);
         elems += q->r.n;
-        if (cfg.plain) break;
+        if (own) break;
       }
     }
     if (batch.empty()) continue;
@@ -160,14 +190,16 @@ void lr_server::worker(int idx) {
     }
     const double tl = now_ms();
     for (Req *q : batch) q->res.t_launch_ms = tl;
+    const bool alone = batch.size() == 1;
     if (stage == LR_OK) {
-      lr_status st = run_tables(batch);
-      if (st == LR_OK || batch.size() == 1) {
-        for (Req *q : batch) q->res.status = st;
+      if (alone) {
+        batch[0]->res.status = run_alone(batch[0]);
       } else {
-        for (Req *q : batch) {   // attribute the error: re-rank each request alone
-          std::vector<Req *> one{q};
-          q->res.status = run_tables(one);
+        lr_status st = run_tables(batch);
+        if (st == LR_OK) {
+          for (Req *q : batch) q->res.status = st;
+        } else {
+          for (Req *q : batch) q->res.status = run_alone(q);   // attribute the error
         }
       }
       for (Req *q : batch)
@@ -197,6 +229,7 @@ void lr_server::worker(int idx) {
       }
       last_done = t;
       batches += 1;
+      ranked_alone += alone ? 1 : 0;
     }
     cv_done.notify_all();
     cv_work.notify_all();
@@ -218,6 +251,7 @@ void lr_server_config_default(lr_server_config *c) {
   c->max_batch_elems = (int64_t)1 << 28;
   c->device = 0;
   c->plain = 0;
+  c->alone_min_n = 0;
 }
 
 lr_status lr_server_create(const lr_server_config *cfg, lr_server **out) {
@@ -302,6 +336,7 @@ lr_status lr_server_stats_get(lr_server *s, lr_server_stats *out) {
   out->elements = s->elements;
   out->batches = s->batches;
   out->peak_resident_bytes = s->peak;
+  out->ranked_alone = s->ranked_alone;
   if (!s->lat.empty()) {
     std::vector<double> v = s->lat;
     std::sort(v.begin(), v.end());

@@ -102,7 +102,35 @@ def test_server_alone_equals_in_mix(n_streams, plain):
     assert st["completed"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
     if not plain:
         assert st["batches"] <= len(reqs)
+    else:
+        assert st["ranked_alone"] == len(reqs)
     srv.close()
+
+
+def test_server_large_requests_ranked_alone():
+    # Requests of at least alone_min_n elements are batches of their own and
+    # take the single-list path (which contracts the locality and identity
+    # orders); smaller ones are batched.  Every result equals the oracle's.
+    reqs = []
+    for i in range(6):
+        m = (1 << 17) + 1000 * i + 7
+        kind = ("random", "locality", "identity")[i % 3]
+        reqs.append((gen.list_of_order_kind(kind, m, 600 + i), gen.weights_i64(m, 700 + i)))
+    for i in range(10):
+        m = 3000 + 977 * i
+        reqs.append((gen.list_of_order_kind(("random", "locality")[i % 2], m, 800 + i), gen.weights_i64(m, 900 + i)))
+    order = np.random.default_rng(3).permutation(len(reqs))
+    reqs = [reqs[i] for i in order]
+    for alone_min, n_big in ((1 << 16, 6), (-1, 0)):
+        srv = lr.Server(budget_bytes=4_000_000_000, n_streams=1, max_batch=32, alone_min_n=alone_min)
+        tickets = [srv.submit(dev(s_), dev(w_)) for s_, w_ in reqs]
+        for (succ, w), t in zip(reqs, tickets):
+            out, _ = srv.wait(t)
+            np.testing.assert_array_equal(out.cpu().numpy(), oracle.rank(succ, w, np.int64))
+        st = srv.stats()
+        assert st["completed"] == len(reqs)
+        assert st["ranked_alone"] >= n_big       # plus small requests that happened to arrive alone
+        srv.close()
 
 
 def test_server_budget_and_errors():
