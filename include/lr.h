@@ -291,9 +291,10 @@ lr_status lr_get_device_status(lr_stream stream);
  *  - Workspace is a fixed 64 MiB scratch array compiled into liblr.so; every
  *    GPU that loads the library holds it until the process exits.  The
  *    first call on a device looks up the array's device address (with that
- *    device current).  No cudaMalloc, cudaFree or other allocating call is
- *    made.  Inputs with so many lists that the recursion does not fit the
- *    scratch return LR_ERR_CAPACITY.
+ *    device current) and sets up the library's kernels there; make that
+ *    first call before any stream capture begins.  No cudaMalloc, cudaFree
+ *    or other allocating call is made.  Inputs with so many lists that the
+ *    recursion does not fit the scratch return LR_ERR_CAPACITY.
  *  - All calls share the scratch, which keeps the last call's contents
  *    (everything that must start at zero is cleared by each call).  Calls
  *    that overlap on the GPU race, and the host side is not thread-safe:
