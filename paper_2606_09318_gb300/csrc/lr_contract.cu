@@ -18,10 +18,13 @@
 // Contracted ids are dense: a rank/select structure over the local-head
 // bitmap gives node(x) = heads in earlier tiles + heads before x in its tile.
 //
-// Inside a tile, dist and t come from short bounded walks between
-// sub-rulers in shared memory (every element once) and pointer doubling
-// over the few sub-rulers: O(tile) work, unlike pointer doubling over the
-// whole tile's O(tile log tile).
+// Inside a tile, dist and t come from pointer doubling over all of the
+// tile's elements in shared memory, each thread holding the pointers and
+// distances of its eight elements in registers: at most log2(tile) rounds
+// of one shared-memory gather per element, with no divergence, and it stops
+// as soon as a round moves no pointer.  (A ruling set inside the tile does
+// less work, but its walks diverge and its phases need more barriers; on
+// GB300 the doubling was the faster of the two.)
 //
 // Passes: solve (every tile in shared memory: distances to the local tails,
 // the local-head bitmap), scan (tile prefixes), nodes (the contracted
@@ -63,220 +66,204 @@ __device__ __forceinline__ bool lc_is_head(uint32_t x, const uint32_t *hb) {
   return (__ldcg(hb + (x >> 5)) >> (x & 31u)) & 1u;
 }
 
-constexpr uint32_t kSubDefault = 8;    // every ksub-th local id is a sub-ruler (dense tiles)
-constexpr uint32_t kMaxSr = 2 * kLcThreads;   // sub-rulers ranked by pointer doubling
-
-// Shared-memory state of one tile.
-template <class VT>
+// Shared-memory state of one tile.  Every element of the tile carries a
+// pointer p (first its local successor, or itself for a local tail) and the
+// link-weight distance d to p; pointer doubling (p, d) <- (p[p], d + d[p])
+// from one buffer into the other reaches the local tail and the distance to
+// it in at most kTileShift rounds, because a local sublist has fewer than
+// kTile links.  p < 2^16, so one word holds d << 16 | p where d fits:
+// unweighted distances (below kTile) in 32 bits, distances over weights
+// that fit in int32 (below kTile * 2^31 in magnitude) in 64 bits.  Adding
+// two packed words whose first has its p bits cleared adds the distances
+// and takes the second's pointer.  A tile with a wider int64 weight keeps
+// the distances in a separate array, single-buffered (two barriers a round).
+template <int WT>
 struct LcTile {
-  uint32_t raw[kTile];       // succ of each element of the tile
-  uint16_t nxt[kTile];       // local successor or kEnd16; then per sub-ruler: next sub-ruler
-  uint16_t sub[kTile];       // predecessor marks; then the element's sub-ruler; per sub-ruler:
-                             // its local tail once known (kEnd16 between tiles)
-  VT off[kTile];             // link weight; then offset from the sub-ruler; per sub-ruler: distance
+  uint32_t pk[2][kTile];     // d << 16 | p, double-buffered
   uint32_t pred[kTileWords]; // has-local-predecessor bitmap
-  uint16_t srl[kMaxSr];      // dense tiles: heads whose id is not a multiple of ksub
-  uint32_t nheads, nlinks, nextra, dense, submask;
+  uint32_t tail[kTileWords]; // local-tail bitmap: no local successor
+};
+template <>
+struct LcTile<1> {
+  uint64_t pk[2][kTile];
+  uint32_t pred[kTileWords];
+  uint32_t tail[kTileWords];
+};
+template <>
+struct LcTile<2> {
+  union {
+    uint64_t pk[2][kTile];   // every weight of the tile fits in int32
+    struct {
+      uint64_t d[kTile];     // otherwise: distances
+      uint16_t p[kTile];     // and pointers
+    } w;
+  };
+  uint32_t pred[kTileWords];
+  uint32_t tail[kTileWords];
 };
 
-template <class VT>
-__device__ __forceinline__ bool lc_head(const LcTile<VT> &S, uint32_t j) {
-  return !((S.pred[j >> 5] >> (j & 31u)) & 1u);
+// Per-element state a thread keeps in registers: the packed word (WT 0
+// and 1), or the distance with the pointer beside it (WT 2).
+template <int WT> struct LcState { using T = uint64_t; };
+template <> struct LcState<0> { using T = uint32_t; };
+
+// Elements a thread owns: two runs of four consecutive ids, 4*tid and
+// kTile/2 + 4*tid, so that every run is one vector load or store.
+constexpr uint32_t kLcRuns = kTile / (4 * kLcThreads);
+static_assert(kLcRuns * 4 * kLcThreads == kTile, "a tile is kLcRuns runs of four per thread");
+constexpr uint32_t kLcRunStride = kTile / kLcRuns;
+
+// Store a run of four elements: packed into buffer b, or (wide) the
+// distances and pointers of the single-buffered form.
+template <int WT>
+__device__ __forceinline__ void lc_put(LcTile<WT> &S, int b, uint32_t j0, const typename LcState<WT>::T (&x)[4],
+                                       const uint32_t (&p)[4], bool wide) {
+  if constexpr (WT == 0) {
+    *reinterpret_cast<uint4 *>(&S.pk[b][j0]) = make_uint4(x[0], x[1], x[2], x[3]);
+  } else {
+    if constexpr (WT == 2) {
+      if (wide) {
+        *reinterpret_cast<uint2 *>(&S.w.p[j0]) = make_uint2(p[0] | p[1] << 16, p[2] | p[3] << 16);
+        *reinterpret_cast<ulonglong2 *>(&S.w.d[j0]) = make_ulonglong2(x[0], x[1]);
+        *reinterpret_cast<ulonglong2 *>(&S.w.d[j0 + 2]) = make_ulonglong2(x[2], x[3]);
+        return;
+      }
+    }
+    *reinterpret_cast<ulonglong2 *>(&S.pk[b][j0]) = make_ulonglong2(x[0], x[1]);
+    *reinterpret_cast<ulonglong2 *>(&S.pk[b][j0 + 2]) = make_ulonglong2(x[2], x[3]);
+  }
 }
 
-// Sub-rulers: the local heads, and in dense tiles (few heads, long local
-// sublists) also every ksub-th id.  A walk never enters a local head, so
-// "the next element is a sub-ruler" is an arithmetic test.
-template <class VT>
-__device__ __forceinline__ bool lc_is_sr(const LcTile<VT> &S, uint32_t j) {
-  return lc_head(S, j) || (S.dense && (j & S.submask) == 0);
-}
-
-// One element of the load: succ, local link, weight; marks its target.
-template <int WT, class VT>
-__device__ __forceinline__ void lc_load1(LcTile<VT> &S, uint32_t j, uint32_t s, VT w, uint32_t t,
-                                         uint32_t base, uint32_t n, uint32_t &bad, uint32_t &links) {
-  const uint32_t i = base + j;
-  const bool local = s < n && s != i && (s >> kTileShift) == t;
-  if (s >= n) bad |= kErrRange;
-  S.nxt[j] = local ? (uint16_t)(s - base) : kEnd16;
-  S.off[j] = local ? w : (VT)0;
-  if (local) { S.sub[s - base] = (uint16_t)j; ++links; }
-}
-
-// Load tile `t` and find for every element its local tail and distance to
-// it.  sub[] must hold kEnd16 on entry.
-//   Marks: every local link stores its source into sub[target] (plain
-//   stores); one ballot per 32 elements turns them into the
-//   has-local-predecessor bitmap, and fewer marked targets than local links
-//   means an element with two predecessors.
-//   Level 1: every sub-ruler walks to the next sub-ruler (or its local
-//   tail), recording (sub-ruler, offset) in each element it passes.
-//   Level 2 (dense tiles): synchronous pointer doubling over the at most
-//   kMaxSr sub-rulers gives each its tail and distance.  In sparse tiles the
-//   sub-rulers are the heads alone, whose walks already end at their tails.
-// Walks are bounded by the tile length; an element no walk reaches lies on
-// a cycle.  Returns the tile length.
-template <int WT, class VT>
-__device__ uint32_t lc_tile_solve(LcTile<VT> &S, uint32_t t, const uint32_t *succ, const void *weight,
-                                  uint32_t n, uint32_t *err, bool vec, uint32_t ksub) {
+// Load tile `t` (len elements) and give every element its local tail p and
+// distance d to it (in the rank's arithmetic, modulo 2^64); p = kEnd16 for
+// an element on, or leading into, a cycle inside the tile.  Two local links
+// into one element and successors out of range are reported.  pred[] and
+// tail[] hold the tile's bitmaps afterwards.
+template <int WT>
+__device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uint32_t *succ,
+                              const void *weight, uint32_t n, bool vec, uint32_t (&p)[kLcRuns][4],
+                              uint64_t (&d)[kLcRuns][4], uint32_t &bad) {
+  using T = typename LcState<WT>::T;
   const uint32_t base = t << kTileShift;
-  const uint32_t len = min(kTile, n - base);
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t submask = ksub - 1u;
-  // the ids of one bitmap word that are multiples of ksub (2 <= ksub <= 32)
-  const uint32_t mulbits = ksub >= 32 ? 1u : (0xFFFFFFFFu / ((1u << ksub) - 1u));
-  if (threadIdx.x == 0) { S.nheads = 0; S.nlinks = 0; S.nextra = 0; S.submask = submask; }
-  uint32_t bad = 0, links = 0;
-  // load, four elements per thread and step
-  for (uint32_t g = threadIdx.x; g * 4 < len; g += blockDim.x) {
-    const uint32_t j = g * 4;
-    if (vec && j + 4 <= len) {
-      const uint4 sv = __ldcs(reinterpret_cast<const uint4 *>(succ + base + j));
-      VT w0 = 1, w1 = 1, w2 = 1, w3 = 1;
+  const uint32_t tid = threadIdx.x;
+  T x[kLcRuns][4];
+  // int64 weights: does any weight of the tile leave the int32 range?
+  bool wide = false;
+  if constexpr (WT == 2) {
+    int any = 0;
+#pragma unroll
+    for (uint32_t r = 0; r < kLcRuns; ++r)
+#pragma unroll
+      for (uint32_t e = 0; e < 4; ++e) {
+        const uint32_t j = r * kLcRunStride + 4 * tid + e;
+        if (j < len) {
+          const uint64_t v = lc_weight<2>(weight, base + j);
+          any |= ((v + 0x80000000ull) >> 32) != 0;
+        }
+      }
+    wide = __syncthreads_or(any) != 0;
+  }
+  // load: pointer = local successor, or the element itself when its link
+  // leaves the tile (a local tail, distance 0); mark local predecessors
+#pragma unroll
+  for (uint32_t r = 0; r < kLcRuns; ++r) {
+    const uint32_t j0 = r * kLcRunStride + 4 * tid;
+    uint32_t s[4];
+    uint64_t w[4] = {1, 1, 1, 1};
+    if (vec && j0 + 4 <= len) {
+      const uint4 sv = __ldcs(reinterpret_cast<const uint4 *>(succ + base + j0));
+      s[0] = sv.x; s[1] = sv.y; s[2] = sv.z; s[3] = sv.w;
       if constexpr (WT == 1) {
-        const int4 q = __ldcs(reinterpret_cast<const int4 *>(reinterpret_cast<const int *>(weight) + base + j));
-        w0 = (VT)(int64_t)q.x; w1 = (VT)(int64_t)q.y; w2 = (VT)(int64_t)q.z; w3 = (VT)(int64_t)q.w;
+        const int4 q = __ldcs(reinterpret_cast<const int4 *>(reinterpret_cast<const int *>(weight) + base + j0));
+        w[0] = (uint64_t)(int64_t)q.x; w[1] = (uint64_t)(int64_t)q.y;
+        w[2] = (uint64_t)(int64_t)q.z; w[3] = (uint64_t)(int64_t)q.w;
       } else if constexpr (WT == 2) {
-        const longlong2 *wp = reinterpret_cast<const longlong2 *>(reinterpret_cast<const long long *>(weight) + base + j);
+        const longlong2 *wp = reinterpret_cast<const longlong2 *>(reinterpret_cast<const long long *>(weight) + base + j0);
         const longlong2 q0 = __ldcs(wp), q1 = __ldcs(wp + 1);
-        w0 = (VT)q0.x; w1 = (VT)q0.y; w2 = (VT)q1.x; w3 = (VT)q1.y;
+        w[0] = (uint64_t)q0.x; w[1] = (uint64_t)q0.y; w[2] = (uint64_t)q1.x; w[3] = (uint64_t)q1.y;
       }
-      *reinterpret_cast<uint4 *>(&S.raw[j]) = sv;
-      lc_load1<WT, VT>(S, j + 0, sv.x, w0, t, base, n, bad, links);
-      lc_load1<WT, VT>(S, j + 1, sv.y, w1, t, base, n, bad, links);
-      lc_load1<WT, VT>(S, j + 2, sv.z, w2, t, base, n, bad, links);
-      lc_load1<WT, VT>(S, j + 3, sv.w, w3, t, base, n, bad, links);
     } else {
-      for (uint32_t q = j; q < min(len, j + 4); ++q) {
-        const uint32_t sq = __ldcs(succ + base + q);
-        S.raw[q] = sq;
-        lc_load1<WT, VT>(S, q, sq, (VT)lc_weight<WT>(weight, base + q), t, base, n, bad, links);
+#pragma unroll
+      for (uint32_t e = 0; e < 4; ++e) {
+        const uint32_t j = j0 + e;
+        s[e] = j < len ? __ldcs(succ + base + j) : base + j;     // beyond the tile: a lone tail
+        if constexpr (WT != 0) w[e] = j < len ? lc_weight<WT>(weight, base + j) : 0u;
       }
     }
-  }
-  links = __reduce_add_sync(0xFFFFFFFFu, links);
-  if (lane == 0 && links) atomicAdd(&S.nlinks, links);
-  __syncthreads();
-  // the has-local-predecessor bitmap; marks are cleared as they are read
-  for (uint32_t j0 = 0; j0 < kTile; j0 += blockDim.x) {
-    const uint32_t j = j0 + threadIdx.x;
-    const bool has = j < len && S.sub[j] != kEnd16;
-    S.sub[j] = kEnd16;
-    const uint32_t word = __ballot_sync(0xFFFFFFFFu, has);
-    if (lane == 0) S.pred[j >> 5] = word;
-  }
-  __syncthreads();
-  // heads per tile; in dense tiles also the heads that are not multiples of ksub
-  if (threadIdx.x < 32) {
-    uint32_t hw[4], cnt = 0, extra = 0;
+    uint32_t tails = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint32_t w = threadIdx.x * 4 + q, lo = w * 32;
-      const uint32_t valid = lo >= len ? 0u : (len - lo >= 32 ? 0xFFFFFFFFu : ((1u << (len - lo)) - 1u));
-      hw[q] = ~S.pred[w] & valid;
-      cnt += __popc(hw[q]);
-      extra += __popc(hw[q] & ~mulbits);              // heads off the ksub grid
-    }
-    const uint32_t heads = __reduce_add_sync(0xFFFFFFFFu, cnt);
-    const uint32_t marked = len - heads;
-    if (marked < S.nlinks) bad |= kErrNotList;            // two links into one element
-    const bool dense = heads + (len + ksub - 1) / ksub <= kMaxSr;
-    if (dense) {
-      uint32_t incl = extra;
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if ((int)lane >= d) incl += v;
+    for (uint32_t e = 0; e < 4; ++e) {
+      const uint32_t j = j0 + e, i = base + j;
+      if (j < len && s[e] >= n) bad |= kErrRange;
+      const bool local = j < len && s[e] < n && s[e] != i && (s[e] >> kTileShift) == t;
+      p[r][e] = local ? s[e] - base : j;
+      const uint64_t dw = local ? w[e] : 0u;
+      x[r][e] = wide ? (T)dw : (T)(dw << 16) | (T)p[r][e];
+      if (local) {
+        const uint32_t y = s[e] - base, bit = 1u << (y & 31u);
+        if (atomicOr(&S.pred[y >> 5], bit) & bit) bad |= kErrNotList;   // a second local link into y
+      } else {
+        tails |= 1u << e;
       }
-      uint32_t pos = incl - extra;
+    }
+    if (tails) atomicOr(&S.tail[j0 >> 5], tails << (j0 & 31u));
+    lc_put<WT>(S, 0, j0, x[r], p[r], wide);
+  }
+  __syncthreads();
+  // pointer doubling until no pointer moves (a valid tile needs at most
+  // kTileShift rounds and one more to see it; a cycle never settles)
+  if (!wide) {
+    int b = 0;
+    for (int round = 0; round <= kTileShift; ++round) {
+      uint32_t diff = 0;          // low 16 bits: some pointer moved
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t bits = hw[q] & ~mulbits;
-        while (bits) {
-          const uint32_t b = __ffs(bits) - 1;
-          bits &= bits - 1u;
-          S.srl[pos++] = (uint16_t)((threadIdx.x * 4 + q) * 32 + b);
+      for (uint32_t r = 0; r < kLcRuns; ++r) {
+#pragma unroll
+        for (uint32_t e = 0; e < 4; ++e) {
+          const T v = S.pk[b][(uint32_t)x[r][e] & 0xFFFFu];
+          diff |= (uint32_t)v ^ (uint32_t)x[r][e];
+          x[r][e] = (x[r][e] & ~(T)0xFFFFu) + v;
         }
+        lc_put<WT>(S, b ^ 1, r * kLcRunStride + 4 * tid, x[r], p[r], false);
       }
-      if (lane == 31) S.nextra = incl;
+      b ^= 1;
+      if (!__syncthreads_or((diff & 0xFFFFu) != 0)) break;
     }
-    if (lane == 0) { S.nheads = heads; S.dense = dense; }
-  }
-  __syncthreads();
-  const bool dense = S.dense;
-  const uint32_t nmul = (len + ksub - 1) / ksub;
-  const uint32_t nsr = dense ? nmul + S.nextra : len;
-  // level 1
-  for (uint32_t p = threadIdx.x; p < nsr; p += blockDim.x) {
-    uint32_t j = p;
-    if (dense) j = p < nmul ? p * ksub : S.srl[p - nmul];
-    else if (!lc_head(S, j)) continue;
-    uint32_t x = j, steps = 0;
-    VT o = 0;
-    uint16_t nx = kEnd16, tail = kEnd16;
-    for (;;) {
-      const VT wx = S.off[x];
-      const uint16_t y = S.nxt[x];
-      S.sub[x] = (uint16_t)j;
-      S.off[x] = o;
-      if (y == kEnd16) { tail = (uint16_t)x; break; }
-      o += wx;
-      if (dense && (y & submask) == 0) { nx = y; break; }
-      x = y;
-      if (++steps > len) { bad |= kErrCycle; break; }
-    }
-    S.nxt[j] = nx;                    // per sub-ruler: the next one (kEnd16: done)
-    S.off[j] = o;                     // weight to it, or distance to the tail
-    S.sub[j] = tail;                  // the tail, known once nxt is kEnd16
-  }
-  __syncthreads();
-  // level 2: synchronous pointer doubling over the sub-rulers
-  if (dense) {
-    uint32_t rounds = 0;
-    while ((1u << rounds) < nsr) ++rounds;
-    for (uint32_t r = 0; r < rounds; ++r) {
-      uint16_t tn[2], tt[2];
-      VT tv[2];
+  } else if constexpr (WT == 2) {
+    // wide int64 weights: read every element's target, wait, write back
+    for (int round = 0; round <= kTileShift; ++round) {
+      uint32_t diff = 0;
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const uint32_t p = threadIdx.x + e * kLcThreads;
-        if (p < nsr) {
-          const uint32_t j = p < nmul ? p * ksub : S.srl[p - nmul];
-          const uint16_t a = S.nxt[j];
-          if (a != kEnd16) { tv[e] = S.off[j] + S.off[a]; tn[e] = S.nxt[a]; tt[e] = S.sub[a]; }
-          else { tv[e] = S.off[j]; tn[e] = kEnd16; tt[e] = S.sub[j]; }
+      for (uint32_t r = 0; r < kLcRuns; ++r)
+#pragma unroll
+        for (uint32_t e = 0; e < 4; ++e) {
+          const uint32_t q = S.w.p[p[r][e]];
+          diff |= q ^ p[r][e];
+          x[r][e] += S.w.d[p[r][e]];
+          p[r][e] = q;
         }
-      }
       __syncthreads();
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const uint32_t p = threadIdx.x + e * kLcThreads;
-        if (p < nsr) {
-          const uint32_t j = p < nmul ? p * ksub : S.srl[p - nmul];
-          S.nxt[j] = tn[e]; S.off[j] = tv[e]; S.sub[j] = tt[e];
-        }
-      }
-      __syncthreads();
+      for (uint32_t r = 0; r < kLcRuns; ++r) lc_put<WT>(S, 0, r * kLcRunStride + 4 * tid, x[r], p[r], true);
+      if (!__syncthreads_or(diff != 0)) break;
     }
   }
-  if (bad) record_error(err, bad);
-  return len;
-}
-
-// Distance from element j to its local tail, and the tail (kEnd16: j is on
-// or leads into a cycle inside the tile).  Valid after lc_tile_solve.
-template <class VT>
-__device__ __forceinline__ uint16_t lc_elem(const LcTile<VT> &S, uint32_t j, VT *dist) {
-  uint32_t sr = j;
-  VT ox = 0;
-  if (!lc_is_sr(S, j)) {
-    sr = S.sub[j];
-    if (sr == kEnd16) return kEnd16;
-    ox = S.off[j];
-  }
-  if (S.nxt[sr] != kEnd16) return kEnd16;          // its sub-ruler chain never ended
-  *dist = S.off[sr] - ox;
-  return S.sub[sr];
+  // unpack; a pointer that did not settle on a local tail marks a cycle
+#pragma unroll
+  for (uint32_t r = 0; r < kLcRuns; ++r)
+#pragma unroll
+    for (uint32_t e = 0; e < 4; ++e) {
+      if constexpr (WT == 0) {
+        d[r][e] = x[r][e] >> 16;
+        p[r][e] = x[r][e] & 0xFFFFu;
+      } else if (!wide) {
+        d[r][e] = (uint64_t)((int64_t)x[r][e] >> 16);        // signed: |d| < 2^47
+        p[r][e] = (uint32_t)x[r][e] & 0xFFFFu;
+      } else {
+        d[r][e] = x[r][e];
+      }
+      if (!((S.tail[p[r][e] >> 5] >> (p[r][e] & 31u)) & 1u)) p[r][e] = kEnd16;
+    }
 }
 }  // namespace
 
@@ -297,30 +284,56 @@ k_lc_scan(const uint32_t *__restrict__ tcnt, uint32_t ntiles, uint32_t *__restri
 // Solve pass: per tile, every element's distance to its local tail goes to
 // rank[] (in the rank type) and its tail (local index) to tail16[]; the
 // local-head bitmap, the head counts before each word of the tile and the
-// heads per tile go to hb, wpre and tcnt.
-template <int WT, class VT, class RT>
-__global__ void __launch_bounds__(kLcThreads, WT == 0 ? 4 : 3)
+// heads per tile go to hb, wpre and tcnt.  vec: bit 0 = succ and weight
+// 16-byte aligned, bit 1 = rank 16-byte and tail16 8-byte aligned.
+template <int WT, class RT>
+__global__ void __launch_bounds__(kLcThreads, WT == 2 ? 2 : 3)
 k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, uint32_t n,
            RT *__restrict__ rank, uint16_t *__restrict__ tail16, uint32_t *__restrict__ hb,
-           uint16_t *__restrict__ wpre, uint32_t *__restrict__ tcnt, uint32_t *__restrict__ err, int vec,
-           uint32_t ksub) {
+           uint16_t *__restrict__ wpre, uint32_t *__restrict__ tcnt, uint32_t *__restrict__ err, int vec) {
   extern __shared__ __align__(16) unsigned char lc_smem[];
-  LcTile<VT> &S = *reinterpret_cast<LcTile<VT> *>(lc_smem);
+  LcTile<WT> &S = *reinterpret_cast<LcTile<WT> *>(lc_smem);
   const uint32_t ntiles = (n + kTile - 1) >> kTileShift;
-  for (uint32_t j = threadIdx.x; j < kTile; j += blockDim.x) S.sub[j] = kEnd16;
+  for (uint32_t w = threadIdx.x; w < kTileWords; w += blockDim.x) { S.pred[w] = 0; S.tail[w] = 0; }
   __syncthreads();
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint32_t len = lc_tile_solve<WT, VT>(S, t, succ, weight, n, err, vec != 0, ksub);
     const uint32_t base = t << kTileShift;
+    const uint32_t len = min(kTile, n - base);
+    uint32_t p[kLcRuns][4];
+    uint64_t d[kLcRuns][4];
+    uint32_t bad = 0;
+    lc_tile_solve<WT>(S, t, len, succ, weight, n, (vec & 1) != 0, p, d, bad);
     bool cyc = false;
-    for (uint32_t j = threadIdx.x; j < len; j += blockDim.x) {
-      VT d = 0;
-      const uint16_t tj = lc_elem(S, j, &d);
-      if (tj == kEnd16) cyc = true;              // on or into a cycle inside the tile
-      __stcs(rank + base + j, tj == j ? (RT)0 : (RT)d);
-      __stcs(tail16 + base + j, tj);
+#pragma unroll
+    for (uint32_t r = 0; r < kLcRuns; ++r) {
+      const uint32_t j0 = r * kLcRunStride + 4 * threadIdx.x;
+      if (j0 >= len) continue;
+      RT o[4];
+#pragma unroll
+      for (uint32_t e = 0; e < 4; ++e) {
+        if (j0 + e < len && p[r][e] == kEnd16) cyc = true;
+        o[e] = p[r][e] == kEnd16 ? (RT)0 : (RT)d[r][e];
+      }
+      if ((vec & 2) && j0 + 4 <= len) {
+        if constexpr (sizeof(RT) == 4) {
+          __stcs(reinterpret_cast<uint4 *>(rank + base + j0), make_uint4(o[0], o[1], o[2], o[3]));
+        } else {
+          __stcs(reinterpret_cast<ulonglong2 *>(rank + base + j0), make_ulonglong2(o[0], o[1]));
+          __stcs(reinterpret_cast<ulonglong2 *>(rank + base + j0 + 2), make_ulonglong2(o[2], o[3]));
+        }
+        __stcs(reinterpret_cast<uint2 *>(tail16 + base + j0),
+               make_uint2(p[r][0] | p[r][1] << 16, p[r][2] | p[r][3] << 16));
+      } else {
+#pragma unroll
+        for (uint32_t e = 0; e < 4; ++e) {
+          if (j0 + e >= len) break;
+          __stcs(rank + base + j0 + e, o[e]);
+          __stcs(tail16 + base + j0 + e, (uint16_t)p[r][e]);
+        }
+      }
     }
-    if (cyc) record_error(err, kErrCycle);
+    if (cyc) bad |= kErrCycle;
+    if (bad) record_error(err, bad);
     if (threadIdx.x < 32) {
       // 4 words per lane; exclusive prefix of the head counts over the tile
       uint32_t h[4], c = 0;
@@ -333,9 +346,9 @@ k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, u
         c += __popc(h[q]);
       }
       uint32_t incl = c;
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if ((int)threadIdx.x >= d) incl += v;
+      for (int dd = 1; dd < 32; dd <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, dd);
+        if ((int)threadIdx.x >= dd) incl += v;
       }
       uint32_t run = incl - c;
 #pragma unroll
@@ -348,7 +361,7 @@ k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, u
       if (threadIdx.x == 31) tcnt[t] = incl;
     }
     __syncthreads();
-    for (uint32_t j = threadIdx.x; j < kTile; j += blockDim.x) S.sub[j] = kEnd16;   // for the next tile
+    for (uint32_t w = threadIdx.x; w < kTileWords; w += blockDim.x) { S.pred[w] = 0; S.tail[w] = 0; }
     __syncthreads();
   }
 }
@@ -457,9 +470,8 @@ k_lc_fix(uint32_t n, RT *__restrict__ rank, const uint16_t *__restrict__ tail16,
   }
 }
 
-size_t lc_smem_bytes(bool weighted, int rank_bytes) {
-  (void)rank_bytes;
-  return weighted ? sizeof(LcTile<uint64_t>) : sizeof(LcTile<uint32_t>);
+static size_t lc_smem_bytes(int wtype) {
+  return wtype == 0 ? sizeof(LcTile<0>) : (wtype == 1 ? sizeof(LcTile<1>) : sizeof(LcTile<2>));
 }
 
 uint32_t lc_tiles(uint64_t n) { return (uint32_t)((n + kTile - 1) >> kTileShift); }
@@ -469,31 +481,31 @@ cudaError_t lc_setup() {
   cudaError_t e = cudaSuccess;
 #define LC_ATTR(K, BYTES) \
   if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BYTES))
-  LC_ATTR((k_lc_solve<0, uint32_t, uint32_t>), sizeof(LcTile<uint32_t>));
-  LC_ATTR((k_lc_solve<0, uint32_t, unsigned long long>), sizeof(LcTile<uint32_t>));
-  LC_ATTR((k_lc_solve<1, uint64_t, uint32_t>), sizeof(LcTile<uint64_t>));
-  LC_ATTR((k_lc_solve<1, uint64_t, unsigned long long>), sizeof(LcTile<uint64_t>));
-  LC_ATTR((k_lc_solve<2, uint64_t, uint32_t>), sizeof(LcTile<uint64_t>));
-  LC_ATTR((k_lc_solve<2, uint64_t, unsigned long long>), sizeof(LcTile<uint64_t>));
+  LC_ATTR((k_lc_solve<0, uint32_t>), sizeof(LcTile<0>));
+  LC_ATTR((k_lc_solve<0, unsigned long long>), sizeof(LcTile<0>));
+  LC_ATTR((k_lc_solve<1, uint32_t>), sizeof(LcTile<1>));
+  LC_ATTR((k_lc_solve<1, unsigned long long>), sizeof(LcTile<1>));
+  LC_ATTR((k_lc_solve<2, uint32_t>), sizeof(LcTile<2>));
+  LC_ATTR((k_lc_solve<2, unsigned long long>), sizeof(LcTile<2>));
 #undef LC_ATTR
   return e;
 }
 
 cudaError_t launch_lc_solve(const uint32_t *succ, const void *weight, int wtype, uint32_t n, void *rank,
                             int rank_bytes, uint16_t *tail16, uint32_t *hb, uint16_t *wpre, uint32_t *tcnt,
-                            uint32_t *tpre, uint32_t *err, uint32_t ksub, cudaStream_t s) {
-  if (ksub < 2 || ksub > 32 || (ksub & (ksub - 1))) ksub = kSubDefault;
+                            uint32_t *tpre, uint32_t *err, cudaStream_t s) {
   const uint32_t nt = lc_tiles(n);
-  const size_t sm = lc_smem_bytes(wtype != 0, rank_bytes);
-  const int per_sm = wtype ? 3 : 4;
+  const size_t sm = lc_smem_bytes(wtype);
+  const int per_sm = wtype == 2 ? 2 : 3;
   const int grid = (int)std::min<uint32_t>(nt, (uint32_t)device_sm_count() * per_sm);
-  const int vec = ((uintptr_t)succ & 15u) == 0 && ((uintptr_t)weight & 15u) == 0;
-#define LC_SOLVE(W, V, R)                                                                          \
-  k_lc_solve<W, V, R><<<grid, kLcThreads, sm, s>>>(succ, weight, n, reinterpret_cast<R *>(rank), tail16, \
-                                                   hb, wpre, tcnt, err, vec, ksub)
-  if (wtype == 0) { if (rank_bytes == 4) LC_SOLVE(0, uint32_t, uint32_t); else LC_SOLVE(0, uint32_t, unsigned long long); }
-  else if (wtype == 1) { if (rank_bytes == 4) LC_SOLVE(1, uint64_t, uint32_t); else LC_SOLVE(1, uint64_t, unsigned long long); }
-  else { if (rank_bytes == 4) LC_SOLVE(2, uint64_t, uint32_t); else LC_SOLVE(2, uint64_t, unsigned long long); }
+  const int vec = (((uintptr_t)succ & 15u) == 0 && ((uintptr_t)weight & 15u) == 0 ? 1 : 0) |
+                  (((uintptr_t)rank & 15u) == 0 && ((uintptr_t)tail16 & 7u) == 0 ? 2 : 0);
+#define LC_SOLVE(W, R)                                                                             \
+  k_lc_solve<W, R><<<grid, kLcThreads, sm, s>>>(succ, weight, n, reinterpret_cast<R *>(rank), tail16, \
+                                                hb, wpre, tcnt, err, vec)
+  if (wtype == 0) { if (rank_bytes == 4) LC_SOLVE(0, uint32_t); else LC_SOLVE(0, unsigned long long); }
+  else if (wtype == 1) { if (rank_bytes == 4) LC_SOLVE(1, uint32_t); else LC_SOLVE(1, unsigned long long); }
+  else { if (rank_bytes == 4) LC_SOLVE(2, uint32_t); else LC_SOLVE(2, unsigned long long); }
 #undef LC_SOLVE
   k_lc_scan<<<1, 1024, 0, s>>>(tcnt, nt, tpre);
   count_launch(2);

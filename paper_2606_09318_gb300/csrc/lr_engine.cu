@@ -567,7 +567,7 @@ static lr_status run_contracted(const Inputs &in, const lr_tuning *tuning, Ctx *
   uint32_t *tpre = (uint32_t *)(b + off_tpre);
   uint16_t *tail16 = (uint16_t *)(b + off_tail);
   LR_TRY(launch_lc_solve(in.succ, in.weight, in.wtype, n, in.rank, in.rank_bytes, tail16, hb, wpre, tcnt,
-                         tpre, err, env_u32(getenv("LR_TUNING"), "lcsub", 0), s));
+                         tpre, err, s));
   LR_TRY(cudaMemcpyAsync(c->host_words + 1, tpre + nt, 4, cudaMemcpyDeviceToHost, s));
   LR_TRY(cudaStreamSynchronize(s));
   const uint64_t m = c->host_words[1];

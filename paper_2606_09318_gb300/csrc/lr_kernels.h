@@ -151,7 +151,7 @@ cudaError_t lc_setup();
 // tail16, the local-head bitmap and counts), then the tile prefixes.
 cudaError_t launch_lc_solve(const uint32_t *succ, const void *weight, int wtype, uint32_t n, void *rank,
                             int rank_bytes, uint16_t *tail16, uint32_t *hb, uint16_t *wpre, uint32_t *tcnt,
-                            uint32_t *tpre, uint32_t *err, uint32_t ksub, cudaStream_t s);
+                            uint32_t *tpre, uint32_t *err, cudaStream_t s);
 // The contracted list: one node per local head.
 cudaError_t launch_lc_nodes(const uint32_t *succ, const void *weight, int wtype, uint32_t n, const void *rank,
                             int rank_bytes, const uint16_t *tail16, const uint32_t *hb, const uint16_t *wpre,

@@ -75,6 +75,45 @@ def test_weighted(wkind, rdt):
         np.testing.assert_array_equal(rank(succ, w, tdt, tuning=t), want)
 
 
+def test_weighted_extreme_int32():
+    # int32 weights over their whole range: in-tile distances reach about
+    # 2^43 in magnitude, the largest the packed in-tile form must carry
+    n = 5 * TILE + 3
+    for kind in ("locality", "identity"):
+        succ = gen.list_of_order_kind(kind, n, 509)
+        w = np.random.default_rng(510).integers(-(1 << 31), 1 << 31, size=n, dtype=np.int64).astype(np.int32)
+        w[:TILE] = np.int32(-(1 << 31))                   # one tile of the most negative weight
+        want = oracle.rank(succ, w, np.int64)
+        for t in (None, ON):
+            np.testing.assert_array_equal(rank(succ, w, torch.int64, tuning=t), want)
+
+
+def test_weighted_int64_mixed_tiles():
+    # int64 weights: tiles whose weights all fit in int32 take the packed
+    # in-tile form, the tile holding a wider weight the separate one
+    n = 6 * TILE + 9
+    for kind in ("locality", "identity"):
+        succ = gen.list_of_order_kind(kind, n, 511)
+        w = gen.weights_i64(n, 512)
+        w[TILE + 7] = 1 << 50
+        w[3 * TILE + 100] = -(1 << 62)
+        want = oracle.rank(succ, w, np.int64)
+        for t in (None, ON):
+            np.testing.assert_array_equal(rank(succ, w, torch.int64, tuning=t), want)
+    # a cycle inside a tile with a wide weight is still found
+    succ = gen.identity_list(n).astype(np.int64)
+    succ[999] = 1101
+    succ[1100] = 1000
+    w = gen.weights_i64(n, 513)
+    w[1050] = 1 << 45
+    try:
+        lr.rank(dev(succ.astype(np.uint32)), dev(w), tuning=ON)
+        got = "LR_OK"
+    except lr.LRError as e:
+        got = e.name
+    assert got == "LR_ERR_CYCLE"
+
+
 def test_euler_tour_forced():
     parent = gen.random_recursive_tree(1 << 16, 508)
     succ, w = gen.euler_tour(parent)
@@ -99,8 +138,8 @@ def test_errors_with_contraction():
     cyc[200] = 150                         # a cycle inside tile 0 (150..200), rest is a list
     assert oracle.rank_status(cyc.astype(np.uint32))[0] != oracle.OK
     assert _status(cyc.astype(np.uint32), tuning=ON) != "LR_OK"
-    for a, b in ((1000, 1100), (1025, 1055)):   # headless cycles inside tile 0, with and
-        hc = succ.copy()                      # without sub-ruler ids (multiples of 32) in them
+    for a, b in ((1000, 1100), (1025, 1055), (2000, 2001), (3000, 3063)):   # headless cycles
+        hc = succ.copy()                      # inside tile 0, of lengths 101, 31, 2 and 64
         hc[a - 1] = b + 1                     # the list skips a..b
         hc[b] = a                             # which close on themselves
         assert oracle.rank_status(hc.astype(np.uint32))[0] == oracle.CYCLE
