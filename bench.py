@@ -422,8 +422,8 @@ def run_reference(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(1e3 * t / len(times), 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "single random-order list, unweighted, int32 ranks (oracle sample n=2^22)",
-                   "n": n},
+        "config": {"workload": "single random-order list, n=2^28, unweighted, int32 ranks",
+                   "n": 1 << 28, "sample_n": n, "parallelism": "single GPU"},
         "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
