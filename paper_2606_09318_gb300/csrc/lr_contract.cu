@@ -32,6 +32,7 @@
 // Whether to contract is decided by the caller from the prep pass's count
 // of links that stay inside their tile.
 #include <algorithm>
+#include <cstddef>
 #include <cuda_runtime.h>
 
 #include "lr_device.cuh"
@@ -71,36 +72,47 @@ __device__ __forceinline__ bool lc_is_head(uint32_t x, const uint32_t *hb) {
 // link-weight distance d to p; pointer doubling (p, d) <- (p[p], d + d[p])
 // from one buffer into the other reaches the local tail and the distance to
 // it in at most kTileShift rounds, because a local sublist has fewer than
-// kTile links.  p < 2^16, so one word holds d << 16 | p where d fits:
+// kTile links.  The low 16 bits of a word hold p and a settled bit (below),
+// so one word holds d << 16 | bits where d fits:
 // unweighted distances (below kTile) in 32 bits, distances over weights
 // that fit in int32 (below kTile * 2^31 in magnitude) in 64 bits.  Adding
 // two packed words whose first has its p bits cleared adds the distances
 // and takes the second's pointer.  A tile with a wider int64 weight keeps
 // the distances in a separate array, single-buffered (two barriers a round).
+// Predecessor marks are plain byte stores (one per local link), turned into
+// the has-local-predecessor bitmap afterwards; fewer marked elements than
+// local links means an element with two local predecessors.
+struct LcMarks {
+  uint8_t mark[kTile];       // 1: the element has a local predecessor
+  uint32_t pred[kTileWords]; // has-local-predecessor bitmap
+  uint32_t tail[kTileWords]; // local-tail bitmap (wide int64 tiles only)
+  uint32_t nlinks, nmarked;  // local links; marked elements
+};
+// The word arrays come first: they are read and written as 16-byte vectors.
 template <int WT>
 struct LcTile {
-  uint32_t pk[2][kTile];     // d << 16 | p, double-buffered
-  uint32_t pred[kTileWords]; // has-local-predecessor bitmap
-  uint32_t tail[kTileWords]; // local-tail bitmap: no local successor
+  alignas(16) uint32_t pk[2][kTile];   // d << 16 | low bits, double-buffered
+  LcMarks m;
 };
 template <>
 struct LcTile<1> {
-  uint64_t pk[2][kTile];
-  uint32_t pred[kTileWords];
-  uint32_t tail[kTileWords];
+  alignas(16) uint64_t pk[2][kTile];
+  LcMarks m;
 };
 template <>
 struct LcTile<2> {
-  union {
+  union alignas(16) {
     uint64_t pk[2][kTile];   // every weight of the tile fits in int32
     struct {
       uint64_t d[kTile];     // otherwise: distances
       uint16_t p[kTile];     // and pointers
     } w;
   };
-  uint32_t pred[kTileWords];
-  uint32_t tail[kTileWords];
+  LcMarks m;
 };
+static_assert(offsetof(LcTile<0>, m) % 16 == 0 && offsetof(LcTile<1>, m) % 16 == 0 &&
+                  offsetof(LcTile<2>, m) % 16 == 0 && offsetof(LcMarks, mark) == 0,
+              "vector accesses to the tile arrays and the marks stay aligned");
 
 // Per-element state a thread keeps in registers: the packed word (WT 0
 // and 1), or the distance with the pointer beside it (WT 2).
@@ -112,6 +124,11 @@ template <> struct LcState<0> { using T = uint32_t; };
 constexpr uint32_t kLcRuns = kTile / (4 * kLcThreads);
 static_assert(kLcRuns * 4 * kLcThreads == kTile, "a tile is kLcRuns runs of four per thread");
 constexpr uint32_t kLcRunStride = kTile / kLcRuns;
+// Low half of a packed word: the pointer, and a bit set once the pointer is
+// a local tail (the pointer's own word has it then).
+constexpr uint32_t kLcPtrMask = kTile - 1u;
+constexpr uint32_t kLcSettled = 0x8000u;
+static_assert(kTile <= kLcSettled, "pointers stay below the settled bit");
 
 // Store a run of four elements: packed into buffer b, or (wide) the
 // distances and pointers of the single-buffered form.
@@ -147,6 +164,7 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
   const uint32_t base = t << kTileShift;
   const uint32_t tid = threadIdx.x;
   T x[kLcRuns][4];
+  uint32_t links = 0;
   // int64 weights: does any weight of the tile leave the int32 range?
   bool wide = false;
   if constexpr (WT == 2) {
@@ -198,36 +216,58 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
       const bool local = j < len && s[e] < n && s[e] != i && (s[e] >> kTileShift) == t;
       p[r][e] = local ? s[e] - base : j;
       const uint64_t dw = local ? w[e] : 0u;
-      x[r][e] = wide ? (T)dw : (T)(dw << 16) | (T)p[r][e];
+      x[r][e] = wide ? (T)dw : (T)(dw << 16) | (T)p[r][e] | (local ? (T)0 : (T)kLcSettled);
       if (local) {
-        const uint32_t y = s[e] - base, bit = 1u << (y & 31u);
-        if (atomicOr(&S.pred[y >> 5], bit) & bit) bad |= kErrNotList;   // a second local link into y
+        S.m.mark[s[e] - base] = 1;
+        ++links;
       } else {
         tails |= 1u << e;
       }
     }
-    if (tails) atomicOr(&S.tail[j0 >> 5], tails << (j0 & 31u));
+    if (wide && tails) atomicOr(&S.m.tail[j0 >> 5], tails << (j0 & 31u));
     lc_put<WT>(S, 0, j0, x[r], p[r], wide);
   }
+  links = __reduce_add_sync(0xFFFFFFFFu, links);
+  if ((tid & 31u) == 0 && links) atomicAdd(&S.m.nlinks, links);
   __syncthreads();
+  // marks -> bitmap: eight marks per thread, four threads per word; the
+  // marks are cleared for the next tile as they are read
+  {
+    const uint2 mk = *reinterpret_cast<const uint2 *>(&S.m.mark[8 * tid]);
+    *reinterpret_cast<uint2 *>(&S.m.mark[8 * tid]) = make_uint2(0u, 0u);
+    // bytes are 0 or 1: the product gathers four of them into one nibble
+    uint32_t v = (((mk.x * 0x01020408u) >> 24) | (((mk.y * 0x01020408u) >> 24) << 4)) << (8 * (tid & 3u));
+    v |= __shfl_xor_sync(0xFFFFFFFFu, v, 1);
+    v |= __shfl_xor_sync(0xFFFFFFFFu, v, 2);
+    uint32_t c = (tid & 3u) == 0 ? (uint32_t)__popc(v) : 0u;
+    if ((tid & 3u) == 0) S.m.pred[tid >> 2] = v;
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+    if ((tid & 31u) == 0 && c) atomicAdd(&S.m.nmarked, c);
+  }
   // pointer doubling until no pointer moves (a valid tile needs at most
   // kTileShift rounds and one more to see it; a cycle never settles)
   if (!wide) {
+    // A word whose pointer has reached a local tail is final: it is not
+    // gathered again, and the rounds end when every word is final.  The
+    // settled bit travels with the pointer (a tail's own word has it), so
+    // after a gather it says whether the new pointer is a tail.
     int b = 0;
     for (int round = 0; round <= kTileShift; ++round) {
-      uint32_t diff = 0;          // low 16 bits: some pointer moved
+      uint32_t all = kLcSettled;
 #pragma unroll
       for (uint32_t r = 0; r < kLcRuns; ++r) {
 #pragma unroll
         for (uint32_t e = 0; e < 4; ++e) {
-          const T v = S.pk[b][(uint32_t)x[r][e] & 0xFFFFu];
-          diff |= (uint32_t)v ^ (uint32_t)x[r][e];
-          x[r][e] = (x[r][e] & ~(T)0xFFFFu) + v;
+          if (!((uint32_t)x[r][e] & kLcSettled)) {
+            const T v = S.pk[b][(uint32_t)x[r][e] & kLcPtrMask];
+            x[r][e] = (x[r][e] & ~(T)0xFFFFu) + v;
+          }
+          all &= (uint32_t)x[r][e];
         }
         lc_put<WT>(S, b ^ 1, r * kLcRunStride + 4 * tid, x[r], p[r], false);
       }
       b ^= 1;
-      if (!__syncthreads_or((diff & 0xFFFFu) != 0)) break;
+      if (__syncthreads_and(all & kLcSettled)) break;
     }
   } else if constexpr (WT == 2) {
     // wide int64 weights: read every element's target, wait, write back
@@ -249,20 +289,26 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
     }
   }
   // unpack; a pointer that did not settle on a local tail marks a cycle
+  // (also one whose length is a power of two: it settles on itself, which
+  // is not a tail)
 #pragma unroll
   for (uint32_t r = 0; r < kLcRuns; ++r)
 #pragma unroll
     for (uint32_t e = 0; e < 4; ++e) {
+      bool settled;
       if constexpr (WT == 0) {
         d[r][e] = x[r][e] >> 16;
-        p[r][e] = x[r][e] & 0xFFFFu;
+        p[r][e] = x[r][e] & kLcPtrMask;
+        settled = (x[r][e] & kLcSettled) != 0;
       } else if (!wide) {
         d[r][e] = (uint64_t)((int64_t)x[r][e] >> 16);        // signed: |d| < 2^47
-        p[r][e] = (uint32_t)x[r][e] & 0xFFFFu;
+        p[r][e] = (uint32_t)x[r][e] & kLcPtrMask;
+        settled = ((uint32_t)x[r][e] & kLcSettled) != 0;
       } else {
         d[r][e] = x[r][e];
+        settled = (S.m.tail[p[r][e] >> 5] >> (p[r][e] & 31u)) & 1u;
       }
-      if (!((S.tail[p[r][e] >> 5] >> (p[r][e] & 31u)) & 1u)) p[r][e] = kEnd16;
+      if (!settled) p[r][e] = kEnd16;
     }
 }
 }  // namespace
@@ -294,7 +340,9 @@ k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, u
   extern __shared__ __align__(16) unsigned char lc_smem[];
   LcTile<WT> &S = *reinterpret_cast<LcTile<WT> *>(lc_smem);
   const uint32_t ntiles = (n + kTile - 1) >> kTileShift;
-  for (uint32_t w = threadIdx.x; w < kTileWords; w += blockDim.x) { S.pred[w] = 0; S.tail[w] = 0; }
+  for (uint32_t j = threadIdx.x; j < kTile / 4; j += blockDim.x) reinterpret_cast<uint32_t *>(S.m.mark)[j] = 0;
+  for (uint32_t w = threadIdx.x; w < kTileWords; w += blockDim.x) S.m.tail[w] = 0;
+  if (threadIdx.x == 0) { S.m.nlinks = 0; S.m.nmarked = 0; }
   __syncthreads();
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint32_t base = t << kTileShift;
@@ -333,6 +381,7 @@ k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, u
       }
     }
     if (cyc) bad |= kErrCycle;
+    if (threadIdx.x == 0 && S.m.nmarked < S.m.nlinks) bad |= kErrNotList;   // two local links into one element
     if (bad) record_error(err, bad);
     if (threadIdx.x < 32) {
       // 4 words per lane; exclusive prefix of the head counts over the tile
@@ -342,7 +391,7 @@ k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, u
         const uint32_t w = threadIdx.x * 4 + q;
         const uint32_t lo = w * 32;
         const uint32_t valid = lo >= len ? 0u : (len - lo >= 32 ? 0xFFFFFFFFu : ((1u << (len - lo)) - 1u));
-        h[q] = ~S.pred[w] & valid;
+        h[q] = ~S.m.pred[w] & valid;
         c += __popc(h[q]);
       }
       uint32_t incl = c;
@@ -361,7 +410,9 @@ k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, u
       if (threadIdx.x == 31) tcnt[t] = incl;
     }
     __syncthreads();
-    for (uint32_t w = threadIdx.x; w < kTileWords; w += blockDim.x) { S.pred[w] = 0; S.tail[w] = 0; }
+    if constexpr (WT == 2)
+      for (uint32_t w = threadIdx.x; w < kTileWords; w += blockDim.x) S.m.tail[w] = 0;
+    if (threadIdx.x == 0) { S.m.nlinks = 0; S.m.nmarked = 0; }
     __syncthreads();
   }
 }
