@@ -321,3 +321,40 @@ def test_host_async_two_streams():
     torch.cuda.synchronize()
     assert lr.device_status(streams[0]) == 0
     np.testing.assert_array_equal(out64.numpy(), oracle.rank(succ, w, np.int64))
+
+
+def _view(a, off):
+    """A device copy of `a` that starts `off` elements into its allocation, so
+    that 16-byte vector accesses cannot be used on it."""
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint32:
+        a = a.view(np.int32)
+    buf = torch.zeros(a.size + off + 3, dtype=torch.from_numpy(a[:1]).dtype, device="cuda")
+    v = buf[off:off + a.size]
+    v.copy_(torch.from_numpy(a))
+    return v
+
+
+@pytest.mark.parametrize("kind", ["random", "locality"])
+@pytest.mark.parametrize("wkind", [None, "i32", "i64"])
+def test_misaligned_buffers(kind, wkind):
+    """Successors, weights and ranks one or three elements past an aligned
+    start: every kernel that reads or writes them in 16-byte vectors takes its
+    scalar form, with the same result, whichever level-0 form or contraction
+    runs."""
+    n = 3 * 4096 * 8 + 13
+    succ = gen.list_of_order_kind(kind, n, 60)
+    w = None if wkind is None else (gen.weights_i32(n, 61) if wkind == "i32" else gen.weights_i64(n, 62))
+    rdt = np.int32 if w is None else np.int64
+    want = oracle.rank(succ, w, rdt)
+    tunings = [None, lr.Tuning(contract=lr.CONTRACT_ON), lr.Tuning(contract=lr.CONTRACT_OFF)]
+    if w is None:
+        tunings.append(lr.Tuning(chase0=lr.CHASE0_LOG))
+    for off in (1, 3):
+        ds = _view(succ, off)
+        dw = None if w is None else _view(w, off)
+        for t in tunings:
+            out = torch.full((n + off + 2,), -9, dtype=torch.int32 if rdt == np.int32 else torch.int64,
+                             device="cuda")[off:off + n]
+            lr.rank(ds, dw, out=out, tuning=t)
+            np.testing.assert_array_equal(host(out), want)
