@@ -676,6 +676,12 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   // Single instance, no validation: heads from the streaming sums (one list)
   // with the bitmap as the fallback, instead of atomics for every element.
   const bool sums0 = !log0 && !ptrs && in.offsets == nullptr && !in.validate && in.n > u.cutoff;
+  // A batch with its list bound given: per-instance sums (kept at the start
+  // of the bitmap's memory, which must hold 16 bytes per instance) give one
+  // head per instance, with the bitmap as the fallback.
+  const bool sums0b = !log0 && !ptrs && in.offsets != nullptr && !in.validate && in.max_lists > 0 &&
+                      !extras && !spawn0 && in.n > u.cutoff && in.k > 0 &&
+                      (uint64_t)in.k * 16 <= 4 * ((in.n + 31) / 32);
   Profiler prof;
   if (!in.ctx) prof.begin(s, (int64_t)in.n);
   unsigned long long *acc = (unsigned long long *)(fixed + p.off_acc);
@@ -686,6 +692,9 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   else if (ptrs)
     LR_TRY(launch_prep0_ptrs(in.sptr, in.wptr, in.wtype, (uint32_t)in.n, work0, bitmap, err,
                              in.validate, in.offsets, in.k, s));
+  else if (sums0b)
+    LR_TRY(launch_prep0_sums(in.succ, in.weight, in.wtype, (uint32_t)in.n, work0, err, in.offsets, in.k,
+                             reinterpret_cast<unsigned long long *>(bitmap), s));
   else
     LR_TRY(launch_prep0(in.succ, in.weight, in.wtype, (uint32_t)in.n, work0, bitmap, err,
                         in.validate, in.offsets, in.k, sums0 ? acc : nullptr, count_local ? acc + 2 : nullptr,
@@ -758,6 +767,9 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   }
   if (log0 || sums0)
     LR_TRY(launch_heads0_log(desc, acc, hA0, in.succ, (uint32_t)in.n, bitmap, err, in.validate, s));
+  else if (sums0b)
+    LR_TRY(launch_heads0_batch(desc, reinterpret_cast<unsigned long long *>(bitmap), in.offsets, in.k, hA0,
+                               p.hcap, work0, rec16_0, (uint32_t)in.n, bitmap, s));
 
   auto work_of = [&](int l) -> void * { return l == 0 ? work0 : (void *)(var + p.off_work[l]); };
   auto R_of = [&](int l) -> void * { return l == 0 ? in.rank : (void *)(var + p.off_R[l]); };

@@ -220,6 +220,216 @@ cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, ui
   return cudaGetLastError();
 }
 
+// Batched prep without per-element atomics.  Each instance j of a batch that
+// is one list has exactly one terminal, and its successors are every local id
+// but the head's, so head_j = n_j (n_j - 1) / 2 - sum of its non-terminal
+// successors (Section 1.1's findInit, by sums).  isums[2 j] counts instance
+// j's terminals and isums[2 j + 1] sums its local successors; a warp whose
+// 128 elements lie in one instance adds its sums with two atomics.  Records
+// as in k_prep0.  The loop runs warp-uniformly so that the warp can combine.
+template <int WT>
+__global__ void __launch_bounds__(256)
+k_prep0_sums(const uint32_t *__restrict__ succ, const void *__restrict__ weight, uint32_t n,
+             void *__restrict__ work, uint32_t *__restrict__ err, int vec, const int64_t *__restrict__ offsets,
+             int32_t k, unsigned long long *__restrict__ isums) {
+  const uint32_t ngroups = (uint32_t)(((uint64_t)n + 3u) / 4u);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t gw = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); gw < ngroups; gw += stride) {
+    const uint32_t g = gw + lane;
+    const bool active = g < ngroups;
+    const uint32_t i0 = g * 4u;
+    // instance of the warp's first element by binary search (lane 0), then
+    // each lane walks forward to its own
+    int32_t lo = 0;
+    if (lane == 0) {
+      int32_t hi = k;
+      while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if ((uint64_t)__ldg(offsets + mid) <= (uint64_t)gw * 4u) lo = mid; else hi = mid;
+      }
+    }
+    lo = __shfl_sync(0xFFFFFFFFu, lo, 0);
+    int32_t inst = -1;                 // the one instance of this lane's elements, or -1
+    unsigned long long sT = 0, sS = 0;
+    if (active) {
+      const uint32_t cnt = min(4u, n - i0);
+      uint32_t s[4];
+      uint64_t w[4];
+      if (vec && cnt == 4u) {
+        const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(succ + i0));
+        s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
+        if constexpr (WT == 1) {
+          const int4 q = __ldcs(reinterpret_cast<const int4 *>(reinterpret_cast<const int *>(weight) + i0));
+          w[0] = (uint64_t)(int64_t)q.x; w[1] = (uint64_t)(int64_t)q.y;
+          w[2] = (uint64_t)(int64_t)q.z; w[3] = (uint64_t)(int64_t)q.w;
+        } else if constexpr (WT == 2) {
+          const longlong2 *wp = reinterpret_cast<const longlong2 *>(reinterpret_cast<const long long *>(weight) + i0);
+          const longlong2 a = __ldcs(wp), b = __ldcs(wp + 1);
+          w[0] = (uint64_t)a.x; w[1] = (uint64_t)a.y; w[2] = (uint64_t)b.x; w[3] = (uint64_t)b.y;
+        } else {
+          w[0] = w[1] = w[2] = w[3] = 1u;
+        }
+      } else {
+        for (uint32_t j = 0; j < 4u; ++j) {
+          s[j] = j < cnt ? __ldcs(succ + i0 + j) : 0u;
+          w[j] = j < cnt ? load_weight<WT>(weight, i0 + j) : 0u;
+        }
+      }
+      uint64_t base = (uint64_t)__ldg(offsets + lo), end = (uint64_t)__ldg(offsets + lo + 1);
+      int32_t first = -2;
+      for (uint32_t j = 0; j < cnt; ++j) {
+        const uint32_t i = i0 + j;
+        while (i >= end && lo + 1 < k) { ++lo; base = end; end = (uint64_t)__ldg(offsets + lo + 1); }
+        const uint64_t gl = base + s[j];
+        bool term;
+        if (i < base || i >= end || (uint64_t)s[j] >= end - base || gl >= n) {
+          record_error(err, kErrRange);   // successor outside its instance (or a bad table)
+          s[j] = i;
+          term = true;
+        } else {
+          term = gl == i;
+          if (!term) sS += s[j];          // local id
+          s[j] = (uint32_t)gl;
+        }
+        if (term) { w[j] = 0u; sT += 1; }
+        if (first == -2) first = lo;
+        else if (first != lo) first = -1;  // the group straddles two instances
+      }
+      if (first >= 0) {
+        inst = first;
+      } else if (first == -1) {            // rare: add each element's share alone
+        sT = 0; sS = 0;
+        uint64_t b2 = (uint64_t)__ldg(offsets + lo);
+        int32_t l2 = lo;
+        for (int32_t jj = (int32_t)cnt - 1; jj >= 0; --jj) {
+          const uint32_t i = i0 + (uint32_t)jj;
+          while (i < b2 && l2 > 0) { --l2; b2 = (uint64_t)__ldg(offsets + l2); }
+          if (s[jj] == i) atomicAdd(isums + 2 * (size_t)l2, 1ull);
+          else atomicAdd(isums + 2 * (size_t)l2 + 1, (unsigned long long)(s[jj] - b2));
+        }
+      }
+      if constexpr (WT == 0) {
+        uint2 *out = reinterpret_cast<uint2 *>(work) + i0;
+        if (cnt == 4u) {
+          st_sector(out, s[0], kUnvisited, s[1], kUnvisited, s[2], kUnvisited, s[3], kUnvisited);
+        } else {
+          for (uint32_t j = 0; j < cnt; ++j) out[j] = make_uint2(s[j], kUnvisited);
+        }
+      } else {
+        uint4 *out = reinterpret_cast<uint4 *>(work) + i0;
+        if (cnt == 4u) {
+          st_sector(out, s[0], kUnvisited, (uint32_t)w[0], (uint32_t)(w[0] >> 32),
+                    s[1], kUnvisited, (uint32_t)w[1], (uint32_t)(w[1] >> 32));
+          st_sector(out + 2, s[2], kUnvisited, (uint32_t)w[2], (uint32_t)(w[2] >> 32),
+                    s[3], kUnvisited, (uint32_t)w[3], (uint32_t)(w[3] >> 32));
+        } else {
+          for (uint32_t j = 0; j < cnt; ++j)
+            __stcs(out + j, make_uint4(s[j], kUnvisited, (uint32_t)w[j], (uint32_t)(w[j] >> 32)));
+        }
+      }
+    }
+    // combine: one pair of atomics per warp when all its lanes share an instance
+    const int32_t inst0 = __shfl_sync(0xFFFFFFFFu, inst, 0);
+    if (__all_sync(0xFFFFFFFFu, inst == inst0 || (inst == -1 && sT == 0 && sS == 0)) && inst0 >= 0) {
+      for (int d = 16; d > 0; d >>= 1) {
+        sT += __shfl_down_sync(0xFFFFFFFFu, sT, d);
+        sS += __shfl_down_sync(0xFFFFFFFFu, sS, d);
+      }
+      if (lane == 0) {
+        if (sT) atomicAdd(isums + 2 * (size_t)inst0, sT);
+        if (sS) atomicAdd(isums + 2 * (size_t)inst0 + 1, sS);
+      }
+    } else if (inst >= 0) {
+      if (sT) atomicAdd(isums + 2 * (size_t)inst, sT);
+      if (sS) atomicAdd(isums + 2 * (size_t)inst + 1, sS);
+    }
+  }
+}
+
+cudaError_t launch_prep0_sums(const uint32_t *succ, const void *weight, int wtype, uint32_t n, void *work,
+                              uint32_t *err, const int64_t *offsets, int32_t k, unsigned long long *isums,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int block = 256;
+  const int grid = stream_grid(((uint64_t)n + 3) / 4, block);
+  int vec = ((uintptr_t)succ & 15u) == 0;
+  if (wtype != 0) vec = vec && ((uintptr_t)weight & 15u) == 0;
+  switch (wtype) {
+    case 0: k_prep0_sums<0><<<grid, block, 0, s>>>(succ, weight, n, work, err, vec, offsets, k, isums); break;
+    case 1: k_prep0_sums<1><<<grid, block, 0, s>>>(succ, weight, n, work, err, vec, offsets, k, isums); break;
+    default: k_prep0_sums<2><<<grid, block, 0, s>>>(succ, weight, n, work, err, vec, offsets, k, isums); break;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Level-0 heads of a batch from its per-instance sums (one CTA): the head of
+// every non-empty instance that has exactly one terminal, listed in instance
+// order.  If any non-empty instance has another number of terminals, or the
+// heads would not fit the list (capacity hcap), the has-predecessor bitmap
+// is used instead: the sums are cleared (they share its memory) and
+// k_bitmap0_recs fills it.
+__global__ void __launch_bounds__(1024)
+k_heads0_batch(LevelDesc *desc, unsigned long long *isums, const int64_t *__restrict__ offsets, int32_t k,
+               uint32_t *__restrict__ hlist0, uint32_t hcap) {
+  __shared__ uint64_t sm[33];
+  LevelDesc &d = desc[0];
+  int fallback = 0;
+  uint32_t total = 0;
+  for (int32_t j0 = 0; j0 < k; j0 += (int32_t)blockDim.x) {
+    const int32_t j = j0 + (int32_t)threadIdx.x;
+    uint32_t has = 0;
+    uint64_t head = 0;
+    if (j < k) {
+      const uint64_t b = (uint64_t)offsets[j], nj = (uint64_t)offsets[j + 1] - b;
+      if (nj > 0) {
+        const unsigned long long T = isums[2 * (size_t)j], S = isums[2 * (size_t)j + 1];
+        const unsigned long long h = nj * (nj - 1) / 2 - S;
+        if (T == 1 && h < nj) { has = 1; head = b + h; }
+        else fallback = 1;
+      }
+    }
+    uint64_t cnt;
+    const uint64_t pos = block_exclusive_scan((uint64_t)has, sm, &cnt);
+    if (has && total + pos < hcap) hlist0[total + pos] = (uint32_t)head;
+    total += (uint32_t)cnt;
+    __syncthreads();
+  }
+  if (total > hcap) fallback = 1;
+  fallback = __syncthreads_or(fallback);
+  if (fallback) {
+    // the sums occupy the start of the bitmap's memory: clear them
+    for (int32_t j = (int32_t)threadIdx.x; j < 2 * k; j += (int32_t)blockDim.x) isums[j] = 0ull;
+    if (threadIdx.x == 0) d.hsrc = kHeadsBitmap;
+  } else if (threadIdx.x == 0) {
+    d.h = total;
+    d.hsrc = kHeadsList;
+  }
+}
+
+// Has-predecessor bitmap from the level-0 records (global successors), only
+// when k_heads0_batch fell back to it.
+__global__ void __launch_bounds__(256)
+k_bitmap0_recs(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ recs, uint32_t words_per_rec,
+               uint32_t n, uint32_t *__restrict__ bitmap) {
+  if (desc[0].hsrc != kHeadsBitmap) return;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t s = __ldcs(recs + (size_t)i * words_per_rec);
+    if (s != i) atomicOr(bitmap + (s >> 5), 1u << (s & 31u));
+  }
+}
+
+cudaError_t launch_heads0_batch(LevelDesc *desc, unsigned long long *isums, const int64_t *offsets, int32_t k,
+                                uint32_t *hlist0, uint32_t hcap, const void *work, bool rec16, uint32_t n,
+                                uint32_t *bitmap, cudaStream_t s) {
+  k_heads0_batch<<<1, 1024, 0, s>>>(desc, isums, offsets, k, hlist0, hcap);
+  k_bitmap0_recs<<<stream_grid(n, 256), 256, 0, s>>>(desc, reinterpret_cast<const uint32_t *>(work),
+                                                      rec16 ? 4u : 2u, n, bitmap);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
 // Batched input given as one device pointer per instance (the serving path
 // ranks requests where they already live, without gathering them first).
 template <int WT>

@@ -41,6 +41,16 @@ cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, ui
                          const int64_t *offsets, int32_t k, unsigned long long *sums,
                          unsigned long long *local, cudaStream_t s);
 
+// Batched prep that sums each instance's terminals and local successors
+// (isums[2k], zeroed) instead of marking predecessors; then the level-0 head
+// list from those sums, or the bitmap from the records when some instance is
+// not one list.
+cudaError_t launch_prep0_sums(const uint32_t *succ, const void *weight, int wtype, uint32_t n, void *work,
+                              uint32_t *err, const int64_t *offsets, int32_t k, unsigned long long *isums,
+                              cudaStream_t s);
+cudaError_t launch_heads0_batch(LevelDesc *desc, unsigned long long *isums, const int64_t *offsets, int32_t k,
+                                uint32_t *hlist0, uint32_t hcap, const void *work, bool rec16, uint32_t n,
+                                uint32_t *bitmap, cudaStream_t s);
 cudaError_t launch_prep0_ptrs(const uint32_t *const *sptr, const void *const *wptr, int wtype,
                               uint32_t n, void *work, uint32_t *bitmap, uint32_t *err, int validate,
                               const int64_t *offsets, int32_t k, cudaStream_t s);

@@ -156,3 +156,80 @@ def test_server_budget_and_errors():
     with pytest.raises(lr.LRError):
         srv.wait(123456)
     srv.close()
+
+
+def _batch(lens, seed, forest_at=()):
+    """Instances of the given sizes back to back (local successor ids): random
+    single lists, or a forest of short lists for the indices in forest_at."""
+    offsets = np.zeros(len(lens) + 1, dtype=np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    succ = np.empty(int(offsets[-1]), dtype=np.uint32)
+    for j, m in enumerate(lens):
+        a, b = int(offsets[j]), int(offsets[j + 1])
+        if m == 0:
+            continue
+        if j in forest_at and m > 8:
+            succ[a:b] = gen.forest(m, seed + j, n_long=1, long_len=m // 4, mean_short=4)[0]
+        else:
+            succ[a:b] = gen.random_list(m, seed + j)
+    return offsets, succ
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_batch_heads_from_sums(weighted):
+    # With the list bound given, a batch takes each instance's head from the
+    # sums of its successors.  Ragged sizes put instance boundaries inside
+    # warps and groups of four; empty instances are skipped.
+    rng = np.random.default_rng(31)
+    lens = rng.integers(1, 500, size=64)
+    lens[[3, 10, 11]] = 0
+    lens[20] = 1
+    offsets, succ = _batch(lens, 900)
+    n = int(offsets[-1])
+    assert n > 12288
+    w = gen.weights_i64(n, 901) if weighted else None
+    want = oracle.rank_batch(offsets, succ, w, np.int64 if weighted else np.int32)
+    rdt = torch.int64 if weighted else torch.int32
+    for ml in (64, 200):
+        got = lr.rank_batch(dev(offsets), dev(succ), None if w is None else dev(w), rank_dtype=rdt,
+                            max_lists=ml).cpu().numpy()
+        np.testing.assert_array_equal(got, want)
+
+
+def test_batch_sums_fallbacks_and_errors():
+    rng = np.random.default_rng(32)
+    lens = rng.integers(100, 900, size=48)
+    # instances that are forests: the heads come from the bitmap instead
+    offsets, succ = _batch(lens, 950, forest_at=(5, 6, 40))
+    want = oracle.rank_batch(offsets, succ, None, np.int32)
+    lists = sum(int((succ[int(offsets[j]):int(offsets[j + 1])] ==
+                     np.arange(int(offsets[j + 1] - offsets[j]))).sum()) for j in range(len(lens)))
+    got = lr.rank_batch(dev(offsets), dev(succ), rank_dtype=torch.int32, max_lists=lists).cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    # more lists than the bound: a capacity error, as without the sums
+    with pytest.raises(lr.LRError) as e:
+        lr.rank_batch(dev(offsets), dev(succ), rank_dtype=torch.int32, max_lists=len(lens))
+    assert e.value.name == "LR_ERR_CAPACITY"
+    # a single-list batch with one bad instance
+    offsets, succ = _batch(lens, 960)
+    bad = succ.copy()
+    a = int(offsets[7])
+    bad[a + 3] = int(offsets[8] - offsets[7]) + 5            # out of its instance
+    with pytest.raises(lr.LRError) as e:
+        lr.rank_batch(dev(offsets), dev(bad), rank_dtype=torch.int32, max_lists=len(lens))
+    assert e.value.name == "LR_ERR_OUT_OF_RANGE"
+    cyc = succ.copy()                                        # a list plus a cycle, one terminal
+    m = int(offsets[9] - offsets[8])
+    order = np.asarray(gen.random_order(m, 961), dtype=np.int64)
+    loc = np.empty(m, dtype=np.uint32)
+    loc[order[:-1]] = order[1:]
+    loc[order[-1]] = order[-1]
+    loc[order[m // 2 - 1]] = order[m - 1]                    # the list skips the middle
+    loc[order[m - 2]] = order[m // 2]                        # which closes on itself
+    cyc[int(offsets[8]):int(offsets[9])] = loc
+    assert oracle.rank_batch_status(offsets, cyc, None, np.int32)[0] != oracle.OK
+    with pytest.raises(lr.LRError):
+        lr.rank_batch(dev(offsets), dev(cyc), rank_dtype=torch.int32, max_lists=len(lens))
+    # the stream still works
+    got = lr.rank_batch(dev(offsets), dev(succ), rank_dtype=torch.int32, max_lists=len(lens)).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.rank_batch(offsets, succ, None, np.int32))
