@@ -676,12 +676,11 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   // Single instance, no validation: heads from the streaming sums (one list)
   // with the bitmap as the fallback, instead of atomics for every element.
   const bool sums0 = !log0 && !ptrs && in.offsets == nullptr && !in.validate && in.n > u.cutoff;
-  // A batch with its list bound given: per-instance sums (kept at the start
-  // of the bitmap's memory, which must hold 16 bytes per instance) give one
-  // head per instance, with the bitmap as the fallback.
-  const bool sums0b = !log0 && !ptrs && in.offsets != nullptr && !in.validate && in.max_lists > 0 &&
-                      !extras && !spawn0 && in.n > u.cutoff && in.k > 0 &&
-                      (uint64_t)in.k * 16 <= 4 * ((in.n + 31) / 32);
+  // A batch: per-instance sums (kept at the start of the bitmap's memory,
+  // which must hold 16 bytes per instance) give one head per instance and the
+  // number of lists, with the bitmap as the fallback for the heads.
+  const bool sums0b = !log0 && !ptrs && in.offsets != nullptr && !in.validate && !extras && !spawn0 &&
+                      in.n > u.cutoff && in.k > 0 && (uint64_t)in.k * 16 <= 4 * ((in.n + 31) / 32);
   Profiler prof;
   if (!in.ctx) prof.begin(s, (int64_t)in.n);
   unsigned long long *acc = (unsigned long long *)(fixed + p.off_acc);
@@ -701,10 +700,14 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
                         s));
   if (need_count) {
     // count the lists (one wait), then size the recursion for exactly that many:
-    // a single-instance pass counts terminals in its reduction, the batched
-    // passes count zero bits of the has-predecessor bitmap
+    // a single-instance pass counts terminals in its reduction, a batch adds
+    // its instances' terminal counts, the other passes count zero bits of the
+    // has-predecessor bitmap
     if (log0 || sums0) {
       LR_TRY(cudaMemcpyAsync(c->host_words + 1, acc, 4, cudaMemcpyDeviceToHost, s));
+    } else if (sums0b) {
+      LR_TRY(launch_count_batch(reinterpret_cast<const unsigned long long *>(bitmap), in.k, hcount, s));
+      LR_TRY(cudaMemcpyAsync(c->host_words + 1, hcount, 4, cudaMemcpyDeviceToHost, s));
     } else {
       LR_TRY(launch_count_heads(bitmap, (uint32_t)in.n, hcount, s));
       LR_TRY(cudaMemcpyAsync(c->host_words + 1, hcount, 4, cudaMemcpyDeviceToHost, s));

@@ -420,6 +420,23 @@ k_bitmap0_recs(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ 
   }
 }
 
+// Lists of a batch from its per-instance sums: every list has one terminal.
+__global__ void __launch_bounds__(1024)
+k_count_batch(const unsigned long long *__restrict__ isums, int32_t k, uint32_t *__restrict__ out) {
+  __shared__ uint64_t sm[33];
+  uint64_t t = 0;
+  for (int32_t j = (int32_t)threadIdx.x; j < k; j += (int32_t)blockDim.x) t += isums[2 * (size_t)j];
+  uint64_t total;
+  block_exclusive_scan(t, sm, &total);
+  if (threadIdx.x == 0) *out = total > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)total;
+}
+
+cudaError_t launch_count_batch(const unsigned long long *isums, int32_t k, uint32_t *out, cudaStream_t s) {
+  k_count_batch<<<1, 1024, 0, s>>>(isums, k, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_heads0_batch(LevelDesc *desc, unsigned long long *isums, const int64_t *offsets, int32_t k,
                                 uint32_t *hlist0, uint32_t hcap, const void *work, bool rec16, uint32_t n,
                                 uint32_t *bitmap, cudaStream_t s) {

@@ -48,6 +48,7 @@ cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, ui
 cudaError_t launch_prep0_sums(const uint32_t *succ, const void *weight, int wtype, uint32_t n, void *work,
                               uint32_t *err, const int64_t *offsets, int32_t k, unsigned long long *isums,
                               cudaStream_t s);
+cudaError_t launch_count_batch(const unsigned long long *isums, int32_t k, uint32_t *out, cudaStream_t s);
 cudaError_t launch_heads0_batch(LevelDesc *desc, unsigned long long *isums, const int64_t *offsets, int32_t k,
                                 uint32_t *hlist0, uint32_t hcap, const void *work, bool rec16, uint32_t n,
                                 uint32_t *bitmap, cudaStream_t s);

@@ -190,7 +190,7 @@ def test_batch_heads_from_sums(weighted):
     w = gen.weights_i64(n, 901) if weighted else None
     want = oracle.rank_batch(offsets, succ, w, np.int64 if weighted else np.int32)
     rdt = torch.int64 if weighted else torch.int32
-    for ml in (64, 200):
+    for ml in (0, 64, 200):                                  # 0: the call counts the lists
         got = lr.rank_batch(dev(offsets), dev(succ), None if w is None else dev(w), rank_dtype=rdt,
                             max_lists=ml).cpu().numpy()
         np.testing.assert_array_equal(got, want)
@@ -204,8 +204,9 @@ def test_batch_sums_fallbacks_and_errors():
     want = oracle.rank_batch(offsets, succ, None, np.int32)
     lists = sum(int((succ[int(offsets[j]):int(offsets[j + 1])] ==
                      np.arange(int(offsets[j + 1] - offsets[j]))).sum()) for j in range(len(lens)))
-    got = lr.rank_batch(dev(offsets), dev(succ), rank_dtype=torch.int32, max_lists=lists).cpu().numpy()
-    np.testing.assert_array_equal(got, want)
+    for ml in (lists, 0):
+        got = lr.rank_batch(dev(offsets), dev(succ), rank_dtype=torch.int32, max_lists=ml).cpu().numpy()
+        np.testing.assert_array_equal(got, want)
     # more lists than the bound: a capacity error, as without the sums
     with pytest.raises(lr.LRError) as e:
         lr.rank_batch(dev(offsets), dev(succ), rank_dtype=torch.int32, max_lists=len(lens))
