@@ -69,16 +69,22 @@ __device__ __forceinline__ bool lc_is_head(uint32_t x, const uint32_t *hb) {
 
 // Shared-memory state of one tile.  Every element of the tile carries a
 // pointer p (first its local successor, or itself for a local tail) and the
-// link-weight distance d to p; pointer doubling (p, d) <- (p[p], d + d[p])
-// from one buffer into the other reaches the local tail and the distance to
-// it in at most kTileShift rounds, because a local sublist has fewer than
-// kTile links.  The low 16 bits of a word hold p and a settled bit (below),
-// so one word holds d << 16 | bits where d fits:
-// unweighted distances (below kTile) in 32 bits, distances over weights
-// that fit in int32 (below kTile * 2^31 in magnitude) in 64 bits.  Adding
-// two packed words whose first has its p bits cleared adds the distances
-// and takes the second's pointer.  A tile with a wider int64 weight keeps
-// the distances in a separate array, single-buffered (two barriers a round).
+// number of links d to p; pointer doubling (p, d) <- (p[p], d + d[p]) from
+// one buffer into the other reaches the local tail and the link count to it
+// in at most kTileShift rounds, because a local sublist has fewer than kTile
+// links.  One 32-bit word holds d << 16 | s | p, where s is a settled bit
+// set once p is a local tail; adding two words whose first has its low half
+// cleared adds the counts and takes the second's pointer.
+//
+// With weights, the link counts place every element of a local sublist in
+// list order: the sublists get consecutive ranges of positions (a scan over
+// their heads, whose link count is the sublist's length less one), an
+// element sits at its tail's position less its link count, and one prefix
+// sum of the weights in position order gives every weighted distance as a
+// difference of two sums.  A tile with an int64 weight beyond the int32
+// range instead doubles separate 64-bit distances, single-buffered (two
+// barriers a round).
+//
 // Predecessor marks are plain byte stores (one per local link), turned into
 // the has-local-predecessor bitmap afterwards; fewer marked elements than
 // local links means an element with two local predecessors.
@@ -88,21 +94,29 @@ struct LcMarks {
   uint32_t tail[kTileWords]; // local-tail bitmap (wide int64 tiles only)
   uint32_t nlinks, nmarked;  // local links; marked elements
 };
+struct LcPos {
+  union {
+    uint32_t pk[2][kTile];   // the doubling's words, double-buffered
+    uint64_t P[kTile];       // then the weights by list position, and their prefix sums
+  };
+  int32_t w[kTile];          // each element's link weight (0 for a local tail)
+  uint16_t E[kTile];         // list position of each local tail
+};
 // The word arrays come first: they are read and written as 16-byte vectors.
 template <int WT>
 struct LcTile {
-  alignas(16) uint32_t pk[2][kTile];   // d << 16 | low bits, double-buffered
+  alignas(16) LcPos q;
   LcMarks m;
 };
 template <>
-struct LcTile<1> {
-  alignas(16) uint64_t pk[2][kTile];
+struct LcTile<0> {
+  alignas(16) uint32_t pk[2][kTile];   // unweighted: the doubling's words only
   LcMarks m;
 };
 template <>
 struct LcTile<2> {
   union alignas(16) {
-    uint64_t pk[2][kTile];   // every weight of the tile fits in int32
+    LcPos q;                 // every weight of the tile fits in int32
     struct {
       uint64_t d[kTile];     // otherwise: distances
       uint16_t p[kTile];     // and pointers
@@ -111,13 +125,15 @@ struct LcTile<2> {
   LcMarks m;
 };
 static_assert(offsetof(LcTile<0>, m) % 16 == 0 && offsetof(LcTile<1>, m) % 16 == 0 &&
-                  offsetof(LcTile<2>, m) % 16 == 0 && offsetof(LcMarks, mark) == 0,
+                  offsetof(LcTile<2>, m) % 16 == 0 && offsetof(LcMarks, mark) == 0 &&
+                  offsetof(LcPos, w) % 16 == 0 && offsetof(LcPos, E) % 16 == 0,
               "vector accesses to the tile arrays and the marks stay aligned");
 
-// Per-element state a thread keeps in registers: the packed word (WT 0
-// and 1), or the distance with the pointer beside it (WT 2).
-template <int WT> struct LcState { using T = uint64_t; };
-template <> struct LcState<0> { using T = uint32_t; };
+template <int WT>
+__device__ __forceinline__ uint32_t *lc_words(LcTile<WT> &S, int b) {
+  if constexpr (WT == 0) return S.pk[b];
+  else return S.q.pk[b];
+}
 
 // Elements a thread owns: two runs of four consecutive ids, 4*tid and
 // kTile/2 + 4*tid, so that every run is one vector load or store.
@@ -129,41 +145,23 @@ constexpr uint32_t kLcRunStride = kTile / kLcRuns;
 constexpr uint32_t kLcPtrMask = kTile - 1u;
 constexpr uint32_t kLcSettled = 0x8000u;
 static_assert(kTile <= kLcSettled, "pointers stay below the settled bit");
-
-// Store a run of four elements: packed into buffer b, or (wide) the
-// distances and pointers of the single-buffered form.
-template <int WT>
-__device__ __forceinline__ void lc_put(LcTile<WT> &S, int b, uint32_t j0, const typename LcState<WT>::T (&x)[4],
-                                       const uint32_t (&p)[4], bool wide) {
-  if constexpr (WT == 0) {
-    *reinterpret_cast<uint4 *>(&S.pk[b][j0]) = make_uint4(x[0], x[1], x[2], x[3]);
-  } else {
-    if constexpr (WT == 2) {
-      if (wide) {
-        *reinterpret_cast<uint2 *>(&S.w.p[j0]) = make_uint2(p[0] | p[1] << 16, p[2] | p[3] << 16);
-        *reinterpret_cast<ulonglong2 *>(&S.w.d[j0]) = make_ulonglong2(x[0], x[1]);
-        *reinterpret_cast<ulonglong2 *>(&S.w.d[j0 + 2]) = make_ulonglong2(x[2], x[3]);
-        return;
-      }
-    }
-    *reinterpret_cast<ulonglong2 *>(&S.pk[b][j0]) = make_ulonglong2(x[0], x[1]);
-    *reinterpret_cast<ulonglong2 *>(&S.pk[b][j0 + 2]) = make_ulonglong2(x[2], x[3]);
-  }
-}
+// Weighted: the prefix sums are taken by each thread over 8 consecutive
+// positions, then across the threads.
+static_assert(kLcThreads * 8 == kTile, "one thread per 8 positions");
 
 // Load tile `t` (len elements) and give every element its local tail p and
 // distance d to it (in the rank's arithmetic, modulo 2^64); p = kEnd16 for
 // an element on, or leading into, a cycle inside the tile.  Two local links
-// into one element and successors out of range are reported.  pred[] and
-// tail[] hold the tile's bitmaps afterwards.
+// into one element and successors out of range are reported.  pred[] holds
+// the tile's has-local-predecessor bitmap afterwards.
 template <int WT>
 __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uint32_t *succ,
                               const void *weight, uint32_t n, bool vec, uint32_t (&p)[kLcRuns][4],
                               uint64_t (&d)[kLcRuns][4], uint32_t &bad) {
-  using T = typename LcState<WT>::T;
+  __shared__ uint64_t scan_sm[33];
   const uint32_t base = t << kTileShift;
   const uint32_t tid = threadIdx.x;
-  T x[kLcRuns][4];
+  uint32_t x[kLcRuns][4];      // d << 16 | settled | p
   uint32_t links = 0;
   // int64 weights: does any weight of the tile leave the int32 range?
   bool wide = false;
@@ -215,8 +213,8 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
       if (j < len && s[e] >= n) bad |= kErrRange;
       const bool local = j < len && s[e] < n && s[e] != i && (s[e] >> kTileShift) == t;
       p[r][e] = local ? s[e] - base : j;
-      const uint64_t dw = local ? w[e] : 0u;
-      x[r][e] = wide ? (T)dw : (T)(dw << 16) | (T)p[r][e] | (local ? (T)0 : (T)kLcSettled);
+      x[r][e] = (local ? 1u << 16 : kLcSettled) | p[r][e];
+      if constexpr (WT != 0) d[r][e] = local ? w[e] : 0u;   // exact in int32 unless the tile is wide
       if (local) {
         S.m.mark[s[e] - base] = 1;
         ++links;
@@ -224,8 +222,17 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
         tails |= 1u << e;
       }
     }
-    if (wide && tails) atomicOr(&S.m.tail[j0 >> 5], tails << (j0 & 31u));
-    lc_put<WT>(S, 0, j0, x[r], p[r], wide);
+    if (!wide) {
+      *reinterpret_cast<uint4 *>(&lc_words(S, 0)[j0]) = make_uint4(x[r][0], x[r][1], x[r][2], x[r][3]);
+      if constexpr (WT != 0)
+        *reinterpret_cast<int4 *>(&S.q.w[j0]) =
+            make_int4((int32_t)d[r][0], (int32_t)d[r][1], (int32_t)d[r][2], (int32_t)d[r][3]);
+    } else if constexpr (WT == 2) {
+      atomicOr(&S.m.tail[j0 >> 5], tails << (j0 & 31u));
+      *reinterpret_cast<uint2 *>(&S.w.p[j0]) = make_uint2(p[r][0] | p[r][1] << 16, p[r][2] | p[r][3] << 16);
+      *reinterpret_cast<ulonglong2 *>(&S.w.d[j0]) = make_ulonglong2(d[r][0], d[r][1]);
+      *reinterpret_cast<ulonglong2 *>(&S.w.d[j0 + 2]) = make_ulonglong2(d[r][2], d[r][3]);
+    }
   }
   links = __reduce_add_sync(0xFFFFFFFFu, links);
   if ((tid & 31u) == 0 && links) atomicAdd(&S.m.nlinks, links);
@@ -244,30 +251,119 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
     c = __reduce_add_sync(0xFFFFFFFFu, c);
     if ((tid & 31u) == 0 && c) atomicAdd(&S.m.nmarked, c);
   }
-  // pointer doubling until no pointer moves (a valid tile needs at most
-  // kTileShift rounds and one more to see it; a cycle never settles)
   if (!wide) {
-    // A word whose pointer has reached a local tail is final: it is not
-    // gathered again, and the rounds end when every word is final.  The
-    // settled bit travels with the pointer (a tail's own word has it), so
-    // after a gather it says whether the new pointer is a tail.
+    // Pointer doubling on the packed words.  A word whose pointer has
+    // reached a local tail is final: it is not gathered again, and the
+    // rounds end when every word is final (a valid tile needs at most
+    // kTileShift rounds; a cycle never settles).
     int b = 0;
     for (int round = 0; round <= kTileShift; ++round) {
       uint32_t all = kLcSettled;
+      const uint32_t *cur = lc_words(S, b);
+      uint32_t *nxt = lc_words(S, b ^ 1);
 #pragma unroll
       for (uint32_t r = 0; r < kLcRuns; ++r) {
 #pragma unroll
         for (uint32_t e = 0; e < 4; ++e) {
-          if (!((uint32_t)x[r][e] & kLcSettled)) {
-            const T v = S.pk[b][(uint32_t)x[r][e] & kLcPtrMask];
-            x[r][e] = (x[r][e] & ~(T)0xFFFFu) + v;
+          if (!(x[r][e] & kLcSettled)) {
+            const uint32_t v = cur[x[r][e] & kLcPtrMask];
+            x[r][e] = (x[r][e] & 0xFFFF0000u) + v;
           }
-          all &= (uint32_t)x[r][e];
+          all &= x[r][e];
         }
-        lc_put<WT>(S, b ^ 1, r * kLcRunStride + 4 * tid, x[r], p[r], false);
+        *reinterpret_cast<uint4 *>(&nxt[r * kLcRunStride + 4 * tid]) =
+            make_uint4(x[r][0], x[r][1], x[r][2], x[r][3]);
       }
       b ^= 1;
       if (__syncthreads_and(all & kLcSettled)) break;
+    }
+    // unpack; a word that never settled is on, or leads into, a cycle (also
+    // one whose length is a power of two: its pointer comes back to itself)
+#pragma unroll
+    for (uint32_t r = 0; r < kLcRuns; ++r)
+#pragma unroll
+      for (uint32_t e = 0; e < 4; ++e) {
+        p[r][e] = (x[r][e] & kLcSettled) ? (x[r][e] & kLcPtrMask) : kEnd16;
+        if constexpr (WT == 0) d[r][e] = x[r][e] >> 16;
+      }
+    if constexpr (WT != 0) {
+      // positions: every settled local head opens a range of its sublist's
+      // length; its tail gets the range's last position
+      uint32_t cnt = 0;
+#pragma unroll
+      for (uint32_t r = 0; r < kLcRuns; ++r)
+#pragma unroll
+        for (uint32_t e = 0; e < 4; ++e) {
+          const uint32_t j = r * kLcRunStride + 4 * tid + e;
+          const bool head = j < len && p[r][e] != kEnd16 && !((S.m.pred[j >> 5] >> (j & 31u)) & 1u);
+          if (head) cnt += (x[r][e] >> 16) + 1u;
+        }
+      uint64_t total;
+      uint32_t at = (uint32_t)block_exclusive_scan((uint64_t)cnt, scan_sm, &total);
+      // more positions than elements: merged sublists (two predecessors,
+      // reported by the marks); no weighted distances for this tile
+      const bool fits = total <= kTile;
+      if (fits) {
+#pragma unroll
+        for (uint32_t r = 0; r < kLcRuns; ++r)
+#pragma unroll
+          for (uint32_t e = 0; e < 4; ++e) {
+            const uint32_t j = r * kLcRunStride + 4 * tid + e;
+            const bool head = j < len && p[r][e] != kEnd16 && !((S.m.pred[j >> 5] >> (j & 31u)) & 1u);
+            if (head) {
+              at += (x[r][e] >> 16) + 1u;
+              S.q.E[p[r][e]] = (uint16_t)(at - 1u);
+            }
+          }
+      }
+      __syncthreads();                       // E is written; the doubling's buffers are free
+      if (fits) {
+        // weights by position (a tail's own link does not count); ids past
+        // the end of the last tile are lone tails of no sublist
+#pragma unroll
+        for (uint32_t r = 0; r < kLcRuns; ++r)
+#pragma unroll
+          for (uint32_t e = 0; e < 4; ++e) {
+            const uint32_t j = r * kLcRunStride + 4 * tid + e;
+            if (j < len && p[r][e] != kEnd16) {
+              const uint32_t pos = ((uint32_t)S.q.E[p[r][e]] - (x[r][e] >> 16)) & kLcPtrMask;
+              S.q.P[pos] = (uint64_t)(int64_t)S.q.w[j];
+            }
+          }
+      }
+      __syncthreads();
+      if (fits) {
+        // inclusive prefix sums over the positions, 8 per thread
+        uint64_t v[8];
+        const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(&S.q.P[8 * tid]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const ulonglong2 u = src[q];
+          v[2 * q] = u.x;
+          v[2 * q + 1] = u.y;
+        }
+#pragma unroll
+        for (int q = 1; q < 8; ++q) v[q] += v[q - 1];
+        const uint64_t off = block_exclusive_scan(v[7], scan_sm, nullptr);
+        ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(&S.q.P[8 * tid]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_ulonglong2(v[2 * q] + off, v[2 * q + 1] + off);
+      } else if (tid == 0) {
+        bad |= kErrNotList;
+      }
+      __syncthreads();
+      // distance = sum of the weights from the element's position to its tail's
+#pragma unroll
+      for (uint32_t r = 0; r < kLcRuns; ++r)
+#pragma unroll
+        for (uint32_t e = 0; e < 4; ++e) {
+          d[r][e] = 0;
+          if (fits && p[r][e] != kEnd16 && r * kLcRunStride + 4 * tid + e < len) {
+            const uint32_t last = S.q.E[p[r][e]] & kLcPtrMask;
+            const uint32_t pos = (last - (x[r][e] >> 16)) & kLcPtrMask;
+            d[r][e] = S.q.P[last] - (pos ? S.q.P[pos - 1] : 0u);
+          }
+        }
     }
   } else if constexpr (WT == 2) {
     // wide int64 weights: read every element's target, wait, write back
@@ -279,37 +375,26 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
         for (uint32_t e = 0; e < 4; ++e) {
           const uint32_t q = S.w.p[p[r][e]];
           diff |= q ^ p[r][e];
-          x[r][e] += S.w.d[p[r][e]];
+          d[r][e] += S.w.d[p[r][e]];
           p[r][e] = q;
         }
       __syncthreads();
 #pragma unroll
-      for (uint32_t r = 0; r < kLcRuns; ++r) lc_put<WT>(S, 0, r * kLcRunStride + 4 * tid, x[r], p[r], true);
+      for (uint32_t r = 0; r < kLcRuns; ++r) {
+        const uint32_t j0 = r * kLcRunStride + 4 * tid;
+        *reinterpret_cast<uint2 *>(&S.w.p[j0]) = make_uint2(p[r][0] | p[r][1] << 16, p[r][2] | p[r][3] << 16);
+        *reinterpret_cast<ulonglong2 *>(&S.w.d[j0]) = make_ulonglong2(d[r][0], d[r][1]);
+        *reinterpret_cast<ulonglong2 *>(&S.w.d[j0 + 2]) = make_ulonglong2(d[r][2], d[r][3]);
+      }
       if (!__syncthreads_or(diff != 0)) break;
     }
+    // a pointer that did not settle on a local tail marks a cycle
+#pragma unroll
+    for (uint32_t r = 0; r < kLcRuns; ++r)
+#pragma unroll
+      for (uint32_t e = 0; e < 4; ++e)
+        if (!((S.m.tail[p[r][e] >> 5] >> (p[r][e] & 31u)) & 1u)) p[r][e] = kEnd16;
   }
-  // unpack; a pointer that did not settle on a local tail marks a cycle
-  // (also one whose length is a power of two: it settles on itself, which
-  // is not a tail)
-#pragma unroll
-  for (uint32_t r = 0; r < kLcRuns; ++r)
-#pragma unroll
-    for (uint32_t e = 0; e < 4; ++e) {
-      bool settled;
-      if constexpr (WT == 0) {
-        d[r][e] = x[r][e] >> 16;
-        p[r][e] = x[r][e] & kLcPtrMask;
-        settled = (x[r][e] & kLcSettled) != 0;
-      } else if (!wide) {
-        d[r][e] = (uint64_t)((int64_t)x[r][e] >> 16);        // signed: |d| < 2^47
-        p[r][e] = (uint32_t)x[r][e] & kLcPtrMask;
-        settled = ((uint32_t)x[r][e] & kLcSettled) != 0;
-      } else {
-        d[r][e] = x[r][e];
-        settled = (S.m.tail[p[r][e] >> 5] >> (p[r][e] & 31u)) & 1u;
-      }
-      if (!settled) p[r][e] = kEnd16;
-    }
 }
 }  // namespace
 
