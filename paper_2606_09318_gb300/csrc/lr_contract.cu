@@ -18,13 +18,14 @@
 // Contracted ids are dense: a rank/select structure over the local-head
 // bitmap gives node(x) = heads in earlier tiles + heads before x in its tile.
 //
-// Inside a tile, dist and t come from pointer doubling over all of the
-// tile's elements in shared memory, each thread holding the pointers and
-// distances of its eight elements in registers: at most log2(tile) rounds
-// of one shared-memory gather per element, with no divergence, and it stops
-// as soon as a round moves no pointer.  (A ruling set inside the tile does
-// less work, but its walks diverge and its phases need more barriers; on
-// GB300 the doubling was the faster of the two.)
+// Inside a tile, t and the link count to it come from pointer doubling over
+// all of the tile's elements in shared memory, each thread holding the
+// words of its eight elements in registers: at most log2(tile) rounds of
+// one shared-memory gather per unsettled element, with no divergence, until
+// every pointer has reached a local tail.  Weighted distances then follow
+// from one prefix sum of the weights in list order.  (A ruling set inside
+// the tile does less work, but its walks diverge and its phases need more
+// barriers; on GB300 the doubling was the faster of the two.)
 //
 // Passes: solve (every tile in shared memory: distances to the local tails,
 // the local-head bitmap), scan (tile prefixes), nodes (the contracted
