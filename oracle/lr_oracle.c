@@ -16,7 +16,7 @@
  *   - The unweighted problem is the weighted one with weight 1 on every link
  *     and weight 0 on the terminal (Section 1.1, last paragraph).
  *
- * Readings where the paper is silent (listed again in the design doc):
+ * Readings where the paper is silent:
  *   - weight[i] is the weight of the link i -> succ[i]; a terminal has no
  *     outgoing link, so its weight is ignored and rank[t] == 0.
  *   - Sums wrap around in two's complement in the rank type; int32 weights
