@@ -372,7 +372,7 @@ cudaError_t launch_prep0_sums(const uint32_t *succ, const void *weight, int wtyp
 // k_bitmap0_recs fills it.
 __global__ void __launch_bounds__(1024)
 k_heads0_batch(LevelDesc *desc, unsigned long long *isums, const int64_t *__restrict__ offsets, int32_t k,
-               uint32_t *__restrict__ hlist0, uint32_t hcap) {
+               uint32_t *__restrict__ hlist0, uint32_t hcap, uint32_t n) {
   __shared__ uint64_t sm[33];
   LevelDesc &d = desc[0];
   int fallback = 0;
@@ -382,8 +382,11 @@ k_heads0_batch(LevelDesc *desc, unsigned long long *isums, const int64_t *__rest
     uint32_t has = 0;
     uint64_t head = 0;
     if (j < k) {
-      const uint64_t b = (uint64_t)offsets[j], nj = (uint64_t)offsets[j + 1] - b;
-      if (nj > 0) {
+      const int64_t b0 = offsets[j], b1 = offsets[j + 1];
+      if (b0 < 0 || b1 < b0 || (uint64_t)b1 > n) {
+        fallback = 1;                        // a bad offset table: the prep reported it
+      } else if (b1 > b0) {
+        const uint64_t b = (uint64_t)b0, nj = (uint64_t)(b1 - b0);
         const unsigned long long T = isums[2 * (size_t)j], S = isums[2 * (size_t)j + 1];
         const unsigned long long h = nj * (nj - 1) / 2 - S;
         if (T == 1 && h < nj) { has = 1; head = b + h; }
@@ -440,7 +443,7 @@ cudaError_t launch_count_batch(const unsigned long long *isums, int32_t k, uint3
 cudaError_t launch_heads0_batch(LevelDesc *desc, unsigned long long *isums, const int64_t *offsets, int32_t k,
                                 uint32_t *hlist0, uint32_t hcap, const void *work, bool rec16, uint32_t n,
                                 uint32_t *bitmap, cudaStream_t s) {
-  k_heads0_batch<<<1, 1024, 0, s>>>(desc, isums, offsets, k, hlist0, hcap);
+  k_heads0_batch<<<1, 1024, 0, s>>>(desc, isums, offsets, k, hlist0, hcap, n);
   k_bitmap0_recs<<<stream_grid(n, 256), 256, 0, s>>>(desc, reinterpret_cast<const uint32_t *>(work),
                                                       rec16 ? 4u : 2u, n, bitmap);
   count_launch(2);

@@ -234,3 +234,19 @@ def test_batch_sums_fallbacks_and_errors():
     # the stream still works
     got = lr.rank_batch(dev(offsets), dev(succ), rank_dtype=torch.int32, max_lists=len(lens)).cpu().numpy()
     np.testing.assert_array_equal(got, oracle.rank_batch(offsets, succ, None, np.int32))
+
+
+def test_batch_bad_offset_table():
+    # A decreasing offset table is reported, not trusted: with or without a
+    # list bound the call fails with an error status.
+    n = 20000
+    succ = gen.random_list(n, 970)
+    offsets = np.array([0, 5000, 3000, n], dtype=np.int64)
+    for ml in (0, 3):
+        with pytest.raises(lr.LRError):
+            lr.rank_batch(dev(offsets), dev(succ), rank_dtype=torch.int32, max_lists=ml, n_total=n)
+    good = np.array([0, 5000, 12000, n], dtype=np.int64)
+    parts = [gen.random_list(int(good[j + 1] - good[j]), 971 + j) for j in range(3)]
+    s2 = np.concatenate(parts).astype(np.uint32)
+    got = lr.rank_batch(dev(good), dev(s2), rank_dtype=torch.int32, max_lists=3).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.rank_batch(good, s2, None, np.int32))
