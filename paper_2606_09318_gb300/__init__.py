@@ -591,7 +591,12 @@ class Pipeline:
 
 
 class Server:
-    """Continuous-batching ranking server (lr_server_* of the C ABI)."""
+    """Continuous-batching ranking server (lr_server_* of the C ABI).
+
+    Requests of at least alone_min_n elements (0: the library's default,
+    2^20; negative: never) are ranked on their own through the single-list
+    path; smaller ones that wait together are ranked as one forest.  With
+    plain=True every request is ranked on its own (the baseline mode)."""
 
     def __init__(self, budget_bytes=40_000_000_000, n_streams=2, max_batch=256,
                  max_batch_elems=1 << 28, device=0, plain=False, alone_min_n=0):
