@@ -147,8 +147,11 @@ int lro_rank_batch(const int64_t *offsets, int32_t k, const uint32_t *succ,
  *               succ[x] == x;
  *   prefix[i] = the sum of the link weights from the head of i's list up to
  *               i, not counting i's own link (0 at a head);
- *   inclusive: rank[i] += weight of the terminal (1 when unweighted), i.e. the
- *               terminal's weight is no longer ignored.
+ *   inclusive: rank[i] += weight of the terminal, i.e. the terminal's weight
+ *               is no longer ignored.  In the unweighted problem the terminal
+ *               weighs 0 (Section 1.1: unweighted means weight 1 on every
+ *               element except the terminal, which gets 0), so there the
+ *               inclusive form equals the plain rank.
  * term and prefix may be NULL (not produced); prefix has the rank type.
  */
 int lro_rank_ext(const uint32_t *succ, const void *weight, int wtype, int64_t n,
@@ -167,7 +170,7 @@ int lro_rank_ext(const uint32_t *succ, const void *weight, int wtype, int64_t n,
         while (succ[t] != t) t = succ[t];
         /* walk again from the head: terminal, running prefix, inclusive rank */
         uint64_t acc = 0;
-        uint64_t wt = weight_of(weight, wtype, t);
+        uint64_t wt = wtype == LRO_W_NONE ? 0u : weight_of(weight, wtype, t);
         uint32_t x = (uint32_t)h;
         for (;;) {
             if (term) term[x] = t;

@@ -286,7 +286,8 @@ def test_ext_brute_force_forest(seed):
         np.testing.assert_array_equal(p, bp)
         np.testing.assert_array_equal(r, brute_force(succ, weight, np.int64))
         ri, ti, pi = oracle.rank_ext(succ, weight, np.int64, inclusive=True)
-        wt = np.ones(400, dtype=np.int64) if weight is None else weight.astype(np.int64)
+        # Section 1.1: the unweighted problem gives the terminal weight 0
+        wt = np.zeros(400, dtype=np.int64) if weight is None else weight.astype(np.int64)
         np.testing.assert_array_equal(ri, r + wt[bt])
         np.testing.assert_array_equal(ti, bt)
         np.testing.assert_array_equal(pi, bp)
@@ -299,7 +300,7 @@ def test_ext_identity_closed_form(n):
     np.testing.assert_array_equal(t, np.full(n, n - 1))
     np.testing.assert_array_equal(p, np.arange(n))
     ri, _, _ = oracle.rank_ext(succ, inclusive=True)
-    np.testing.assert_array_equal(ri, n - np.arange(n))
+    np.testing.assert_array_equal(ri, n - 1 - np.arange(n))  # unweighted terminal weighs 0
     w = gen.weights_i64(n, n, lo=-50, hi=50)
     r, t, p = oracle.rank_ext(succ, w, np.int64)
     excl = np.concatenate([[0], np.cumsum(w[:-1])])          # sum of the links before i
@@ -357,8 +358,9 @@ def test_ext_batch_local_terminals():
 _EXT_MUTATIONS = {
     "prefix_counts_own_link": ("            acc += weight_of(weight, wtype, x);\n            x = succ[x];",
                                "            x = succ[x];\n            acc += weight_of(weight, wtype, x);"),
-    "inclusive_uses_head_weight": ("uint64_t wt = weight_of(weight, wtype, t);",
-                                   "uint64_t wt = weight_of(weight, wtype, h);"),
+    "inclusive_uses_head_weight": ("0u : weight_of(weight, wtype, t);",
+                                   "0u : weight_of(weight, wtype, h);"),
+    "unweighted_terminal_weighs_one": ("wtype == LRO_W_NONE ? 0u :", "wtype == LRO_W_NONE ? 1u :"),
     "term_is_head": ("if (term) term[x] = t;", "if (term) term[x] = (uint32_t)h;"),
     "prefix_starts_at_head_weight": ("        uint64_t acc = 0;\n        uint64_t wt",
                                      "        uint64_t acc = weight_of(weight, wtype, h);\n        uint64_t wt"),
@@ -383,6 +385,13 @@ def _ext_pins_pass(lib):
                                   t.ctypes.data, p.ctypes.data, incl)
             want_r = brute_force(succ, w, np.int64) + (w.astype(np.int64)[bt] if incl else 0)
             if st != 0 or not (np.array_equal(t, bt) and np.array_equal(p, bp) and np.array_equal(r, want_r)):
+                return False
+            # unweighted: the terminal weighs 0 (Section 1.1), so the
+            # inclusive form is the plain link count
+            r = np.zeros(300, dtype=np.int64)
+            st = lib.lro_rank_ext(succ.ctypes.data, None, 0, 300, r.ctypes.data, 2,
+                                  t.ctypes.data, p.ctypes.data, incl)
+            if st != 0 or not np.array_equal(r, brute_force(succ, None, np.int64)):
                 return False
     return True
 
