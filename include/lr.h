@@ -206,7 +206,9 @@ lr_status lr_rank_batch_ex(const int64_t *offsets, const uint32_t *succ, const v
  *                   weights from i's head to i (0 at a head; the list's
  *                   total at its terminal).  NULL: not produced.
  *   inclusive_tail  1: rank[i] also counts the terminal's own weight
- *                   (weight[t], or 1 when unweighted), so rank[t] = w(t).
+ *                   weight[t], so rank[t] = weight[t].  Unweighted, the
+ *                   terminal weighs 0 (Section 1.1: weight 1 on every
+ *                   element but the terminal), so the flag changes nothing.
  *                   prefix is the same either way.
  * Not available with LR_ALGO_WYLLIE (LR_ERR_INVALID_ARGUMENT).  Errors as
  * for lr_rank_ex; on error the extra outputs are unspecified too.

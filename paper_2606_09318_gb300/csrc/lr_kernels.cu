@@ -1144,8 +1144,9 @@ k_out_heads(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ bit
 
 // Streaming pass: prefix[i] = total - rank[i] (a terminal's entry holds the
 // total and keeps it, its rank being 0, so the pass may run in place); the
-// inclusive form adds the terminal's weight (1 when unweighted); in the
-// batched form terminal ids become local to their instance.
+// inclusive form adds the terminal's weight (weighted input only: unweighted,
+// the terminal weighs 0, Section 1.1); in the batched form terminal ids
+// become local to their instance.
 template <class RT>
 __global__ void __launch_bounds__(256)
 k_out_fix(uint32_t n, uint32_t *__restrict__ term, RT *__restrict__ rank, RT *__restrict__ prefix,
@@ -1157,7 +1158,7 @@ k_out_fix(uint32_t n, uint32_t *__restrict__ term, RT *__restrict__ rank, RT *__
     const RT r = rank[i];
     if (prefix) prefix[i] = (RT)(__ldcg(prefix + t) - r);
     if (incl) {
-      uint64_t wt = 1u;
+      uint64_t wt = 0u;
       if (wtype == 1) wt = (uint64_t)(int64_t)__ldg(reinterpret_cast<const int *>(weight) + t);
       else if (wtype == 2) wt = (uint64_t)__ldg(reinterpret_cast<const long long *>(weight) + t);
       rank[i] = (RT)(r + (RT)wt);
@@ -1178,6 +1179,7 @@ cudaError_t launch_outputs(const LevelDesc *desc, const uint32_t *bitmap, const 
                            int incl, const void *weight, int wtype, const int64_t *offsets, int32_t k,
                            int local, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
+  if (wtype == 0) incl = 0;                     // an unweighted terminal weighs 0
   const int grid = stream_grid(n, 256);
   int launches = 0;
   if (rank_bytes == 4) {

@@ -89,6 +89,8 @@ def test_only_some_outputs_and_workspace():
     np.testing.assert_array_equal(p.cpu().numpy(), want_p)
     r, t, p = lr.rank_outputs(dev(succ), term=False, prefix=False, inclusive_tail=True)
     np.testing.assert_array_equal(r.cpu().numpy(), want_r)
+    # unweighted, the terminal weighs 0 (Section 1.1): the inclusive form is the plain rank
+    np.testing.assert_array_equal(r.cpu().numpy(), oracle.rank(succ))
     ws = torch.empty(lr.workspace_size(n, max_lists=1, term=True), dtype=torch.uint8, device="cuda")
     s = torch.cuda.Stream()
     r, t, p = lr.rank_outputs(dev(succ), term=True, workspace=ws, max_lists=1, sync=False, stream=s)
