@@ -292,11 +292,17 @@ lr_status lr_get_device_status(lr_stream stream);
  *    LR_ERR_INVALID_ARGUMENT.
  *  - Workspace is a fixed 64 MiB scratch array compiled into liblr.so; every
  *    GPU that loads the library holds it until the process exits.  The
- *    first call on a device looks up the array's device address (with that
- *    device current) and sets up the library's kernels there; make that
- *    first call before any stream capture begins.  No cudaMalloc, cudaFree
- *    or other allocating call is made.  Inputs with so many lists that the
- *    recursion does not fit the scratch return LR_ERR_CAPACITY.
+ *    library's set-up on a device (done by the first lr_* call made with
+ *    that device current) looks up the array's device address, which is
+ *    also what places the array there; make some lr_* call on each device
+ *    early, before the process has taken all free device memory, and before
+ *    any stream capture begins.  If the array could not be placed then, the
+ *    first lr_rank_noalloc call tries again and returns
+ *    LR_ERR_OUT_OF_MEMORY when the device has no room.  No cudaMalloc,
+ *    cudaFree or other allocating call is made.  The ruling-set settings
+ *    are fixed (LR_TUNING and autotuned entries are not consulted).  Inputs
+ *    with so many lists that the recursion does not fit the scratch return
+ *    LR_ERR_CAPACITY.
  *  - All calls share the scratch, which keeps the last call's contents
  *    (everything that must start at zero is cleared by each call).  Calls
  *    that overlap on the GPU race, and the host side is not thread-safe:
@@ -339,18 +345,24 @@ lr_status lr_profile_read(lr_profile *out, int32_t reset);
 /*
  * Memory-system probe (measurement only; the paper has no counterpart).
  * The chase of Algorithm 1 is a dependent random walk, so its ceiling on a
- * GPU is the rate of random 32-byte accesses that miss L2, not the streaming
- * bandwidth.  On the caller's device buffer (>= 64 MiB, 256-byte aligned,
- * far larger than L2 for a meaningful number; its contents are destroyed)
- * this measures a streaming copy, a dependent random 8-byte gather and a
- * dependent random 8-byte atomic exchange, each over one seeded random
- * cycle through the buffer.  Waits for the device.
+ * GPU is the rate at which random accesses are served, not the streaming
+ * bandwidth, and that rate depends on the footprint the accesses cover.  On
+ * the caller's device buffer (>= 16 MiB, 256-byte aligned; its size is the
+ * footprint; its contents are destroyed) this measures a streaming copy, a
+ * dependent random 4-byte gather (the chase's own access), independent
+ * random 4-byte gathers with 8 in flight per thread, the same confined per
+ * warp to one random 2 MiB region at a time, and a dependent random 8-byte
+ * atomic exchange.  Each walk follows one seeded random cycle through the
+ * buffer.  Waits for the device.
  */
 typedef struct lr_probe_result {
     double copy_gbs;            /* streaming read + write, GB/s                  */
-    double gather_gsteps;       /* dependent random loads, G steps/s             */
-    double gather_xchg_gsteps;  /* dependent random exchanges, G steps/s         */
-    size_t footprint_bytes;     /* bytes the random walks covered                */
+    double gather_gsteps;       /* dependent random 4-byte loads, G steps/s      */
+    double gather_xchg_gsteps;  /* dependent random 8-byte exchanges, G steps/s  */
+    size_t footprint_bytes;     /* bytes the random accesses covered             */
+    double indep_gather_gsteps; /* independent random 4-byte loads, G/s          */
+    double region_gather_gsteps;/* the same inside one 2 MiB region per warp and */
+                                /* round, G/s (0 for footprints under 4 MiB)     */
 } lr_probe_result;
 
 lr_status lr_probe_memory(void *buf, size_t bytes, lr_probe_result *out, lr_stream stream);

@@ -287,6 +287,12 @@ lr_status setup_device_once() {
     if (e == cudaSuccess) e = log_setup();
     if (e == cudaSuccess) e = lc_setup();
     if (e != cudaSuccess) return from_cuda(e);
+    // Place lr_rank_noalloc's scratch array on this device now, while the
+    // process can still spare its 64 MiB: under lazy module loading it would
+    // otherwise be placed only at the first lr_rank_noalloc call, which may
+    // come after the caller's allocator has taken all free memory.  Best
+    // effort: a failure here surfaces at that call, with its status.
+    (void)noalloc_resolve_scratch();
     g_setup_done[dev] = true;
   }
   return LR_OK;
@@ -448,6 +454,7 @@ struct Inputs {
   int incl;                      // inclusive-tail ranks
   uint32_t *err_ext;             // record device errors here (and do not clear it)
   int no_contract;               // never contract (the contracted list itself)
+  int builtin_tuning;            // ignore LR_TUNING and the autotuned table
 };
 
 static lr_status map_device_bits(uint32_t bits) {
@@ -624,7 +631,9 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     return LR_OK;
   }
   const bool capturing = stream_capturing(s);
-  const Tuning u = resolve_tuning(tuning, (int64_t)in.n, in.wtype != 0, in.offsets != nullptr || ptrs);
+  const Tuning u = in.builtin_tuning ? resolve_tuning_builtin((int64_t)in.n, in.wtype != 0)
+                                     : resolve_tuning(tuning, (int64_t)in.n, in.wtype != 0,
+                                                      in.offsets != nullptr || ptrs);
   if (u.algo == LR_ALGO_WYLLIE && !ptrs) {
     if (in.term || in.prefix || in.incl) return LR_ERR_INVALID_ARGUMENT;   // default algorithm only
     return run_wyllie(in, c, s);
@@ -877,6 +886,9 @@ lr_status run_fixed_scratch(const uint32_t *succ, int64_t n, int32_t *rank, void
   in.ws_bytes = scratch_bytes;
   in.ctx = ctx;
   in.count_in_ws = 1;
+  // fixed settings: whether a valid list fits the scratch must not depend on
+  // LR_TUNING or on what the autotuner stored in this process
+  in.builtin_tuning = 1;
   return run(in, nullptr, s);
 }
 

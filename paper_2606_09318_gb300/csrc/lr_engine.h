@@ -94,6 +94,10 @@ lr_status run_fixed_scratch(const uint32_t *succ, int64_t n, int32_t *rank, void
                             size_t scratch_bytes, Ctx *ctx, cudaStream_t s);
 // Kernel attributes (shared-memory limits) for the current device, once.
 lr_status setup_device_once();
+// Device address of lr_rank_noalloc's fixed scratch array on the current
+// device, looked up once per device (lr_noalloc.cu).  setup_device_once calls
+// it, so the array is placed on the device by the first lr_* call there.
+lr_status noalloc_resolve_scratch();
 // One list in device memory, ranked on its own (the single-instance path,
 // with its automatic choices: tile-local contraction, the level-0 form);
 // waits for the result and returns the status.

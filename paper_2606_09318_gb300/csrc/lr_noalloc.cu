@@ -11,9 +11,14 @@
 // process exits.
 //
 // Host code must not take the array's name as a device address (in host code
-// it names a host-side stand-in), so the first call on each device, with that
-// device current, asks the runtime for the array's device address with
-// cudaGetSymbolAddress and keeps it.  All calls share the one array and it
+// it names a host-side stand-in), so the library's set-up on each device (the
+// first lr_* call made with that device current) asks the runtime for the
+// array's device address with cudaGetSymbolAddress and keeps it.  That lookup
+// is also what places the array on the device under lazy module loading, so
+// it happens as early as the library can make it, not at the first
+// lr_rank_noalloc call; if it failed there (no memory left), the first
+// lr_rank_noalloc call tries again and returns LR_ERR_OUT_OF_MEMORY or
+// LR_ERR_CUDA.  All calls share the one array and it
 // keeps the last call's contents; the pipeline clears what has to start at
 // zero on every call.  Calls whose work overlaps on the GPU race on the
 // scratch, so callers must serialise them (one stream, or wait between calls);
@@ -50,9 +55,10 @@ lr_status scratch_for_current_device(DeviceScratch **out) {
   DeviceScratch &d = g_dev[dev];
   if (!d.ptr) {
     void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
       cudaGetLastError();
-      return LR_ERR_CUDA;
+      return e == cudaErrorMemoryAllocation ? LR_ERR_OUT_OF_MEMORY : LR_ERR_CUDA;
     }
     memset(d.words, 0, sizeof(d.words));
     d.ctx.device = dev;
@@ -64,6 +70,13 @@ lr_status scratch_for_current_device(DeviceScratch **out) {
 }
 
 }  // namespace
+
+namespace lr {
+lr_status noalloc_resolve_scratch() {
+  DeviceScratch *d = nullptr;
+  return scratch_for_current_device(&d);
+}
+}  // namespace lr
 
 extern "C" lr_status lr_rank_noalloc(const uint32_t *succ, int64_t n, int32_t *rank, lr_stream stream) {
   if (n < 0 || n > LR_NOALLOC_MAX_N) return LR_ERR_INVALID_ARGUMENT;
