@@ -337,17 +337,18 @@ def run_ours(args):
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
                "api": "lr_pipeline (depth 2, list bound 1), pinned host buffers"}
 
-    # the chase is a dependent random walk: measure the GPU's random-access
-    # ceiling on a buffer far larger than L2 (same memory, same run)
-    probe = None
-    if not args.no_probe:
-        buf = torch.empty(2 << 30, dtype=torch.uint8, device=dev)
-        probe = lr.probe_memory(buf, stream)
-        del buf
-
     hbm, src = measured_peaks()
     chase_ms = prof["ms_chase0"] / max(1, prof["chase0_launches"])
     form = "log" if prof["chase0_log_launches"] == prof["chase0_launches"] > 0 else "exchange"
+
+    # the chase is a dependent random walk: measure the GPU's random-access
+    # ceiling over the chase's own footprint (succ, 4 B per element, for the
+    # log form; the 8 B records for the exchange form), same memory, same run
+    probe = None
+    if not args.no_probe:
+        buf = torch.empty((4 if form == "log" else 8) * n + 256, dtype=torch.uint8, device=dev)
+        probe = lr.probe_memory(buf, stream)
+        del buf
     kname, _, _, _, _, kbytes = CHASE0[form]
     achieved = kbytes * n / (chase_ms * 1e-3) / 1e9
     value = ws * n / (ms * 1e-3) / 1e9
@@ -370,15 +371,20 @@ def run_ours(args):
                      "frac": round(achieved / hbm, 4), "peak_source": src,
                      "traffic": ncu_traffic(n, form), "algorithmic_bytes": kbytes * n,
                      "ms_per_launch": round(chase_ms, 4),
-                     # the chase's own ceiling: dependent random gathers (log form)
-                     # or gathers with an atomic exchange (exchange form)
+                     # the chase's own ceiling over its footprint: independent
+                     # random gathers, 8 in flight per thread (log form), or
+                     # dependent gathers with an atomic exchange (exchange form)
                      "random_access_ceiling": None if probe is None else {
-                         "gather_g_per_s": round(probe["gather_gsteps"], 2),
+                         "footprint_bytes": int(probe["footprint_bytes"]),
+                         "indep_gather_g_per_s": round(probe["indep_gather_gsteps"], 2),
+                         "dependent_gather_g_per_s": round(probe["gather_gsteps"], 2),
+                         "gather_in_2mib_region_g_per_s": round(probe["region_gather_gsteps"], 2),
                          "gather_exchange_g_per_s": round(probe["gather_xchg_gsteps"], 2),
                          "copy_gbs": round(probe["copy_gbs"], 1),
+                         "ceiling": "indep_gather_g_per_s" if form == "log" else "gather_exchange_g_per_s",
                          "chase_frac_of_ceiling": round(
                              n / (chase_ms * 1e-3) / 1e9 /
-                             probe["gather_gsteps" if form == "log" else "gather_xchg_gsteps"], 4)}},
+                             probe["indep_gather_gsteps" if form == "log" else "gather_xchg_gsteps"], 4)}},
         "pipeline": {"random_sector_roofline_gelem_s": round(sector_roof, 2),
                      "frac": round(value / ws / sector_roof, 4),
                      "phases_ms_per_step": {k[3:]: round(prof[k] / steps_prof, 4) for k in
@@ -795,6 +801,29 @@ def run_pd_compare(args):
         torch.cuda.empty_cache()
 
 
+def run_probe_sweep(args):
+    """Random-access rates of the GPU against the footprint the accesses
+    cover (lr_probe_memory on buffers of 32 MiB .. 4 GiB): dependent 4-byte
+    gathers (the chase's access), independent gathers with 8 in flight per
+    thread, the same confined to one 2 MiB region per warp and round, and
+    dependent 8-byte atomic exchanges.  One JSON line per footprint."""
+    import torch
+    import paper_2606_09318_gb300 as lr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    for lg in [int(x) for x in args.probe_sizes.split(",")]:
+        buf = torch.empty((1 << lg) + 256, dtype=torch.uint8, device=dev)
+        r = lr.probe_memory(buf)
+        del buf
+        torch.cuda.empty_cache()
+        print(json.dumps({"workload": "probe", "footprint_mib": (1 << lg) >> 20,
+                          "dependent_gather_g_per_s": round(r["gather_gsteps"], 2),
+                          "indep_gather_g_per_s": round(r["indep_gather_gsteps"], 2),
+                          "gather_in_2mib_region_g_per_s": round(r["region_gather_gsteps"], 2),
+                          "dependent_exchange_g_per_s": round(r["gather_xchg_gsteps"], 2),
+                          "copy_gbs": round(r["copy_gbs"], 1)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -806,9 +835,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access probe")
     ap.add_argument("--pd-sizes", default="20,22,24,26,28", help="log2 sizes of --workload pd")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "sweep", "pd"],
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "sweep", "pd", "probe"],
                     help="single: the headline (default); batch / serve: the batched and serving sets; "
-                         "sweep: sizes and orders; pd: against whole-list pointer doubling")
+                         "sweep: sizes and orders; pd: against whole-list pointer doubling; "
+                         "probe: random-access rates against footprint")
+    ap.add_argument("--probe-sizes", default="25,26,27,28,29,30,31,32",
+                    help="probe: log2 footprints in bytes")
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured requests")
     ap.add_argument("--sweep-sizes", default="24,26,28,30", help="sweep: log2 sizes")
     ap.add_argument("--oracle-sizes", default="20,24,28",
@@ -836,6 +868,8 @@ def main():
         run_sweep(args)
     elif args.workload == "pd":
         run_pd_compare(args)
+    elif args.workload == "probe":
+        run_probe_sweep(args)
     else:
         run_ours(args)
 

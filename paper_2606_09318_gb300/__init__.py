@@ -105,7 +105,8 @@ class _ServerStats(ctypes.Structure):
 
 class _ProbeResult(ctypes.Structure):
     _fields_ = [("copy_gbs", ctypes.c_double), ("gather_gsteps", ctypes.c_double),
-                ("gather_xchg_gsteps", ctypes.c_double), ("footprint_bytes", ctypes.c_size_t)]
+                ("gather_xchg_gsteps", ctypes.c_double), ("footprint_bytes", ctypes.c_size_t),
+                ("indep_gather_gsteps", ctypes.c_double), ("region_gather_gsteps", ctypes.c_double)]
 
 
 _lock = threading.Lock()
