@@ -214,13 +214,37 @@ def ncu_traffic(n, form="exchange"):
     return float(d["dram_bytes_per_elem"]) * n
 
 
-def cpu_baseline(seconds_target=12.0):
-    """The oracle as it stands, one thread, on random lists of 2^24."""
+def host_cpu():
+    """The host's logical CPU count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in r.stdout.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or "unknown"}
+
+
+def cpu_baseline(seconds_target=15.0, lg=26):
+    """The oracle as it stands, one thread, on random lists of 2^26 (a quarter
+    of the headline size: the 2^28 list takes about a minute per run)."""
     import numpy as np
     import gen
     import oracle
     oracle.build()
-    n = 1 << 24
+    n = 1 << lg
     succ = gen.random_list(n, 2028)
     t_total, reps = 0.0, 0
     while t_total < seconds_target and reps < 8:
@@ -229,8 +253,10 @@ def cpu_baseline(seconds_target=12.0):
         t_total += time.perf_counter() - t0
         reps += 1
     assert r.shape[0] == n and np.int64(r.max()) == n - 1
-    return {"value": n * reps / t_total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "random-order list n=2^24 x %d runs (%.1f s), single thread" % (reps, t_total)}
+    out = {"value": n * reps / t_total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "random-order list n=2^%d x %d runs (%.1f s), single thread" % (lg, reps, t_total)}
+    out.update(host_cpu())
+    return out
 
 
 def make_random_list(n, seed, device):
@@ -410,7 +436,7 @@ def run_reference(args):
     import gen
     import oracle
     oracle.build()
-    n = 1 << 22
+    n = 1 << 24
     succ = gen.random_list(n, 4242)
     times = []
     for i in range(args.warmup + args.steps):
@@ -422,7 +448,7 @@ def run_reference(args):
     assert int(np.int64(r.max())) == n - 1
     t = sum(times)
     value = n * len(times) / t / 1e9
-    sample = "random-order list n=2^22 per step (bounded sample of the n=2^28 workload), single thread"
+    sample = "random-order list n=2^24 per step (bounded sample of the n=2^28 workload), single thread"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -430,8 +456,8 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "single random-order list, n=2^28, unweighted, int32 ranks",
                    "n": 1 << 28, "sample_n": n, "parallelism": "single GPU"},
-        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": dict({"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": sample}, **host_cpu()),
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 

@@ -22,6 +22,7 @@ def test_reference_arm_prints_one_complete_line():
     assert d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["nproc"] >= 1 and d["cpu_baseline"]["cpu_model"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("single random-order list, n=2^28")
     assert d["config"]["n"] == 1 << 28
