@@ -420,6 +420,16 @@ def run_ours(args):
         "clocks": clk.summary(),
         "e2e": e2e,
     }
+    # the batched and served forms (configs 4 and 5) on the same GPU, one
+    # replica only: the batch against the per-instance loop, the server
+    # against per-request plain launches on one trace of fresh requests
+    if ws == 1 and not args.no_batch:
+        line["batch"] = batch_measure(5, 3, dev)
+        torch.cuda.empty_cache()
+    if ws == 1 and not args.no_serve:
+        res, info = serve_measure(300, 30, [0.8, 2.0], 2, args.serve_capacity, dev)
+        line["serve"] = dict({"loads": res}, **info)
+        torch.cuda.empty_cache()
     if rk == 0 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     if rk == 0:
@@ -524,16 +534,16 @@ def _fill_succ(succ_view, order):
     succ_view[order[-1]] = order[-1].to(succ_view.dtype)
 
 
-def run_batch(args):
-    """1024 independent random-order instances, sizes floor(2^U), U ~ U[8,22],
-    int64 weights in [0, 2^20): one CUDA-graph replay of the batched call per
-    step, against a host loop of one lr_rank_ex call per instance."""
+def batch_measure(steps, warmup, dev):
+    """Config 4: 1024 independent random-order instances, sizes floor(2^U),
+    U ~ U[8,22], int64 weights in [0, 2^20): one CUDA-graph replay of the
+    autotuned batched call per step, against a host loop of one lr_rank_ex
+    call per instance.  Returns a dict; `exact` is the full recurrence over
+    every instance plus equality with the per-instance loop."""
     import numpy as np
     import torch
     import gen
     import paper_2606_09318_gb300 as lr
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
     k = 1024
     lens = gen.batch_lengths(k, gen.config_seed(4), 8.0, 22.0)
     offsets = np.zeros(k + 1, dtype=np.int64)
@@ -578,107 +588,137 @@ def run_batch(args):
         return e0.elapsed_time(e1) / steps
 
     with torch.cuda.stream(s):
-        ms_b = timed(graph.replay, args.steps, args.warmup)
+        ms_b = timed(graph.replay, steps, warmup)
         views = [(int(offsets[j]), int(offsets[j + 1])) for j in range(k)]
 
         def loop():
             for a, b in views:
                 lr.rank_ex(succ[a:b], w[a:b], out=out_l[a:b], max_lists=1, sync=False, stream=s)
         launches0 = lr.kernel_launch_count()
-        ms_l = timed(loop, max(1, args.steps // 2), 1)
-        per_loop_launches = (lr.kernel_launch_count() - launches0) / (max(1, args.steps // 2) + 1)
+        loop_steps = max(1, steps // 4)
+        ms_l = timed(loop, loop_steps, 1)
+        per_loop_launches = (lr.kernel_launch_count() - launches0) / (loop_steps + 1)
     assert lr.device_status(s) == 0
-    if not torch.equal(out_b, out_l):
-        raise RuntimeError("batched and per-instance results differ")
-    print(json.dumps({
-        "workload": "batch", "metric": "G list elements ranked/s, 1024 instances in one CUDA graph",
-        "value": round(n / (ms_b * 1e-3) / 1e9, 4), "unit": UNIT, "ms_per_step": round(ms_b, 3),
-        "n_total": n, "k": k, "dtype": "i64 weights, i64 ranks",
-        "per_instance_loop": {"value": round(n / (ms_l * 1e-3) / 1e9, 4), "ms_per_step": round(ms_l, 3),
-                              "kernel_launches_per_step": per_loop_launches},
-        "speedup_vs_loop": round(ms_l / ms_b, 3),
-        "autotuned": {"f0_inv": tuned.f0_inv, "f_inv": tuned.f_inv, "cutoff": tuned.cutoff,
-                      "chase_block": tuned.chase_block, "seconds": round(t_tune, 2)},
-        "config": {"workload": "batched: 1024 random-order instances, sizes floor(2^U), U~U[8,22], "
-                               "int64 weights in [0,2^20), graph-captured, autotuned"},
-    }), flush=True)
+    del graph, ws
+    inst = torch.repeat_interleave(torch.arange(k, device=dev), torch.from_numpy(lens).to(dev))
+    sg = d_off[inst] + (succ.to(torch.int64) & 0xFFFFFFFF)
+    del inst
+    exact = bool(torch.equal(out_b, out_l)) and _check_recurrence(sg, w, out_b, dev, global_succ=True)
+    lr.autotune_clear()
+    return {"metric": "G list elements ranked/s, 1024 instances in one CUDA graph",
+            "value": round(n / (ms_b * 1e-3) / 1e9, 4), "unit": UNIT, "ms_per_step": round(ms_b, 3),
+            "steps": steps, "n_total": n, "k": k, "dtype": "i64 weights, i64 ranks", "exact": exact,
+            "per_instance_loop": {"value": round(n / (ms_l * 1e-3) / 1e9, 4), "ms_per_step": round(ms_l, 3),
+                                  "steps": loop_steps, "kernel_launches_per_step": per_loop_launches},
+            "speedup_vs_loop": round(ms_l / ms_b, 3),
+            "autotuned": {"f0_inv": tuned.f0_inv, "f_inv": tuned.f_inv, "cutoff": tuned.cutoff,
+                          "chase_block": tuned.chase_block, "seconds": round(t_tune, 2)},
+            "config": {"workload": "batched: 1024 random-order instances, sizes floor(2^U), U~U[8,22], "
+                                   "int64 weights in [0,2^20), graph-captured, autotuned"}}
 
 
-def run_serve(args):
-    """Poisson request stream, sizes floor(2^U) with U ~ U[10,26], random or
-    locality order with p = 0.5, int64 weights, 40 GB budget: continuous
-    batching against plain per-request launches on the same trace."""
+def run_batch(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    d = batch_measure(args.steps, args.warmup, dev)
+    d["workload"] = "batch"
+    print(json.dumps(d), flush=True)
+
+
+def serve_measure(requests, warmup, loads, streams, capacity, dev, fresh_bytes=100e9):
+    """Config 5: a Poisson request stream, sizes floor(2^U) with U ~ U[10,26],
+    random or locality order with p = 0.5, int64 weights, 40 GB budget;
+    continuous batching against plain per-request launches on the same
+    trace, at each offered load (a multiple of a capacity guess in
+    elements/s).  Requests are generated on the device before the trace,
+    every one distinct while their arrays fit `fresh_bytes` (then reused
+    round-robin).  Returns {load: {"batched": ..., "plain": ...}}."""
     import threading as th
     import numpy as np
     import torch
     import gen
     import paper_2606_09318_gb300 as lr
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
     g = torch.Generator(device=dev)
     g.manual_seed(5000)
-    pool_n = 40
-    arrivals, sizes, kinds, _ = gen.serving_trace(args.requests + args.serve_warmup, gen.config_seed(5),
-                                                 rate_per_s=1.0)
-    pool = []
-    for i in range(pool_n):
+    total = requests + warmup
+    _, sizes, kinds, _ = gen.serving_trace(total, gen.config_seed(5), rate_per_s=1.0)
+    pool, used = [], 0
+    for i in range(total):
         m = int(sizes[i])
+        if used + 20 * m > fresh_bytes:
+            break
         order = _device_random_order(m, g, dev) if kinds[i] == "random" else _device_locality_order(m, g, dev)
         sc = torch.empty(m, dtype=torch.int32, device=dev)
         _fill_succ(sc, order)
-        pool.append((sc, torch.randint(0, 1 << 20, (m,), dtype=torch.int64, device=dev, generator=g)))
-    mean_n = float(np.mean([p[0].numel() for p in pool]))
-    results = {}
-    for mode in ("batched", "plain"):
-        srv = lr.Server(budget_bytes=40_000_000_000, n_streams=args.serve_streams, max_batch=256,
-                        plain=(mode == "plain"))
-        total = args.requests + args.serve_warmup
-        # offered load: args.load x a capacity guess in elements/s
-        rate = args.load * args.serve_capacity / mean_n
-        gaps = np.random.default_rng(55).exponential(1.0 / rate, size=total)
-        outs = [torch.empty(p[0].numel(), dtype=torch.int64, device=dev) for p in pool]
-        tickets = [None] * total
-        t_start = time.perf_counter()
+        del order
+        pool.append((sc, torch.randint(0, 1 << 20, (m,), dtype=torch.int64, device=dev, generator=g),
+                     torch.empty(m, dtype=torch.int64, device=dev)))
+        used += 20 * m
+    pool_n = len(pool)
+    mean_n = float(np.mean(sizes[:total]))
+    out = {}
+    for load in loads:
+        res = {}
+        for mode in ("batched", "plain"):
+            srv = lr.Server(budget_bytes=40_000_000_000, n_streams=streams, max_batch=256,
+                            plain=(mode == "plain"))
+            rate = load * capacity / mean_n
+            gaps = np.random.default_rng(55).exponential(1.0 / rate, size=total)
+            tickets = [None] * total
+            t_start = time.perf_counter()
 
-        def submitter():
-            t = t_start
+            def submitter():
+                t = t_start
+                for i in range(total):
+                    t += gaps[i]
+                    d = t - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    sc, wv, ov = pool[i % pool_n]
+                    tickets[i] = srv.submit(sc, wv, out=ov)
+            thr = th.Thread(target=submitter)
+            thr.start()
+            lat, elems, t_first, t_last = [], 0, None, None
             for i in range(total):
-                t += gaps[i]
-                d = t - time.perf_counter()
-                if d > 0:
-                    time.sleep(d)
-                sc, wv = pool[i % pool_n]
-                tickets[i] = srv.submit(sc, wv, out=outs[i % pool_n])
-        thr = th.Thread(target=submitter)
-        thr.start()
-        lat, elems, t_first, t_last = [], 0, None, None
-        for i in range(total):
-            while tickets[i] is None:
-                time.sleep(0.0002)
-            _, info = srv.wait(tickets[i])
-            if i >= args.serve_warmup:
-                lat.append(info["t_done_ms"] - info["t_submit_ms"])
-                elems += pool[i % pool_n][0].numel()
-                t_first = info["t_submit_ms"] if t_first is None else min(t_first, info["t_submit_ms"])
-                t_last = info["t_done_ms"] if t_last is None else max(t_last, info["t_done_ms"])
-        thr.join()
-        st = srv.stats()
-        srv.close()
-        lat = np.array(lat)
-        results[mode] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                _, info = srv.wait(tickets[i])
+                if i >= warmup:
+                    lat.append(info["t_done_ms"] - info["t_submit_ms"])
+                    elems += pool[i % pool_n][0].numel()
+                    t_first = info["t_submit_ms"] if t_first is None else min(t_first, info["t_submit_ms"])
+                    t_last = info["t_done_ms"] if t_last is None else max(t_last, info["t_done_ms"])
+            thr.join()
+            st = srv.stats()
+            srv.close()
+            lat = np.array(lat)
+            # served results equal the requests ranked alone (a sample)
+            exact = all(bool(torch.equal(ov, lr.rank(sc, wv))) for sc, wv, ov in pool[:min(pool_n, 16)])
+            res[mode] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
                          "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                         "elements_per_s": round(elems / ((t_last - t_first) * 1e-3), 1),
+                         "g_elem_s": round(elems / ((t_last - t_first) * 1e-3) / 1e9, 4),
                          "batches": int(st["batches"]), "ranked_alone": int(st["ranked_alone"]),
-                         "requests": int(args.requests)}
-    print(json.dumps({
+                         "exact": exact}
+        out[str(load)] = res
+    return out, {"requests": requests, "warmup": warmup, "distinct_requests": pool_n, "mean_request": mean_n,
+                 "capacity_guess_elem_s": capacity, "streams": streams}
+
+
+def run_serve(args):
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    res, info = serve_measure(args.requests, args.serve_warmup, [args.load], args.serve_streams,
+                              args.serve_capacity, dev)
+    r = res[str(args.load)]
+    print(json.dumps(dict({
         "workload": "serve", "metric": "served G list elements/s and p50/p99 latency",
-        "value": round(results["batched"]["elements_per_s"] / 1e9, 4), "unit": UNIT,
-        "batched": results["batched"], "plain": results["plain"],
-        "offered_load": args.load, "capacity_guess_elem_s": args.serve_capacity, "mean_request": mean_n,
+        "value": r["batched"]["g_elem_s"], "unit": UNIT,
+        "batched": r["batched"], "plain": r["plain"], "offered_load": args.load,
         "config": {"workload": "serving: Poisson arrivals, sizes floor(2^U) U~U[10,26], random/locality "
-                               "orders p=0.5, int64 weights, 40 GB budget, device-resident inputs "
-                               "(a pool of %d generated requests reused round-robin)" % pool_n},
-    }), flush=True)
+                               "orders p=0.5, int64 weights, 40 GB budget, device-resident inputs"}}, **info)),
+          flush=True)
 
 
 def _device_identity_order(m, dev):
@@ -700,12 +740,13 @@ def _time_call(fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def _check_recurrence(succ, w, rank, dev):
+def _check_recurrence(succ, w, rank, dev, global_succ=False):
     """Exactness at sizes the oracle cannot reach in seconds: tail 0 and
-    rank[i] = w[i] + rank[succ[i]] on every element (wrapping as int64)."""
+    rank[i] = w[i] + rank[succ[i]] on every element (wrapping as int64).
+    global_succ: succ already holds int64 global ids (a batch)."""
     import torch
     n = succ.numel()
-    sl = succ.to(torch.int64) & 0xFFFFFFFF
+    sl = succ if global_succ else succ.to(torch.int64) & 0xFFFFFFFF
     idx = torch.arange(n, device=dev)
     term = sl == idx
     r = rank.to(torch.int64)
@@ -860,6 +901,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access probe")
+    ap.add_argument("--no-batch", action="store_true", help="headline: skip the batched (config 4) object")
+    ap.add_argument("--no-serve", action="store_true", help="headline: skip the serving (config 5) object")
     ap.add_argument("--pd-sizes", default="20,22,24,26,28", help="log2 sizes of --workload pd")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "sweep", "pd", "probe"],
                     help="single: the headline (default); batch / serve: the batched and serving sets; "
