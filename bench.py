@@ -626,7 +626,8 @@ def run_batch(args):
     print(json.dumps(d), flush=True)
 
 
-def serve_measure(requests, warmup, loads, streams, capacity, dev, fresh_bytes=100e9):
+def serve_measure(requests, warmup, loads, streams, capacity, dev, fresh_bytes=100e9, lo_exp=10.0,
+                  hi_exp=26.0, alone_min_n=0):
     """Config 5: a Poisson request stream, sizes floor(2^U) with U ~ U[10,26],
     random or locality order with p = 0.5, int64 weights, 40 GB budget;
     continuous batching against plain per-request launches on the same
@@ -642,7 +643,8 @@ def serve_measure(requests, warmup, loads, streams, capacity, dev, fresh_bytes=1
     g = torch.Generator(device=dev)
     g.manual_seed(5000)
     total = requests + warmup
-    _, sizes, kinds, _ = gen.serving_trace(total, gen.config_seed(5), rate_per_s=1.0)
+    _, sizes, kinds, _ = gen.serving_trace(total, gen.config_seed(5), rate_per_s=1.0, lo_exp=lo_exp,
+                                           hi_exp=hi_exp)
     pool, used = [], 0
     for i in range(total):
         m = int(sizes[i])
@@ -662,7 +664,7 @@ def serve_measure(requests, warmup, loads, streams, capacity, dev, fresh_bytes=1
         res = {}
         for mode in ("batched", "plain"):
             srv = lr.Server(budget_bytes=40_000_000_000, n_streams=streams, max_batch=256,
-                            plain=(mode == "plain"))
+                            plain=(mode == "plain"), alone_min_n=alone_min_n)
             rate = load * capacity / mean_n
             gaps = np.random.default_rng(55).exponential(1.0 / rate, size=total)
             tickets = [None] * total
@@ -702,7 +704,8 @@ def serve_measure(requests, warmup, loads, streams, capacity, dev, fresh_bytes=1
                          "exact": exact}
         out[str(load)] = res
     return out, {"requests": requests, "warmup": warmup, "distinct_requests": pool_n, "mean_request": mean_n,
-                 "capacity_guess_elem_s": capacity, "streams": streams}
+                 "capacity_guess_elem_s": capacity, "streams": streams, "size_exp": [lo_exp, hi_exp],
+                 "alone_min_n": alone_min_n}
 
 
 def run_serve(args):
@@ -710,7 +713,8 @@ def run_serve(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
     res, info = serve_measure(args.requests, args.serve_warmup, [args.load], args.serve_streams,
-                              args.serve_capacity, dev)
+                              args.serve_capacity, dev, lo_exp=args.serve_lo, hi_exp=args.serve_hi,
+                              alone_min_n=args.serve_alone_min)
     r = res[str(args.load)]
     print(json.dumps(dict({
         "workload": "serve", "metric": "served G list elements/s and p50/p99 latency",
@@ -921,6 +925,11 @@ def main():
     ap.add_argument("--serve-streams", type=int, default=2)
     ap.add_argument("--load", type=float, default=0.8, help="serve: offered load / capacity guess")
     ap.add_argument("--serve-capacity", type=float, default=12e9, help="serve: capacity guess, elements/s")
+    ap.add_argument("--serve-lo", type=float, default=10.0, help="serve: request sizes floor(2^U), U >= this")
+    ap.add_argument("--serve-hi", type=float, default=26.0, help="serve: request sizes floor(2^U), U <= this")
+    ap.add_argument("--serve-alone-min", type=int, default=0,
+                    help="serve: requests of at least this many elements are ranked alone (0: default 2^20; "
+                         "-1: never)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
