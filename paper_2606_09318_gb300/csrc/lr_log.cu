@@ -310,6 +310,10 @@ constexpr int kSortCap = kPartTile + 6 * kMaxBuckets;   // runs padded to whole 
 constexpr int kDecodeIlp = 4;              // chunks a warp decodes with their loads in flight
 constexpr uint32_t kDead = 0xFFFFFFFFu;    // bucket region overflowed (invalid input)
 constexpr int kScatterThreads = 512;
+// The log form takes n <= 2^30: at most 2^(30 - kLgWin) windows, which two
+// partition levels of at most kMaxBuckets buckets each must cover.
+static_assert((1u << (30 - kLgWin)) <= (uint32_t)kMaxBuckets * kMaxBuckets,
+              "two partition levels must cover every window");
 
 struct PartSmem {
   uint2 sorted[kSortCap];                  // this tile's pairs, bucket by bucket
@@ -714,6 +718,9 @@ cudaError_t launch_finalize_log(LevelDesc *desc, const uint32_t *log, const uint
                                 const uint32_t *chunk_ctr, const void *r1, uint2 *pairsA, uint2 *pairsB,
                                 uint32_t *curA, uint32_t *curB, const LogGeom &g, uint32_t *rank, uint32_t *err,
                                 cudaStream_t s) {
+  // every partition writes into shared-memory tables of kMaxBuckets buckets
+  if (g.na > (uint32_t)kMaxBuckets || (g.sB > 0 && (1u << g.sB) > (uint32_t)kMaxBuckets))
+    return cudaErrorInvalidValue;
   PartOut A;
   A.out = pairsA;
   A.cur = curA;
