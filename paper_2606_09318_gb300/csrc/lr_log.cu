@@ -36,26 +36,35 @@ k_sum0(const uint32_t *__restrict__ succ, uint32_t n, unsigned long long *__rest
   unsigned long long S = 0, T = 0;
   uint32_t loc = 0;
   uint32_t bad = 0;
+  auto take = [&](uint32_t i, uint32_t s) {
+    if (s >= n) bad = 1;
+    else if (s == i) T += 1;
+    else {
+      S += s;
+      loc += (s >> kContractTileShift) == (i >> kContractTileShift);
+    }
+  };
   const uint32_t ngroups = (uint32_t)(((uint64_t)n + 3u) / 4u);
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += gridDim.x * blockDim.x) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {                                   // two 16-byte loads in flight per thread
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(succ);
+    const uint32_t nfull = n / 4u;
+    for (; (uint64_t)g + stride < nfull; g += 2 * stride) {
+      const uint4 a = __ldcs(s4 + g), b = __ldcs(s4 + g + stride);
+      const uint32_t i = g * 4u, j = (g + stride) * 4u;
+      take(i, a.x); take(i + 1, a.y); take(i + 2, a.z); take(i + 3, a.w);
+      take(j, b.x); take(j + 1, b.y); take(j + 2, b.z); take(j + 3, b.w);
+    }
+  }
+  for (; g < ngroups; g += stride) {
     const uint32_t i0 = g * 4u;
-    uint32_t s[4];
     const uint32_t cnt = min(4u, n - i0);
     if (vec && cnt == 4u) {
-      uint4 v = __ldcs(reinterpret_cast<const uint4 *>(succ + i0));
-      s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
+      const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(succ + i0));
+      take(i0, v.x); take(i0 + 1, v.y); take(i0 + 2, v.z); take(i0 + 3, v.w);
     } else {
-      for (uint32_t j = 0; j < 4u; ++j) s[j] = j < cnt ? __ldcs(succ + i0 + j) : i0 + j;
-    }
-#pragma unroll
-    for (uint32_t j = 0; j < 4u; ++j) {
-      if (j >= cnt) break;
-      if (s[j] >= n) bad = 1;
-      else if (s[j] == i0 + j) T += 1;
-      else {
-        S += s[j];
-        loc += (s[j] >> kContractTileShift) == ((i0 + j) >> kContractTileShift);
-      }
+      for (uint32_t j = 0; j < cnt; ++j) take(i0 + j, __ldcs(succ + i0 + j));
     }
   }
   for (int d = 16; d > 0; d >>= 1) {
