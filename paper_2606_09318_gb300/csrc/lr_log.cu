@@ -337,7 +337,6 @@ struct PartSmem {
   uint4 tile[kMaxBuckets];
   uint32_t tbase[kMaxBuckets];
   uint32_t wsum[32];
-  uint16_t qb[kSortCap / 4];               // bucket of every quad of `sorted`
 };
 
 // Output of one partition: bucket b owns out[b * cap, (b + 1) * cap); cur[b]
@@ -427,13 +426,17 @@ __device__ __forceinline__ void part_init(PartSmem &S, uint32_t nb) {
 }
 
 // One tile of register-held pairs (item[i].x != kLogEnd: a pair, bk[i] its
-// bucket) -> bucket runs in shared memory, laid out so that every aligned
-// quad of `sorted` is one quad of its bucket's output -> whole-sector stores.
+// bucket, which is (item[i].x >> kshift) & kmask) -> bucket runs in shared
+// memory, laid out so that every aligned quad of `sorted` is one quad of its
+// bucket's output -> whole-sector stores.  The first pair of every quad is a
+// real pair (a bucket's run is padded only to the end of its last quad), so
+// the quad's bucket is read off that pair's id.
 // The stored value is item[i].y - sub[i]: the caller may pass item[i].y
 // straight from a load still in flight, which is first used when the pair
 // is placed, after the tile's counting, scan and claims.
 __device__ void part_tile(PartSmem &S, const PartOut &P, const uint2 (&item)[kIpt],
-                          const uint32_t (&sub)[kIpt], const uint32_t (&bk)[kIpt], uint32_t &bad) {
+                          const uint32_t (&sub)[kIpt], const uint32_t (&bk)[kIpt], uint32_t kshift,
+                          uint32_t kmask, uint32_t &bad) {
   const uint32_t tid = threadIdx.x, nb = P.nb;
   uint32_t slot[kIpt];
 #pragma unroll
@@ -471,7 +474,6 @@ __device__ void part_tile(PartSmem &S, const PartOut &P, const uint2 (&item)[kIp
     S.tbase[b] = st + cc;
     S.ccnt[b] = m - full;
     for (uint32_t k = 0; k < cc; ++k) S.sorted[st + k] = S.carry[b * 4 + k];
-    for (uint32_t q = st / 4; q < (st + alloc) / 4; ++q) S.qb[q] = (uint16_t)b;
   }
   __syncthreads();
 #pragma unroll
@@ -480,7 +482,7 @@ __device__ void part_tile(PartSmem &S, const PartOut &P, const uint2 (&item)[kIp
   __syncthreads();
   const uint32_t nq = total / 4;
   for (uint32_t q = tid; q < nq; q += blockDim.x) {
-    const uint32_t b = S.qb[q];
+    const uint32_t b = (S.sorted[4 * q].x >> kshift) & kmask;
     const uint4 t = S.tile[b];
     const uint32_t k = 4 * q - (t.x & 0xFFFFu), rm = t.x >> 16;
     if (k + 4 <= rm) {
@@ -574,7 +576,7 @@ k_part_log(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ log,
     }
 #pragma unroll
     for (int i = 0; i < kIpt; ++i) bk[i] = item[i].x != kLogEnd ? item[i].x >> shift : 0u;
-    part_tile(S, P, item, off, bk, bad);
+    part_tile(S, P, item, off, bk, shift, 0xFFFFFFFFu, bad);
   }
   part_flush(S, P, bad);
   if (bad) record_error(err, bad);
@@ -618,7 +620,7 @@ k_part_win(const LevelDesc *__restrict__ desc, const uint2 *__restrict__ in, con
       bk[j] = (item[j].x >> kLgWin) & wmask;
     }
     const uint32_t zero[kIpt] = {0, 0, 0, 0, 0, 0, 0, 0};
-    part_tile(S, Q, item, zero, bk, bad);
+    part_tile(S, Q, item, zero, bk, kLgWin, wmask, bad);
   }
   part_flush(S, Q, bad);
   if (bad) record_error(err, bad);
