@@ -427,7 +427,7 @@ def run_ours(args):
         line["batch"] = batch_measure(5, 3, dev)
         torch.cuda.empty_cache()
     if ws == 1 and not args.no_serve:
-        res, info = serve_measure(300, 30, [0.8, 2.0], 2, args.serve_capacity, dev)
+        res, info = serve_measure(300, 30, [0.8, 2.0], args.serve_streams, args.serve_capacity, dev)
         line["serve"] = dict({"loads": res}, **info)
         torch.cuda.empty_cache()
     if rk == 0 and not args.no_cpu:
@@ -922,7 +922,7 @@ def main():
                     help="reference sweep: log2 size also timed in random order (0: none)")
     ap.add_argument("--oracle-reps", type=int, default=3, help="reference sweep: runs at n <= 2^24")
     ap.add_argument("--serve-warmup", type=int, default=200)
-    ap.add_argument("--serve-streams", type=int, default=2)
+    ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--load", type=float, default=0.8, help="serve: offered load / capacity guess")
     ap.add_argument("--serve-capacity", type=float, default=12e9, help="serve: capacity guess, elements/s")
     ap.add_argument("--serve-lo", type=float, default=10.0, help="serve: request sizes floor(2^U), U >= this")

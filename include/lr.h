@@ -383,7 +383,7 @@ typedef struct lr_server lr_server;
 
 typedef struct lr_server_config {
     size_t budget_bytes;     /* device memory for resident requests (default 40e9)  */
-    int32_t n_streams;       /* concurrent batches in flight (default 2)             */
+    int32_t n_streams;       /* concurrent batches in flight (default 4)             */
     int32_t max_batch;       /* most requests per launch (default 256)               */
     int64_t max_batch_elems; /* most elements per launch (default 2^28)              */
     int32_t device;          /* CUDA device ordinal (default 0)                      */

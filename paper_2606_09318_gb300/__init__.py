@@ -599,7 +599,7 @@ class Server:
     path; smaller ones that wait together are ranked as one forest.  With
     plain=True every request is ranked on its own (the baseline mode)."""
 
-    def __init__(self, budget_bytes=40_000_000_000, n_streams=2, max_batch=256,
+    def __init__(self, budget_bytes=40_000_000_000, n_streams=4, max_batch=256,
                  max_batch_elems=1 << 28, device=0, plain=False, alone_min_n=0):
         lib = load()
         c = _ServerConfig()

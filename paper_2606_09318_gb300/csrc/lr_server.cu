@@ -246,7 +246,7 @@ void lr_server_config_default(lr_server_config *c) {
   if (!c) return;
   memset(c, 0, sizeof(*c));
   c->budget_bytes = (size_t)40e9;
-  c->n_streams = 2;
+  c->n_streams = 4;
   c->max_batch = 256;
   c->max_batch_elems = (int64_t)1 << 28;
   c->device = 0;

@@ -225,7 +225,7 @@ def test_config5_served_requests_full_sizes():
     for m, kind, sd in zip(sizes, kinds, seeds):
         succ = gen.list_of_order_kind(kind, int(m), int(sd % (1 << 31)))
         reqs.append((succ, gen.weights_i64(int(m), int(sd % (1 << 31)) + 1)))
-    srv = lr.Server(budget_bytes=40_000_000_000, n_streams=2)
+    srv = lr.Server(budget_bytes=40_000_000_000)
     tickets = [srv.submit(dev(s_), dev(w_)) for s_, w_ in reqs]
     for (succ, w), t in zip(reqs, tickets):
         out, _ = srv.wait(t)
