@@ -872,6 +872,61 @@ def run_pd_compare(args):
         torch.cuda.empty_cache()
 
 
+def run_outputs(args):
+    """The extra outputs of Section 1.1 (lr_rank_outputs: terminal ids,
+    head-relative ranks, the inclusive form) against the plain rank on the
+    same list: a random list and the 2^27 forest, unweighted and with int32
+    weights (int64 ranks).  One JSON line per case; every output is checked
+    (the rank recurrence, terminals shared along each list, prefix + rank
+    equal at the terminal's total, the inclusive form = rank + the terminal's
+    weight)."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2606_09318_gb300 as lr
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(2626)
+    n = args.n
+    order = _device_random_order(n, g, dev)
+    rsucc = torch.empty(n, dtype=torch.int32, device=dev)
+    _fill_succ(rsucc, order)
+    del order
+    fs, _ = gen.forest(1 << 27, gen.config_seed(3), n_long=16, long_len=1 << 22, mean_short=64)
+    fsucc = torch.from_numpy(fs.view(np.int32)).to(dev)
+    del fs
+    for name, succ in (("random list n=%d" % n, rsucc), ("forest 2^27", fsucc)):
+        m = succ.numel()
+        for weighted in (False, True):
+            w = torch.randint(-1000, 1001, (m,), dtype=torch.int32, device=dev, generator=g) if weighted else None
+            rdt = torch.int64 if weighted else torch.int32
+            out = torch.empty(m, dtype=rdt, device=dev)
+            term = torch.empty(m, dtype=torch.int32, device=dev)
+            pre = torch.empty(m, dtype=rdt, device=dev)
+            ms_plain = _time_call(lambda: lr.rank_ex(succ, w, out=out, sync=False), args.steps, args.warmup)
+            plain = out.clone()
+            ms_ext = _time_call(lambda: lr.rank_outputs(succ, w, term=term, prefix=pre, out=out, sync=False),
+                                args.steps, args.warmup)
+            assert lr.device_status() == 0
+            sl = succ.to(torch.int64) & 0xFFFFFFFF
+            tl = term.to(torch.int64) & 0xFFFFFFFF
+            ok = bool(torch.equal(out, plain)) and _check_recurrence(succ, w, out, dev)
+            ok = ok and bool((sl[tl] == tl).all()) and bool((tl[sl] == tl).all())
+            ok = ok and bool(((pre.to(torch.int64) + out.to(torch.int64)) == pre.to(torch.int64)[tl]).all())
+            incl = torch.empty_like(out)
+            lr.rank_outputs(succ, w, term=False, prefix=False, inclusive_tail=True, out=incl)
+            wt = torch.zeros(m, dtype=torch.int64, device=dev) if w is None else w.to(torch.int64)
+            ok = ok and bool(torch.equal(incl.to(torch.int64), out.to(torch.int64) + wt[tl]))
+            print(json.dumps({"workload": "outputs", "case": name, "n": m,
+                              "weights": "int32 [-1000,1000] -> int64 ranks" if weighted else "none -> int32 ranks",
+                              "rank_ms": round(ms_plain, 3), "outputs_ms": round(ms_ext, 3),
+                              "outputs_g_elem_s": round(m / (ms_ext * 1e-3) / 1e9, 3),
+                              "overhead": round(ms_ext / ms_plain, 3), "exact": ok}), flush=True)
+            del w, out, term, pre, plain, incl, sl, tl, wt
+            torch.cuda.empty_cache()
+
+
 def run_probe_sweep(args):
     """Random-access rates of the GPU against the footprint the accesses
     cover (lr_probe_memory on buffers of 32 MiB .. 4 GiB): dependent 4-byte
@@ -908,10 +963,12 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="headline: skip the batched (config 4) object")
     ap.add_argument("--no-serve", action="store_true", help="headline: skip the serving (config 5) object")
     ap.add_argument("--pd-sizes", default="20,22,24,26,28", help="log2 sizes of --workload pd")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "serve", "sweep", "pd", "probe"],
+    ap.add_argument("--workload", default="single",
+                    choices=["single", "batch", "serve", "sweep", "pd", "probe", "outputs"],
                     help="single: the headline (default); batch / serve: the batched and serving sets; "
                          "sweep: sizes and orders; pd: against whole-list pointer doubling; "
-                         "probe: random-access rates against footprint")
+                         "probe: random-access rates against footprint; outputs: terminal ids, "
+                         "head-relative and inclusive ranks against the plain rank")
     ap.add_argument("--probe-sizes", default="25,26,27,28,29,30,31,32",
                     help="probe: log2 footprints in bytes")
     ap.add_argument("--requests", type=int, default=2000, help="serve: measured requests")
@@ -948,6 +1005,8 @@ def main():
         run_pd_compare(args)
     elif args.workload == "probe":
         run_probe_sweep(args)
+    elif args.workload == "outputs":
+        run_outputs(args)
     else:
         run_ours(args)
 
