@@ -339,9 +339,9 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         hsucc = succ.cpu().pin_memory()
-        hrank = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
-        pipe = lr.Pipeline(n, depth=2, max_lists=1)
-        for j in range(2):                                       # warm-up both slots
+        hrank = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(args.e2e_depth)]
+        pipe = lr.Pipeline(n, depth=args.e2e_depth, max_lists=1)
+        for j in range(args.e2e_depth):                          # warm-up every slot
             pipe.submit(hsucc, out=hrank[j])
         pipe.wait()
         e2e_steps = max(2, args.steps)
@@ -350,18 +350,19 @@ def run_ours(args):
             i = [0]
 
             def estep():
-                pipe.submit(hsucc, out=hrank[i[0] % 2])
+                pipe.submit(hsucc, out=hrank[i[0] % args.e2e_depth])
                 i[0] += 1
             return estep
         t = timed_steps(estep_factory(), e2e_steps, 0, dist, pipe.wait, dev)
         ref = rank.cpu()
-        if not (torch.equal(hrank[0], ref) and torch.equal(hrank[1], ref)):
+        if not all(torch.equal(h, ref) for h in hrank):
             raise RuntimeError("host-buffer pipeline disagrees with the device path")
         pipe.close()
         del hsucc, hrank, ref
         e2e = {"value": round(ws * n * e2e_steps / t / 1e9, 4), "unit": UNIT,
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n,
-               "api": "lr_pipeline (depth 2, list bound 1), pinned host buffers"}
+               "api": "lr_pipeline (depth %d, list bound 1, %d ranking stream%s), pinned host buffers"
+                      % (args.e2e_depth, 2 if args.e2e_depth >= 3 else 1, "s" if args.e2e_depth >= 3 else "")}
 
     hbm, src = measured_peaks()
     chase_ms = prof["ms_chase0"] / max(1, prof["chase0_launches"])
@@ -960,6 +961,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-probe", action="store_true", help="skip the random-access probe")
+    ap.add_argument("--e2e-depth", type=int, default=3,
+                    help="e2e: slots of the host-buffer pipeline (3 or more rank two lists at a time)")
     ap.add_argument("--no-batch", action="store_true", help="headline: skip the batched (config 4) object")
     ap.add_argument("--no-serve", action="store_true", help="headline: skip the serving (config 5) object")
     ap.add_argument("--pd-sizes", default="20,22,24,26,28", help="log2 sizes of --workload pd")

@@ -476,14 +476,17 @@ void lr_autotune_clear(void);
 /*
  * Host-buffer pipeline: ranks a sequence of HOST-resident lists (Section 1.1
  * problem, one list or forest per submission) with each list's copies
- * overlapping the ranking of its neighbours.  A pipeline owns three CUDA
- * streams on the current device (copy-in, ranking, copy-out), `depth` device
- * slots of max_n elements (successors, weights, ranks) and one engine
- * workspace, all allocated by lr_pipeline_create.  Submission j uses slot
- * j % depth; its copy-in waits
- * until the ranking of submission j - depth has read the slot, its ranking
- * waits for its copy-in and for the copy-out of submission j - depth, and
- * rankings run one after another in submission order.
+ * overlapping the ranking of its neighbours.  A pipeline owns CUDA streams
+ * on the current device (copy-in, copy-out, and one ranking stream, or two
+ * when depth >= 3), `depth` device slots of max_n elements (successors,
+ * weights, ranks) and one engine workspace per ranking stream, all allocated
+ * by lr_pipeline_create.  Submission j uses slot j % depth; its copy-in
+ * waits until the ranking of submission j - depth has read the slot, and its
+ * ranking waits for its copy-in and for the copy-out of submission j - depth.
+ * With one ranking stream rankings run one after another in submission
+ * order; with two, submission k since the last wait ranks on stream k % 2,
+ * so two rankings overlap on the device (one list's chase with the other's
+ * streaming passes), which raises throughput on large lists.
  *
  * opts (copied at create; NULL = defaults) fixes wtype, rtype, tuning,
  * validate, seed and max_lists for every submission; opts->workspace must be
@@ -495,7 +498,8 @@ void lr_autotune_clear(void);
  * submission still overlap this ranking), and the engine grows its own
  * buffers to the count.  depth: 2..4 (0 selects 2).  Device memory:
  * depth * max_n * (4 + weight bytes + rank bytes), plus
- * lr_workspace_size(max_n, 0, opts) when max_lists > 0.
+ * lr_workspace_size(max_n, 0, opts) per ranking stream when max_lists > 0
+ * (the engine's own buffers per ranking stream otherwise).
  *
  * Host buffers should be pinned (cudaHostAlloc / cudaHostRegister); pageable
  * buffers work but their copies block the submitting thread.  The caller

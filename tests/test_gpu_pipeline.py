@@ -47,10 +47,10 @@ def test_pipeline_unweighted(depth, max_lists):
     pipe.close()
 
 
-@pytest.mark.parametrize("wdt", [np.int32, np.int64])
-def test_pipeline_weighted(wdt):
+@pytest.mark.parametrize("wdt,depth", [(np.int32, 2), (np.int64, 2), (np.int64, 4)])
+def test_pipeline_weighted(wdt, depth):
     lists = _lists(7)
-    pipe = lr.Pipeline(1 << 21, wtype=wdt, depth=2)
+    pipe = lr.Pipeline(1 << 21, wtype=wdt, depth=depth)
     ws, outs = [], []
     for i, s in enumerate(lists):
         w = (gen.weights_i32 if wdt == np.int32 else gen.weights_i64)(s.shape[0], 100 + i)
@@ -63,19 +63,27 @@ def test_pipeline_weighted(wdt):
     pipe.close()
 
 
-def test_pipeline_error_index_and_neighbours():
+@pytest.mark.parametrize("depth", [2, 3])
+def test_pipeline_error_index_and_neighbours(depth):
+    # depth 3 ranks on two streams: submissions 1 and 4 fail on different
+    # streams, and the lowest index is the one reported
     n = (1 << 20) + 1
     good = gen.random_list(n, 31)
     bad = good.copy()
     bad[n // 3] = n + 9
     assert oracle.rank_status(bad)[0] == oracle.OUT_OF_RANGE
-    pipe = lr.Pipeline(n, depth=2)
+    pipe = lr.Pipeline(n, depth=depth)
     o0 = pipe.submit(pinned(good))
     pipe.submit(pinned(bad))
     o2 = pipe.submit(pinned(good))
+    if depth > 2:
+        o3 = pipe.submit(pinned(good))
+        pipe.submit(pinned(bad))
     with pytest.raises(lr.LRError) as e:
         pipe.wait()
     assert e.value.name == "LR_ERR_OUT_OF_RANGE" and e.value.index == 1
+    if depth > 2:
+        np.testing.assert_array_equal(o3.numpy(), oracle.rank(good))
     want = oracle.rank(good)
     np.testing.assert_array_equal(o0.numpy(), want)
     np.testing.assert_array_equal(o2.numpy(), want)
@@ -113,14 +121,16 @@ def test_pipeline_argument_errors():
             lr.Pipeline(1000, **bad)
 
 
-def test_pipeline_log_form_sizes():
+@pytest.mark.parametrize("depth,max_lists", [(2, 0), (3, 0), (4, 600_000)])
+def test_pipeline_log_form_sizes(depth, max_lists):
     """Lists of 2^25 and more take the log form at level 0 (auto): through the
-    pipeline's own workspace, sized by lr_workspace_size, in every slot, next
-    to smaller lists ranked with the exchange form."""
+    pipeline's own workspaces (one per ranking stream, sized by
+    lr_workspace_size with a list bound), in every slot, next to smaller
+    lists ranked with the exchange form; depth 3 and 4 rank two at a time."""
     big = (1 << 25) + 1
     lists = [gen.random_list(big, 70), gen.random_list(100_003, 71), gen.random_list(big - 64, 72),
              gen.forest(big, 73, n_long=4, long_len=1 << 20, mean_short=64)[0]]
-    pipe = lr.Pipeline(big, depth=2, max_lists=0)
+    pipe = lr.Pipeline(big, depth=depth, max_lists=max_lists)
     outs = [pipe.submit(pinned(s)) for s in lists]
     pipe.wait()
     for s, o in zip(lists, outs):
