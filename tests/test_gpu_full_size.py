@@ -26,6 +26,8 @@ checked with the full recurrence rank[i] = rank[succ i] + w[i] and rank 0 at
 every terminal, which for a valid input also determines the result, plus a
 sample of whole instances against the oracle.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -89,6 +91,43 @@ def test_config2_random_unweighted_full_size(lg):
     del rank
     want = torch.arange(n - 1, -1, -1, device="cuda", dtype=torch.int32)
     assert bool(torch.equal(got, want))
+
+
+@pytest.mark.parametrize("n", [1 << 30, (1 << 30) + 1])
+def test_log_form_size_limit(n):
+    """The log form of level 0 takes lists up to 2^30 elements; one more
+    element switches to the exchange form.  Both sides of that limit, every
+    element against the closed form."""
+    order = _device_random_order(n, 2300 + (n & 1))
+    succ = _succ_from_order(order)
+    rank = lr.rank(succ)
+    del succ
+    got = rank[order]
+    del rank
+    assert bool(torch.equal(got, torch.arange(n - 1, -1, -1, device="cuda", dtype=torch.int32)))
+
+
+def test_ids_beyond_int32_int64_ranks():
+    """A random list of 2^31 + 3 elements: successor ids above 2^31 (negative
+    as int32 views of the uint32 array), int64 ranks (an int32 rank cannot
+    hold n - 1), every element against the closed form."""
+    n = (1 << 31) + 3
+    # an affine permutation k -> (a k + b) mod n with gcd(a, n) = 1 (the
+    # device's randperm sorts at most 2^31 - 1 keys); it scatters
+    # consecutive list positions over the whole id range
+    a, b = 2654435761, 12345
+    assert math.gcd(a, n) == 1
+    order = (torch.arange(n, device="cuda", dtype=torch.int64) * a + b) % n
+    s = torch.empty(n, dtype=torch.int64, device="cuda")
+    s[order[:-1]] = order[1:]
+    s[order[-1]] = order[-1]
+    succ = (s & 0xFFFFFFFF).to(torch.int32)      # the uint32 bit pattern
+    del s
+    rank = lr.rank(succ, rank_dtype=torch.int64)
+    del succ
+    got = rank[order]
+    del rank
+    assert bool(torch.equal(got, torch.arange(n - 1, -1, -1, device="cuda", dtype=torch.int64)))
 
 
 def _weighted_closed_form(order, w):
