@@ -74,7 +74,7 @@ typedef enum lr_dtype { LR_NONE = 0, LR_I32 = 1, LR_I64 = 2 } lr_dtype;
  */
 typedef struct lr_tuning {
     uint32_t f0_inv;     /* 1/f at level 0 (default by n: 4 below 2^16, 8 below  */
-                         /* 2^22, 16 below 2^27, 64 from 2^27)                   */
+                         /* 2^22, 16 below 2^27, 48 below 2^29, 96 from 2^29)   */
     uint32_t f_inv;      /* 1/f at levels >= 1 (default 8)                       */
     uint32_t cutoff;     /* largest level ranked by the single-CTA base case     */
                          /* (default and maximum 12288)                          */

@@ -47,12 +47,14 @@ static uint32_t env_u32(const char *spec, const char *key, uint32_t dflt) {
 // order, f = 1/8 above level 0).  Small lists are bound by the latency of
 // the dependent exchanges along one segment, so they take more rulers and
 // shorter segments; from 2^27 up the chase is bound by the random-access
-// rate and 1/64 keeps the recursion smallest.
+// rate, and fewer rulers shrink the recursion more than their longer
+// segments lengthen the chase's tail (1/48 at 2^28, 1/96 at 2^30).
 static uint32_t default_f0_inv(int64_t n) {
   if (n < ((int64_t)1 << 16)) return 4;
   if (n < ((int64_t)1 << 22)) return 8;
   if (n < ((int64_t)1 << 27)) return 16;
-  return 64;
+  if (n < ((int64_t)1 << 29)) return 48;
+  return 96;
 }
 
 Tuning resolve_tuning_builtin(int64_t n, bool weighted) {
