@@ -70,6 +70,7 @@ Tuning resolve_tuning_builtin(int64_t n, bool weighted) {
   u.algo = LR_ALGO_SRS;
   u.contract = LR_CONTRACT_AUTO;
   u.spawn = 0;
+  u.ord = 1;
   return u;
 }
 
@@ -95,6 +96,7 @@ Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted, bool batch) 
   u.algo = env_u32(env, "algo", LR_ALGO_SRS);
   u.contract = env_u32(env, "contract", u.contract);
   u.spawn = env_u32(env, "spawn", u.spawn);
+  u.ord = env_u32(env, "ord", u.ord);
   if (t) {
     if (t->spawn) u.spawn = t->spawn;
     if (t->chase0) u.chase0 = t->chase0;
@@ -125,6 +127,14 @@ static bool use_log0(const Tuning &u, uint64_t n, bool weighted, int rank_bytes,
   return u.chase0 == LR_CHASE0_AUTO && n >= kLogAutoMin && !u.spawn;
 }
 
+// Level 0 of a set of contiguous instances (a batch) chases its rulers in
+// element order: a front that crosses the instances a few at a time keeps
+// the records it touches, the reduced records it writes and, in the final
+// pass, the rank gathers within a footprint the L2 holds.
+static bool use_ord0(const Tuning &u, uint64_t n, bool log0, bool spawn0, bool extras, bool multi) {
+  return u.ord != 0 && multi && !log0 && !spawn0 && !extras && n <= 0x7FFFFFFFull;
+}
+
 static uint32_t ceil_log2(uint64_t x) {
   uint32_t b = 0;
   while ((1ull << b) < x) ++b;
@@ -133,8 +143,14 @@ static uint32_t ceil_log2(uint64_t x) {
 
 static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 
-int chase_grid_for(const Tuning &u, bool rec16, bool log0) {
+// CTAs of 256 threads per SM for the chase in element order: the front's
+// width (threads x ruler spacing) must stay small enough that the instances
+// it crosses fit in L2; more threads only queue at the memory system.
+constexpr int kOrdCtasPerSm = 4;
+
+int chase_grid_for(const Tuning &u, bool rec16, bool log0, bool ord0) {
   int per = u.ctas ? (int)u.ctas : (log0 ? chase_log_occupancy((int)u.block) : chase_occupancy(rec16, (int)u.block));
+  if (ord0 && !u.ctas) per = std::min(per, kOrdCtasPerSm * 256 / (int)u.block);
   return device_sm_count() * std::max(1, per);
 }
 
@@ -150,7 +166,7 @@ static uint32_t spawn_capacity(uint64_t n, uint64_t threads) {
 
 Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,
                uint64_t seed, int chase_grid, bool force_srs, bool log0, bool term, bool t0ws,
-               bool spawn0) {
+               bool spawn0, bool ord0) {
   Plan p;
   memset(&p, 0, sizeof(p));
   p.n = n;
@@ -248,6 +264,11 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
     p.off_sctr = o; o = align_up(o + 16 + 4 * (size_t)chase_grid);
     p.off_sused = o; o = align_up(o + 4 * words);
     p.spawn_zero = o - p.off_sctr;                // counter, cursors, claimed bitmap
+  }
+  p.ord0 = ord0 && p.nlev > 1;
+  if (p.ord0) {
+    p.off_ord = o; o = align_up(o + 4 * (size_t)((n + p.f_inv[0] - 1) / p.f_inv[0]));
+    p.off_cum = o; o = align_up(o + 4 * (size_t)((n + 255) / 256));
   }
   p.term = term;
   if (term) {
@@ -647,6 +668,10 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   const bool log0 = use_log0(u, in.n, in.wtype != 0, in.rank_bytes, extras, ptrs || in.offsets != nullptr);
   const bool t0ws = extras && in.term == nullptr;
   const bool spawn0 = u.spawn != 0 && u.xchg != 0 && !log0 && !extras && !ptrs;
+  // a batch chases its level-0 rulers in element order (the has-predecessor
+  // bitmap, free once the heads are chosen, holds the ruler marks; level 1's
+  // rank array, written only after the chase, holds the order)
+  const bool ord0 = use_ord0(u, in.n, log0, spawn0, extras, ptrs || in.offsets != nullptr);
   // tile-local contraction: forced, or decided from the prep pass's count of
   // links that stay inside their tile (read with the list count, no extra wait)
   const bool contractible = u.contract != LR_CONTRACT_OFF && !in.no_contract && !ptrs &&
@@ -657,12 +682,13 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     if (cs != LR_ERR_NOT_FOUND) return cs;
   }
   const bool count_local = contractible && u.contract == LR_CONTRACT_AUTO;
-  const int grid = chase_grid_for(u, rec16_0, log0);
+  const int grid = chase_grid_for(u, rec16_0, log0, ord0);
   const bool need_count = in.max_lists <= 0 && (in.ws == nullptr || in.count_in_ws) &&
                           (in.n > u.cutoff || ptrs);
   if (need_count && capturing) return LR_ERR_CAPTURE;
   uint64_t hb = in.max_lists > 0 ? (uint64_t)in.max_lists : in.n;
-  Plan p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws, spawn0);
+  Plan p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws, spawn0,
+                     ord0);
 
   // fixed part (level 0)
   char *fixed = nullptr;
@@ -737,7 +763,8 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
       }
     }
     hb = std::max<uint64_t>(1, c->host_words[1]);
-    p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws, spawn0);
+    p = make_plan(in.n, hb, u, rec16_0, in.rank_bytes, in.seed, grid, ptrs, log0, extras, t0ws, spawn0,
+                  ord0);
   }
   if (!in.ws) {
     st = ensure_buffer(&c->var, &c->var_bytes, p.var_bytes, s);
@@ -824,14 +851,23 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     else if (l == 0 && p.spawn_cap) {
       // spawning: reduced records at uncompacted ids, then compacted into level 1
       LR_TRY(launch_chase(desc, 0, work0, r16, var + p.off_sraw, ns, qctr, p.chase_grid, p.chase_block,
-                          err, (int)u.xchg, nullptr, nullptr, &spa, s));
+                          err, (int)u.xchg, nullptr, nullptr, &spa, nullptr, s));
       LR_TRY(launch_spawn_compact(desc, 0, p.nlev, spa.ctr, spa.cap, spa.used, (uint32_t *)(var + p.off_supre),
                                   var + p.off_sraw, work_of(1), p.raw_cap, p.cutoff, p.has_pd ? 1u : 0u,
                                   err, s));
-    } else
+    } else {
+      OrdArgs oa;
+      memset(&oa, 0, sizeof(oa));
+      if (l == 0 && p.ord0) {
+        oa.ord = (uint32_t *)(var + p.off_ord);
+        oa.cum = (uint32_t *)(var + p.off_cum);
+        oa.bits = bitmap;        // the has-predecessor bitmap is free once the heads are chosen
+        LR_TRY(launch_order0(desc, (uint32_t)in.n, bcnt, &oa, hout, p.hcap, err, s));
+      }
       LR_TRY(launch_chase(desc, l, work_of(l), r16, work_of(l + 1), ns,
                           qctr + (size_t)l * p.chase_grid, p.chase_grid, p.chase_block, err,
-                          (int)u.xchg, tid_of(l), tid_of(l + 1), nullptr, s));
+                          (int)u.xchg, tid_of(l), tid_of(l + 1), nullptr, oa.ord ? &oa : nullptr, s));
+    }
     if (l == 0) prof.call.log0 = log0;
     prof.mark(l == 0 ? PH_CHASE0 : PH_CHASE);
   }
@@ -1176,9 +1212,10 @@ size_t lr_workspace_size_outputs(int64_t n_total, int32_t k, const lr_outputs *o
   const bool log0 = use_log0(u, (uint64_t)n_total, opts->wtype != LR_NONE, opts->rtype == LR_I64 ? 8 : 4,
                              extras, k != 0);
   const bool spawn0 = u.spawn != 0 && u.xchg != 0 && !log0 && !extras;
+  const bool ord0 = use_ord0(u, (uint64_t)n_total, log0, spawn0, extras, k != 0);
   Plan p = make_plan((uint64_t)n_total, h, u, opts->wtype != LR_NONE,
                      opts->rtype == LR_I64 ? 8 : 4, opts->seed, 256 * 16, false, log0, extras,
-                     extras && !outs->term, spawn0);
+                     extras && !outs->term, spawn0, ord0);
   return p.fixed_bytes + p.var_bytes;
 }
 

@@ -11,7 +11,7 @@
 namespace lr {
 
 struct Tuning {
-  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, chase0, algo, contract, spawn;
+  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, chase0, algo, contract, spawn, ord;
 };
 
 struct Plan {
@@ -38,6 +38,8 @@ struct Plan {
   uint32_t spawn_cap;               // ruler spawning at level 0: most spawned rulers (0: off)
   uint32_t raw_cap;                 //   ids of level 1 before compaction
   size_t off_sraw, off_sused, off_supre, off_sctr, off_srraw, spawn_zero;
+  bool ord0;                        // level 0 chased in element order (a batch)
+  size_t off_ord, off_cum;          // its ruler positions, rulers before every 256 positions
   bool term;                        // terminal ids carried through the levels
   size_t off_T[kMaxLevels + 1], off_tid[kMaxLevels + 1], off_T0, off_hC, off_pdt[2];
   size_t off_log, off_hdr, off_pairs, off_pairsB, off_cur;   // log path
@@ -78,8 +80,8 @@ bool tuned_lookup(int64_t n, bool weighted, bool batch, lr_tuning *out);
 // level-0 terminal ids (when the caller does not receive them).
 Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_bytes,
                uint64_t seed, int chase_grid, bool force_srs, bool log0, bool term = false,
-               bool t0ws = false, bool spawn0 = false);
-int chase_grid_for(const Tuning &u, bool rec16, bool log0);
+               bool t0ws = false, bool spawn0 = false, bool ord0 = false);
+int chase_grid_for(const Tuning &u, bool rec16, bool log0, bool ord0 = false);
 Ctx *get_ctx(cudaStream_t stream, lr_status *st);
 // Forget the context of a stream that is about to be destroyed (waits for
 // the stream, frees the context's buffers).

@@ -698,6 +698,161 @@ cudaError_t launch_heads(LevelDesc *desc, int lev, int nlev, const uint32_t *bit
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- ruler order
+// Level-0 sampled rulers in element order, for inputs made of contiguous
+// instances (a batch).  A chase that takes its rulers in this order works on
+// a few instances at a time, so the records it reads and rewrites at random
+// stay within a footprint the L2 can hold, where the default order (ruler
+// ids, i.e. random positions) touches the whole input at once.  The sampled
+// rulers are the same set (pi(x) < r); only their order and ids change: the
+// id of the ruler at position x is the number of sampled rulers before x, so
+// the reduced records and the final pass's rank gathers are local too.
+//   mark:  bit x of `bits` for every sampled ruler x = pi^{-1}(c), c < r;
+//   count: set bits per CTA (a contiguous run of words per thread);
+//   scan:  exclusive prefix of the per-CTA counts;
+//   write: each thread lists the positions of its run's set bits, in order,
+//          and the count before every 256-position block (cum).
+__global__ void __launch_bounds__(256)
+k_ord_mark(const LevelDesc *__restrict__ desc, uint32_t *__restrict__ bits) {
+  const LevelDesc d = desc[0];
+  if (d.mode != kModeSrs) return;
+  Perm P;
+  P.init(d.n, d.seed);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < d.r; c += stride) {
+    const uint32_t x = P.inv((uint32_t)c);
+    atomicOr(bits + (x >> 5), 1u << (x & 31u));
+  }
+}
+
+// Words [w0, w1) of this thread: CTA b takes a contiguous share of the words
+// and each of its threads a contiguous share of the CTA's.
+__device__ __forceinline__ void ord_run(uint32_t words, uint32_t *w0, uint32_t *w1) {
+  const uint32_t per_cta = (words + gridDim.x - 1) / gridDim.x;
+  const uint32_t c0 = blockIdx.x * per_cta;
+  const uint32_t c1 = min(words, c0 + per_cta);
+  const uint32_t per_thr = (per_cta + blockDim.x - 1) / blockDim.x;
+  *w0 = min(c1, c0 + threadIdx.x * per_thr);
+  *w1 = min(c1, *w0 + per_thr);
+}
+
+__global__ void __launch_bounds__(kHeadThreads)
+k_ord_count(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ bits, uint64_t *__restrict__ cnt) {
+  __shared__ uint64_t sm[33];
+  const LevelDesc d = desc[0];
+  if (d.mode != kModeSrs) return;
+  uint32_t w0, w1, m = 0;
+  ord_run((uint32_t)(((uint64_t)d.n + 31u) / 32u), &w0, &w1);
+  for (uint32_t w = w0; w < w1; ++w) m += __popc(__ldcg(bits + w));
+  uint64_t total;
+  block_exclusive_scan(m, sm, &total);
+  if (threadIdx.x == 0) cnt[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kHeadBlocks)
+k_ord_scan(const LevelDesc *__restrict__ desc, uint64_t *__restrict__ cnt, uint32_t *__restrict__ err) {
+  __shared__ uint64_t sm[33];
+  const LevelDesc d = desc[0];
+  if (d.mode != kModeSrs) return;
+  uint64_t total;
+  const uint64_t ex = block_exclusive_scan(cnt[threadIdx.x], sm, &total);
+  cnt[threadIdx.x] = ex;
+  if (threadIdx.x == 0 && total != d.r) record_error(err, kErrInternal);   // pi is a bijection
+}
+
+__global__ void __launch_bounds__(kHeadThreads)
+k_ord_write(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ bits,
+            const uint64_t *__restrict__ cnt, uint32_t *__restrict__ ord, uint32_t *__restrict__ cum) {
+  __shared__ uint64_t sm[33];
+  const LevelDesc d = desc[0];
+  if (d.mode != kModeSrs) return;
+  uint32_t w0, w1, m = 0;
+  ord_run((uint32_t)(((uint64_t)d.n + 31u) / 32u), &w0, &w1);
+  for (uint32_t w = w0; w < w1; ++w) m += __popc(__ldcg(bits + w));
+  uint64_t pos = cnt[blockIdx.x] + block_exclusive_scan(m, sm, nullptr);
+  for (uint32_t w = w0; w < w1; ++w) {
+    uint32_t b = __ldcg(bits + w);
+    if ((w & 7u) == 0) cum[w >> 3] = (uint32_t)pos;
+    while (b) {
+      const uint32_t i = __ffs(b) - 1;
+      b &= b - 1u;
+      if (pos < d.r) ord[pos] = w * 32u + i;
+      ++pos;
+    }
+  }
+}
+
+// Id of the sampled ruler at position y: rulers before y's 256-position
+// block plus the marks before y inside it (one 32-byte read of the block's
+// eight words).
+__device__ __forceinline__ uint32_t ord_id(const uint32_t *__restrict__ bits, const uint32_t *__restrict__ cum,
+                                           uint32_t y) {
+  const uint32_t b = y >> 8;
+  const uint4 *wp = reinterpret_cast<const uint4 *>(bits) + 2 * (size_t)b;
+  const uint4 lo = __ldcg(wp), hi = __ldcg(wp + 1);
+  uint32_t id = __ldcg(cum + b);
+  const uint32_t wi = (y >> 5) & 7u;
+  const uint32_t m = (1u << (y & 31u)) - 1u;
+  const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+  for (uint32_t i = 0; i < 8; ++i) id += __popc(i < wi ? w[i] : (i == wi ? (w[i] & m) : 0u));
+  return id;
+}
+
+// The next level's head list named the sampled heads by pi(x); give them
+// their ids in element order.
+__global__ void __launch_bounds__(256)
+k_ord_heads(const LevelDesc *__restrict__ desc, uint32_t *__restrict__ hnext, OrdArgs oa) {
+  const LevelDesc d = desc[0];
+  if (d.mode != kModeSrs) return;
+  Perm P;
+  P.init(d.n, d.seed);
+  const uint32_t h = desc[1].h;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < h; e += gridDim.x * blockDim.x) {
+    const uint32_t v = hnext[e];
+    if (v < d.r) hnext[e] = ord_id(oa.bits, oa.cum, P.inv(v));
+  }
+}
+
+cudaError_t launch_order0(LevelDesc *desc, uint32_t n, uint64_t *cnt, const OrdArgs *oa, uint32_t *hnext,
+                          uint32_t hcap, uint32_t *err, cudaStream_t s) {
+  // whole 256-position blocks, so that a lookup may read all 8 words of one
+  cudaError_t e = cudaMemsetAsync(oa->bits, 0, 32 * (((uint64_t)n + 255u) / 256u), s);
+  if (e != cudaSuccess) return e;
+  k_ord_mark<<<stream_grid(n / 8 + 1, 256), 256, 0, s>>>(desc, oa->bits);
+  k_ord_count<<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, oa->bits, cnt);
+  k_ord_scan<<<1, kHeadBlocks, 0, s>>>(desc, cnt, err);
+  k_ord_write<<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, oa->bits, cnt, oa->ord, oa->cum);
+  k_ord_heads<<<stream_grid(hcap, 256), 256, 0, s>>>(desc, hnext, *oa);
+  count_launch(5);
+  return cudaGetLastError();
+}
+
+
+// Ordered queue: CTAs draw positions of the ruler sequence from one global
+// counter, kOrdChunk at a time, and hand them to their threads one by one
+// through a shared-memory window (end << 32) | next.  The thread that draws
+// next == end refills the window; threads that draw past its end meanwhile
+// take single positions from the global counter.  Nobody waits.
+constexpr uint32_t kOrdChunk = 32;
+
+__device__ __forceinline__ uint64_t ord_take(unsigned long long *s_win, uint32_t *gq, uint64_t total) {
+  const unsigned long long w = atomicAdd(s_win, 1ull);
+  const uint32_t next = (uint32_t)w, end = (uint32_t)(w >> 32);
+  if (next < end) return next;
+  if (next == end) {
+    // the chunk is this CTA's whatever its length: every position of it
+    // must be handed out, up to the end of the sequence
+    const uint32_t j = atomicAdd(gq, kOrdChunk);
+    if (j < total) {
+      const uint64_t e = (uint64_t)j + kOrdChunk < total ? (uint64_t)j + kOrdChunk : total;
+      atomicExch(s_win, (e << 32) | (j + 1u));
+    }
+    return j;
+  }
+  return atomicAdd(gq, 1u);
+}
+
 // ---------------------------------------------------------------- chase
 // Persistent CTAs; CTA b owns a contiguous slice of ruler ids and its threads
 // pull ids one at a time from a per-CTA counter (the next id is requested
@@ -730,32 +885,64 @@ __device__ __forceinline__ Rec visit(Rec *p, uint32_t cid, uint64_t off) {
 // claimed element stops there, its next ruler; a queued head that a spawner
 // claimed first becomes a zero-weight link to the spawned ruler.  Ids that
 // were reserved but never claimed leave holes, removed after the chase.
+//
+// ORD (ord.ord != nullptr; level 0 of a batch, no spawning): the rulers come
+// in element order instead, from one global queue over the sequence
+// heads (ids r .. r+k-1, in head-list order) then ord[0 .. r) (positions of
+// the sampled rulers, ascending), so all CTAs advance one front across the
+// instances together; the sampled ruler ord[i] has id i (ord_id of its
+// position).
 template <class Rec, bool XCHG, bool TERM, bool SPAWN>
 __global__ void __launch_bounds__(512)
 k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__restrict__ next,
         const uint32_t *__restrict__ ns, uint32_t *__restrict__ qctr, uint32_t *__restrict__ err,
-        const uint32_t *__restrict__ tid_cur, uint32_t *__restrict__ tid_next, SpawnArgs sp) {
+        const uint32_t *__restrict__ tid_cur, uint32_t *__restrict__ tid_next, SpawnArgs sp,
+        OrdArgs oa) {
+  const uint32_t *__restrict__ ord = oa.ord;
+  __shared__ unsigned long long s_win;
+  if (threadIdx.x == 0) s_win = 0;
+  __syncthreads();
   const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
   const uint32_t n = d.n, r = d.r;
   const uint64_t R = (uint64_t)r + d.k;
   Perm P;
   P.init(n, d.seed);
-  const uint32_t lo = (uint32_t)(R * blockIdx.x / gridDim.x);
-  const uint32_t hi = (uint32_t)(R * (blockIdx.x + 1) / gridDim.x);
+  const uint32_t lo = ord ? 0u : (uint32_t)(R * blockIdx.x / gridDim.x);
+  const uint64_t hi = ord ? R : (uint32_t)(R * (blockIdx.x + 1) / gridDim.x);
   uint32_t *q = qctr + blockIdx.x;
+  // the next position of this thread's ruler sequence: a ruler id, or (ORD)
+  // an index of the ordered sequence
+  auto take = [&]() -> uint64_t {
+    if (ord) return ord_take(&s_win, qctr, R);
+    return (uint64_t)lo + atomicAdd(q, 1u);
+  };
+  auto ord_pos = [&](uint64_t j) -> uint32_t {
+    return (j >= d.k && j < R) ? __ldcg(ord + (j - d.k)) : 0u;
+  };
   uint32_t visited = 0, bad = 0;
   uint32_t myid = kEnd;                                  // SPAWN: reserved, not yet claimed
   const uint32_t slo = (uint32_t)((uint64_t)n * blockIdx.x / gridDim.x);
   const uint32_t shi = (uint32_t)((uint64_t)n * (blockIdx.x + 1) / gridDim.x);
-  uint64_t c64 = (uint64_t)lo + atomicAdd(q, 1u);
+  uint64_t c64 = take();
+  uint32_t xo = ord ? ord_pos(c64) : 0u;                 // ORD: position of c64's ruler, loaded ahead
   for (;;) {
     uint32_t c, rho;
     Rec v;
     if (c64 < hi) {
-      const uint64_t cnext = (uint64_t)lo + atomicAdd(q, 1u);
-      c = (uint32_t)c64;
-      rho = c < r ? P.inv(c) : __ldcg(ns + (c - r));
+      const uint64_t cnext = take();
+      if (!ord) {
+        c = (uint32_t)c64;
+        rho = c < r ? P.inv(c) : __ldcg(ns + (c - r));
+      } else if (c64 < d.k) {
+        c = r + (uint32_t)c64;
+        rho = __ldcg(ns + c64);
+        xo = ord_pos(cnext);
+      } else {
+        rho = xo;
+        c = (uint32_t)(c64 - d.k);
+        xo = ord_pos(cnext);
+      }
       v = visit<XCHG>(work + rho, c, 0);
       c64 = cnext;
       if constexpr (SPAWN) {
@@ -803,8 +990,8 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
         if (y >= n) { bad |= 4u; break; }   // never produced by prep or a chase
         const uint32_t p = P.fwd(y);
         if (p < r) {                 // reached the next ruler
-          nxt = p;
-          if (p == c) bad |= 2u;     // came back to itself: a cycle
+          nxt = ord ? ord_id(oa.bits, oa.cum, y) : p;
+          if (nxt == c) bad |= 2u;   // came back to itself: a cycle
           break;
         }
         v = visit<XCHG>(work + y, c, o);
@@ -846,14 +1033,18 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
 cudaError_t launch_chase(LevelDesc *desc, int lev, void *work, bool rec16, void *next_work,
                          const uint32_t *ns, uint32_t *qctr, int grid, int block, uint32_t *err,
                          int xchg, const uint32_t *tid_cur, uint32_t *tid_next, const SpawnArgs *spawn,
-                         cudaStream_t s) {
+                         const OrdArgs *ord, cudaStream_t s) {
+  if (ord && spawn) return cudaErrorInvalidValue;   // spawning needs the per-CTA slices
   Rec16 *nx = reinterpret_cast<Rec16 *>(next_work);
   SpawnArgs sp;
   memset(&sp, 0, sizeof(sp));
   if (spawn) sp = *spawn;
+  OrdArgs oa;
+  memset(&oa, 0, sizeof(oa));
+  if (ord) oa = *ord;
 #define LR_CHASE(REC, X, T, SP) \
   k_chase<REC, X, T, SP><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<REC *>(work), nx, ns, qctr, err, \
-                                                tid_cur, tid_next, sp)
+                                                tid_cur, tid_next, sp, oa)
   if (spawn) {
     if (rec16) LR_CHASE(Rec16, true, false, true);
     else LR_CHASE(Rec8, true, false, true);
@@ -930,6 +1121,18 @@ k_finalize(const LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ 
           out[j] = propagate<RT>(done_cid(v), done_off(v), nn, rnext, bad);
           if constexpr (TERM) cid[j] = done_cid(v);
         }
+      }
+    } else if (cnt == 4u) {
+      // all four records first, then their four gathers: two round trips
+      // per group instead of eight
+      const uint4 *p = reinterpret_cast<const uint4 *>(work + i0);
+      uint4 a[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[j] = __ldcs(p + j);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        out[j] = propagate<RT>(a[j].y, ((uint64_t)a[j].w << 32) | a[j].z, nn, rnext, bad);
+        if constexpr (TERM) cid[j] = a[j].y;
       }
     } else {
       for (uint32_t j = 0; j < cnt; ++j) {
