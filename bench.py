@@ -535,18 +535,20 @@ def _fill_succ(succ_view, order):
     succ_view[order[-1]] = order[-1].to(succ_view.dtype)
 
 
-def batch_measure(steps, warmup, dev):
+def batch_measure(steps, warmup, dev, k=1024, quick=False):
     """Config 4: 1024 independent random-order instances, sizes floor(2^U),
     U ~ U[8,22], int64 weights in [0, 2^20): one CUDA-graph replay of the
     autotuned batched call per step, against a host loop of one lr_rank_ex
     call per instance.  Returns a dict; `exact` is the full recurrence over
-    every instance plus equality with the per-instance loop."""
+    every instance plus equality with the per-instance loop.
+    k < 1024 keeps the first k of the same instances (a smaller case for
+    profiling); quick skips the autotuner and the loop (default tuning, and
+    `exact` is the recurrence alone)."""
     import numpy as np
     import torch
     import gen
     import paper_2606_09318_gb300 as lr
-    k = 1024
-    lens = gen.batch_lengths(k, gen.config_seed(4), 8.0, 22.0)
+    lens = gen.batch_lengths(1024, gen.config_seed(4), 8.0, 22.0)[:k]
     offsets = np.zeros(k + 1, dtype=np.int64)
     np.cumsum(lens, out=offsets[1:])
     n = int(offsets[-1])
@@ -559,11 +561,11 @@ def batch_measure(steps, warmup, dev):
     w = torch.randint(0, 1 << 20, (n,), dtype=torch.int64, device=dev, generator=g)
     d_off = torch.from_numpy(offsets).to(dev)
     out_b = torch.empty(n, dtype=torch.int64, device=dev)
-    out_l = torch.empty(n, dtype=torch.int64, device=dev)
+    out_l = None if quick else torch.empty(n, dtype=torch.int64, device=dev)
     # autotune the batched shape on this input (untimed); the batched call
     # below passes no tuning, so it takes the tuned entry from the table
     t_tune = time.perf_counter()
-    tuned = lr.autotune(succ=succ, weight=w, offsets=d_off, max_lists=k)
+    tuned = None if quick else lr.autotune(succ=succ, weight=w, offsets=d_off, max_lists=k)
     t_tune = time.perf_counter() - t_tune
     ws = torch.empty(lr.workspace_size(n, k, weighted=True, max_lists=k), dtype=torch.uint8, device=dev)
     s = torch.cuda.Stream()
@@ -590,6 +592,19 @@ def batch_measure(steps, warmup, dev):
 
     with torch.cuda.stream(s):
         ms_b = timed(graph.replay, steps, warmup)
+    if quick:
+        assert lr.device_status(s) == 0
+        del graph, ws
+        inst = torch.repeat_interleave(torch.arange(k, device=dev), torch.from_numpy(lens).to(dev))
+        sg = d_off[inst] + (succ.to(torch.int64) & 0xFFFFFFFF)
+        del inst
+        exact = _check_recurrence(sg, w, out_b, dev, global_succ=True)
+        return {"metric": "G list elements ranked/s, %d instances in one CUDA graph" % k,
+                "value": round(n / (ms_b * 1e-3) / 1e9, 4), "unit": UNIT, "ms_per_step": round(ms_b, 3),
+                "steps": steps, "n_total": n, "k": k, "dtype": "i64 weights, i64 ranks", "exact": exact,
+                "config": {"workload": "batched: the first %d of the 1024 random-order instances, "
+                                       "default tuning, graph-captured" % k}}
+    with torch.cuda.stream(s):
         views = [(int(offsets[j]), int(offsets[j + 1])) for j in range(k)]
 
         def loop():
@@ -606,7 +621,7 @@ def batch_measure(steps, warmup, dev):
     del inst
     exact = bool(torch.equal(out_b, out_l)) and _check_recurrence(sg, w, out_b, dev, global_succ=True)
     lr.autotune_clear()
-    return {"metric": "G list elements ranked/s, 1024 instances in one CUDA graph",
+    return {"metric": "G list elements ranked/s, %d instances in one CUDA graph" % k,
             "value": round(n / (ms_b * 1e-3) / 1e9, 4), "unit": UNIT, "ms_per_step": round(ms_b, 3),
             "steps": steps, "n_total": n, "k": k, "dtype": "i64 weights, i64 ranks", "exact": exact,
             "per_instance_loop": {"value": round(n / (ms_l * 1e-3) / 1e9, 4), "ms_per_step": round(ms_l, 3),
@@ -622,7 +637,7 @@ def run_batch(args):
     import torch
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    d = batch_measure(args.steps, args.warmup, dev)
+    d = batch_measure(args.steps, args.warmup, dev, k=args.batch_k, quick=args.batch_quick)
     d["workload"] = "batch"
     print(json.dumps(d), flush=True)
 
@@ -966,6 +981,10 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="headline: skip the batched (config 4) object")
     ap.add_argument("--no-serve", action="store_true", help="headline: skip the serving (config 5) object")
     ap.add_argument("--pd-sizes", default="20,22,24,26,28", help="log2 sizes of --workload pd")
+    ap.add_argument("--batch-k", type=int, default=1024,
+                    help="batch: rank the first K of the 1024 instances (a smaller case for profiling)")
+    ap.add_argument("--batch-quick", action="store_true",
+                    help="batch: default tuning, no autotuner and no per-instance loop")
     ap.add_argument("--workload", default="single",
                     choices=["single", "batch", "serve", "sweep", "pd", "probe", "outputs"],
                     help="single: the headline (default); batch / serve: the batched and serving sets; "

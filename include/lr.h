@@ -74,12 +74,15 @@ typedef enum lr_dtype { LR_NONE = 0, LR_I32 = 1, LR_I64 = 2 } lr_dtype;
  */
 typedef struct lr_tuning {
     uint32_t f0_inv;     /* 1/f at level 0 (default by n: 4 below 2^16, 8 below  */
-                         /* 2^22, 16 below 2^27, 48 below 2^29, 96 from 2^29)   */
+                         /* 2^22, 16 below 2^27, 48 below 2^29, 96 from 2^29;   */
+                         /* a batch keeps 16 from 2^22 up)                       */
     uint32_t f_inv;      /* 1/f at levels >= 1 (default 8)                       */
     uint32_t cutoff;     /* largest level ranked by the single-CTA base case     */
                          /* (default and maximum 12288)                          */
     uint32_t chase_block;/* threads per CTA of the chase kernel (default 256)    */
-    uint32_t chase_ctas; /* CTAs per SM of the chase kernel (default: occupancy) */
+    uint32_t chase_ctas; /* CTAs per SM of the chase kernel (default: occupancy; */
+                         /* a batch's level 0, chased in element order, 1024    */
+                         /* threads per SM)                                      */
     uint32_t algorithm;  /* LR_ALGO_SRS (0, default) or LR_ALGO_WYLLIE            */
     uint32_t contract;   /* tile-local contraction: 0 auto (default),            */
                          /* LR_CONTRACT_OFF or LR_CONTRACT_ON                     */

@@ -57,10 +57,18 @@ static uint32_t default_f0_inv(int64_t n) {
   return 96;
 }
 
-Tuning resolve_tuning_builtin(int64_t n, bool weighted) {
+// A batch chases level 0 in element order: its records stay in L2 only if
+// the front (threads x ruler spacing) is narrow, so it keeps 1/16 from 2^22
+// up (on the 1024-instance batch of 4.3e8 elements: 17.3 ms at 1/16 and
+// 1/24, 17.8 at 1/32, 18.8 at 1/48).
+static uint32_t default_f0_inv_batch(int64_t n) {
+  return n < ((int64_t)1 << 22) ? default_f0_inv(n) : 16;
+}
+
+Tuning resolve_tuning_builtin(int64_t n, bool weighted, bool batch) {
   (void)weighted;
   Tuning u;
-  u.f0_inv = default_f0_inv(n);
+  u.f0_inv = batch ? default_f0_inv_batch(n) : default_f0_inv(n);
   u.f_inv = 8;
   u.cutoff = kMaxCutoff;
   u.block = 256;
@@ -75,7 +83,7 @@ Tuning resolve_tuning_builtin(int64_t n, bool weighted) {
 }
 
 Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted, bool batch) {
-  Tuning u = resolve_tuning_builtin(n, weighted);
+  Tuning u = resolve_tuning_builtin(n, weighted, batch);
   lr_tuning tt;
   if (tuned_lookup(n, weighted, batch, &tt)) {
     if (tt.f0_inv) u.f0_inv = tt.f0_inv;
@@ -654,7 +662,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     return LR_OK;
   }
   const bool capturing = stream_capturing(s);
-  const Tuning u = in.builtin_tuning ? resolve_tuning_builtin((int64_t)in.n, in.wtype != 0)
+  const Tuning u = in.builtin_tuning ? resolve_tuning_builtin((int64_t)in.n, in.wtype != 0, false)
                                      : resolve_tuning(tuning, (int64_t)in.n, in.wtype != 0,
                                                       in.offsets != nullptr || ptrs);
   if (u.algo == LR_ALGO_WYLLIE && !ptrs) {

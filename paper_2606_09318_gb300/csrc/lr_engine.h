@@ -73,7 +73,7 @@ struct Ctx {
 // entry for (n, weighted, batch), else the built-in defaults.
 Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted, bool batch);
 // The built-in defaults alone.
-Tuning resolve_tuning_builtin(int64_t n, bool weighted);
+Tuning resolve_tuning_builtin(int64_t n, bool weighted, bool batch = false);
 // Autotuned entry for a call of this shape (lr_tune.cu).
 bool tuned_lookup(int64_t n, bool weighted, bool batch, lr_tuning *out);
 // term: also lay out the terminal-id arrays of every level; t0ws: and the

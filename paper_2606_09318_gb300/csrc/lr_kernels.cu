@@ -1091,7 +1091,7 @@ __device__ __forceinline__ uint32_t propagate_term(uint32_t c, uint32_t i, uint3
 template <class Rec, class RT, bool TERM>
 __global__ void __launch_bounds__(256)
 k_finalize(const LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ work,
-           const RT *__restrict__ rnext, RT *__restrict__ rout, uint32_t *__restrict__ err, int vec,
+           const RT *__restrict__ rnext, RT *__restrict__ rout, uint32_t *__restrict__ err,
            const uint32_t *__restrict__ tnext, uint32_t *__restrict__ tout,
            const uint32_t *__restrict__ tid_cur) {
   const LevelDesc d = desc[lev];
@@ -1099,64 +1099,38 @@ k_finalize(const LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ 
   const uint32_t n = d.n, nn = d.nraw ? d.nraw : desc[lev + 1].n;
   uint32_t bad = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0 && d.visited != n) bad |= kErrCycle;
-  const uint32_t ngroups = (uint32_t)(((uint64_t)n + 3u) / 4u);
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += stride) {
-    const uint32_t i0 = g * 4u;
-    const uint32_t cnt = min(4u, n - i0);
-    RT out[4];
-    uint32_t cid[4] = {kEnd, kEnd, kEnd, kEnd};
-    if constexpr (sizeof(Rec) == 8) {
-      if (cnt == 4u) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(work + i0);
-        uint4 a = __ldcs(p), b = __ldcs(p + 1);
-        out[0] = propagate<RT>(a.y, a.x, nn, rnext, bad);
-        out[1] = propagate<RT>(a.w, a.z, nn, rnext, bad);
-        out[2] = propagate<RT>(b.y, b.x, nn, rnext, bad);
-        out[3] = propagate<RT>(b.w, b.z, nn, rnext, bad);
-        if constexpr (TERM) { cid[0] = a.y; cid[1] = a.w; cid[2] = b.y; cid[3] = b.w; }
-      } else {
-        for (uint32_t j = 0; j < cnt; ++j) {
-          Rec v = ld_rec(work + i0 + j);
-          out[j] = propagate<RT>(done_cid(v), done_off(v), nn, rnext, bad);
-          if constexpr (TERM) cid[j] = done_cid(v);
+  // each warp takes 128 consecutive elements at a time and lane l the
+  // elements base + l + 32 j: every record load and rank store of the warp
+  // is one contiguous run, and a lane's four gathers are in flight together
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t step = ((uint64_t)gridDim.x * blockDim.x >> 5) * 128u;
+  for (uint64_t base = warp * 128u; base < n; base += step) {
+    Rec v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t i = base + lane + 32u * j;
+      if (i < n) {
+        if constexpr (sizeof(Rec) == 8) {
+          const uint2 a = __ldcs(reinterpret_cast<const uint2 *>(work + i));
+          v[j].lo = a.x;
+          v[j].hi = a.y;
+        } else {
+          const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(work + i));
+          v[j].succ = a.x;
+          v[j].tag = a.y;
+          v[j].w = ((uint64_t)a.w << 32) | a.z;
         }
       }
-    } else if (cnt == 4u) {
-      // all four records first, then their four gathers: two round trips
-      // per group instead of eight
-      const uint4 *p = reinterpret_cast<const uint4 *>(work + i0);
-      uint4 a[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) a[j] = __ldcs(p + j);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        out[j] = propagate<RT>(a[j].y, ((uint64_t)a[j].w << 32) | a[j].z, nn, rnext, bad);
-        if constexpr (TERM) cid[j] = a[j].y;
-      }
-    } else {
-      for (uint32_t j = 0; j < cnt; ++j) {
-        uint4 a = __ldcs(reinterpret_cast<const uint4 *>(work + i0 + j));
-        out[j] = propagate<RT>(a.y, ((uint64_t)a.w << 32) | a.z, nn, rnext, bad);
-        if constexpr (TERM) cid[j] = a.y;
-      }
     }
-    if constexpr (TERM) {
-      uint32_t t[4];
-      for (uint32_t j = 0; j < 4u; ++j) t[j] = j < cnt ? propagate_term(cid[j], i0 + j, nn, tnext, tid_cur) : 0u;
-      if (vec && cnt == 4u) __stcs(reinterpret_cast<uint4 *>(tout + i0), make_uint4(t[0], t[1], t[2], t[3]));
-      else for (uint32_t j = 0; j < cnt; ++j) tout[i0 + j] = t[j];
-    }
-    if (vec && cnt == 4u) {
-      if constexpr (sizeof(RT) == 4) {
-        __stcs(reinterpret_cast<uint4 *>(rout + i0), make_uint4(out[0], out[1], out[2], out[3]));
-      } else {
-        ulonglong2 *q = reinterpret_cast<ulonglong2 *>(rout + i0);
-        __stcs(q, make_ulonglong2(out[0], out[1]));
-        __stcs(q + 1, make_ulonglong2(out[2], out[3]));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t i = base + lane + 32u * j;
+      if (i < n) {
+        const RT r = propagate<RT>(done_cid(v[j]), done_off(v[j]), nn, rnext, bad);
+        if constexpr (TERM) __stcs(tout + i, propagate_term(done_cid(v[j]), (uint32_t)i, nn, tnext, tid_cur));
+        __stcs(rout + i, r);
       }
-    } else {
-      for (uint32_t j = 0; j < cnt; ++j) rout[i0 + j] = out[j];
     }
   }
   if (bad) record_error(err, bad);
@@ -1208,11 +1182,10 @@ cudaError_t launch_finalize(LevelDesc *desc, int lev, const void *work, bool rec
                             const uint32_t *tid_cur, cudaStream_t s) {
   const int block = 256;
   const int grid = stream_grid(((uint64_t)cap + 3) / 4, block);
-  const int vec = ((uintptr_t)rout & 15u) == 0 && ((uintptr_t)tout & 15u) == 0;
 #define LR_FIN(REC, RT, T)                                                                      \
   k_finalize<REC, RT, T><<<grid, block, 0, s>>>(desc, lev, reinterpret_cast<const REC *>(work), \
                                                 reinterpret_cast<const RT *>(rnext),            \
-                                                reinterpret_cast<RT *>(rout), err, vec, tnext,  \
+                                                reinterpret_cast<RT *>(rout), err, tnext,       \
                                                 tout, tid_cur)
   if (tout) {
     if (rec16) { if (rank_bytes == 4) LR_FIN(Rec16, uint32_t, true); else LR_FIN(Rec16, unsigned long long, true); }

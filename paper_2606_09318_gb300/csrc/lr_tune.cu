@@ -264,7 +264,7 @@ extern "C" lr_status lr_autotune(const uint32_t *succ, const void *weight, const
   }
 
   // reference output with the built-in defaults (table entries ignored)
-  const Tuning d = resolve_tuning_builtin(n_total, weighted);
+  const Tuning d = resolve_tuning_builtin(n_total, weighted, k > 0);
   lr_tuning best;
   memset(&best, 0, sizeof(best));
   best.f0_inv = d.f0_inv;
