@@ -78,7 +78,7 @@ Tuning resolve_tuning_builtin(int64_t n, bool weighted, bool batch) {
   u.algo = LR_ALGO_SRS;
   u.contract = LR_CONTRACT_AUTO;
   u.spawn = 0;
-  u.ord = 1;
+  u.ord = 2;              // batches: every level of 2^20 or more in element order
   return u;
 }
 
@@ -155,6 +155,10 @@ static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
 // width (threads x ruler spacing) must stay small enough that the instances
 // it crosses fit in L2; more threads only queue at the memory system.
 constexpr int kOrdCtasPerSm = 4;
+// Deeper levels of a batch keep each instance's rulers together too; from
+// this size on they are chased in order as well (LR_TUNING ord=1: level 0
+// only; ord=0: no level).
+constexpr uint32_t kOrdMinLevel = 1u << 20;
 
 int chase_grid_for(const Tuning &u, bool rec16, bool log0, bool ord0) {
   int per = u.ctas ? (int)u.ctas : (log0 ? chase_log_occupancy((int)u.block) : chase_occupancy(rec16, (int)u.block));
@@ -275,7 +279,12 @@ Plan make_plan(uint64_t n, uint64_t h, const Tuning &u, bool rec16_0, int rank_b
   }
   p.ord0 = ord0 && p.nlev > 1;
   if (p.ord0) {
-    p.off_ord = o; o = align_up(o + 4 * (size_t)((n + p.f_inv[0] - 1) / p.f_inv[0]));
+    // one set of arrays serves every level chased in order, one at a time:
+    // marks and block counts for level 0's n, positions for the most
+    // sampled rulers of any level
+    uint64_t rmax = 0;
+    for (int l = 0; l < L; ++l) rmax = std::max<uint64_t>(rmax, (p.cap[l] + p.f_inv[l] - 1) / p.f_inv[l]);
+    p.off_ord = o; o = align_up(o + 4 * (size_t)rmax);
     p.off_cum = o; o = align_up(o + 4 * (size_t)((n + 255) / 256));
   }
   p.term = term;
@@ -866,11 +875,11 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
     } else {
       OrdArgs oa;
       memset(&oa, 0, sizeof(oa));
-      if (l == 0 && p.ord0) {
+      if (p.ord0 && (l == 0 || (u.ord >= 2 && p.cap[l] >= kOrdMinLevel))) {
         oa.ord = (uint32_t *)(var + p.off_ord);
         oa.cum = (uint32_t *)(var + p.off_cum);
-        oa.bits = bitmap;        // the has-predecessor bitmap is free once the heads are chosen
-        LR_TRY(launch_order0(desc, (uint32_t)in.n, bcnt, &oa, hout, p.hcap, err, s));
+        oa.bits = bitmap;        // the has-predecessor bitmap is free once level 0's heads are chosen
+        LR_TRY(launch_order(desc, l, p.cap[l], bcnt, &oa, hout, p.hcap, err, s));
       }
       LR_TRY(launch_chase(desc, l, work_of(l), r16, work_of(l + 1), ns,
                           qctr + (size_t)l * p.chase_grid, p.chase_grid, p.chase_block, err,

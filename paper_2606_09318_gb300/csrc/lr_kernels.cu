@@ -699,8 +699,8 @@ cudaError_t launch_heads(LevelDesc *desc, int lev, int nlev, const uint32_t *bit
 }
 
 // ---------------------------------------------------------------- ruler order
-// Level-0 sampled rulers in element order, for inputs made of contiguous
-// instances (a batch).  A chase that takes its rulers in this order works on
+// Sampled rulers in element order, for inputs made of contiguous instances
+// (a batch; each of its levels keeps every instance's elements together).  A chase that takes its rulers in this order works on
 // a few instances at a time, so the records it reads and rewrites at random
 // stay within a footprint the L2 can hold, where the default order (ruler
 // ids, i.e. random positions) touches the whole input at once.  The sampled
@@ -713,8 +713,8 @@ cudaError_t launch_heads(LevelDesc *desc, int lev, int nlev, const uint32_t *bit
 //   write: each thread lists the positions of its run's set bits, in order,
 //          and the count before every 256-position block (cum).
 __global__ void __launch_bounds__(256)
-k_ord_mark(const LevelDesc *__restrict__ desc, uint32_t *__restrict__ bits) {
-  const LevelDesc d = desc[0];
+k_ord_mark(const LevelDesc *__restrict__ desc, int lev, uint32_t *__restrict__ bits) {
+  const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
   Perm P;
   P.init(d.n, d.seed);
@@ -737,9 +737,10 @@ __device__ __forceinline__ void ord_run(uint32_t words, uint32_t *w0, uint32_t *
 }
 
 __global__ void __launch_bounds__(kHeadThreads)
-k_ord_count(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ bits, uint64_t *__restrict__ cnt) {
+k_ord_count(const LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ bits,
+            uint64_t *__restrict__ cnt) {
   __shared__ uint64_t sm[33];
-  const LevelDesc d = desc[0];
+  const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
   uint32_t w0, w1, m = 0;
   ord_run((uint32_t)(((uint64_t)d.n + 31u) / 32u), &w0, &w1);
@@ -750,9 +751,9 @@ k_ord_count(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ bit
 }
 
 __global__ void __launch_bounds__(kHeadBlocks)
-k_ord_scan(const LevelDesc *__restrict__ desc, uint64_t *__restrict__ cnt, uint32_t *__restrict__ err) {
+k_ord_scan(const LevelDesc *__restrict__ desc, int lev, uint64_t *__restrict__ cnt, uint32_t *__restrict__ err) {
   __shared__ uint64_t sm[33];
-  const LevelDesc d = desc[0];
+  const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
   uint64_t total;
   const uint64_t ex = block_exclusive_scan(cnt[threadIdx.x], sm, &total);
@@ -761,10 +762,10 @@ k_ord_scan(const LevelDesc *__restrict__ desc, uint64_t *__restrict__ cnt, uint3
 }
 
 __global__ void __launch_bounds__(kHeadThreads)
-k_ord_write(const LevelDesc *__restrict__ desc, const uint32_t *__restrict__ bits,
+k_ord_write(const LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ bits,
             const uint64_t *__restrict__ cnt, uint32_t *__restrict__ ord, uint32_t *__restrict__ cum) {
   __shared__ uint64_t sm[33];
-  const LevelDesc d = desc[0];
+  const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
   uint32_t w0, w1, m = 0;
   ord_run((uint32_t)(((uint64_t)d.n + 31u) / 32u), &w0, &w1);
@@ -802,28 +803,28 @@ __device__ __forceinline__ uint32_t ord_id(const uint32_t *__restrict__ bits, co
 // The next level's head list named the sampled heads by pi(x); give them
 // their ids in element order.
 __global__ void __launch_bounds__(256)
-k_ord_heads(const LevelDesc *__restrict__ desc, uint32_t *__restrict__ hnext, OrdArgs oa) {
-  const LevelDesc d = desc[0];
+k_ord_heads(const LevelDesc *__restrict__ desc, int lev, uint32_t *__restrict__ hnext, OrdArgs oa) {
+  const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
   Perm P;
   P.init(d.n, d.seed);
-  const uint32_t h = desc[1].h;
+  const uint32_t h = desc[lev + 1].h;
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < h; e += gridDim.x * blockDim.x) {
     const uint32_t v = hnext[e];
     if (v < d.r) hnext[e] = ord_id(oa.bits, oa.cum, P.inv(v));
   }
 }
 
-cudaError_t launch_order0(LevelDesc *desc, uint32_t n, uint64_t *cnt, const OrdArgs *oa, uint32_t *hnext,
-                          uint32_t hcap, uint32_t *err, cudaStream_t s) {
+cudaError_t launch_order(LevelDesc *desc, int lev, uint32_t cap, uint64_t *cnt, const OrdArgs *oa,
+                         uint32_t *hnext, uint32_t hcap, uint32_t *err, cudaStream_t s) {
   // whole 256-position blocks, so that a lookup may read all 8 words of one
-  cudaError_t e = cudaMemsetAsync(oa->bits, 0, 32 * (((uint64_t)n + 255u) / 256u), s);
+  cudaError_t e = cudaMemsetAsync(oa->bits, 0, 32 * (((uint64_t)cap + 255u) / 256u), s);
   if (e != cudaSuccess) return e;
-  k_ord_mark<<<stream_grid(n / 8 + 1, 256), 256, 0, s>>>(desc, oa->bits);
-  k_ord_count<<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, oa->bits, cnt);
-  k_ord_scan<<<1, kHeadBlocks, 0, s>>>(desc, cnt, err);
-  k_ord_write<<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, oa->bits, cnt, oa->ord, oa->cum);
-  k_ord_heads<<<stream_grid(hcap, 256), 256, 0, s>>>(desc, hnext, *oa);
+  k_ord_mark<<<stream_grid(cap / 8 + 1, 256), 256, 0, s>>>(desc, lev, oa->bits);
+  k_ord_count<<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, lev, oa->bits, cnt);
+  k_ord_scan<<<1, kHeadBlocks, 0, s>>>(desc, lev, cnt, err);
+  k_ord_write<<<kHeadBlocks, kHeadThreads, 0, s>>>(desc, lev, oa->bits, cnt, oa->ord, oa->cum);
+  k_ord_heads<<<stream_grid(hcap, 256), 256, 0, s>>>(desc, lev, hnext, *oa);
   count_launch(5);
   return cudaGetLastError();
 }
@@ -886,7 +887,7 @@ __device__ __forceinline__ Rec visit(Rec *p, uint32_t cid, uint64_t off) {
 // claimed first becomes a zero-weight link to the spawned ruler.  Ids that
 // were reserved but never claimed leave holes, removed after the chase.
 //
-// ORD (ord.ord != nullptr; level 0 of a batch, no spawning): the rulers come
+// ORD (ord.ord != nullptr; a level of a batch, no spawning): the rulers come
 // in element order instead, from one global queue over the sequence
 // heads (ids r .. r+k-1, in head-list order) then ord[0 .. r) (positions of
 // the sampled rulers, ascending), so all CTAs advance one front across the

@@ -81,7 +81,7 @@ struct SpawnArgs {
   uint32_t *cursor;   // per CTA: candidates examined in its slice of ids
 };
 
-// Level 0 in element order (a batch): the sampled rulers' positions,
+// A level in element order (a batch): the sampled rulers' positions,
 // ascending (ord[0 .. r)), and a rank table over their marks (bits: n bits;
 // cum[b]: rulers before position 256 b), so that a sampled ruler's id is its
 // index in ord.
@@ -102,15 +102,17 @@ cudaError_t launch_spawn_scatter(LevelDesc *desc, int lev, const void *rc, void 
                                  const uint32_t *used, const uint32_t *upre, uint32_t raw_cap,
                                  cudaStream_t s);
 
-// Build the OrdArgs arrays of level 0 (bits overwritten; per-CTA counts in
-// cnt, kHeadBlocks of them) and rename the sampled heads in level 1's head
-// list (hnext, hcap entries at most).  bits must hold ceil(n / 256) * 8 words.
-cudaError_t launch_order0(LevelDesc *desc, uint32_t n, uint64_t *cnt, const OrdArgs *oa, uint32_t *hnext,
-                          uint32_t hcap, uint32_t *err, cudaStream_t s);
+// Build the OrdArgs arrays of level lev (at most cap elements; bits
+// overwritten; per-CTA counts in cnt, kHeadBlocks of them) and rename the
+// sampled heads in the next level's head list (hnext, hcap entries at most).
+// bits must hold ceil(cap / 256) * 8 words, cum ceil(cap / 256), ord the
+// level's sampled rulers.
+cudaError_t launch_order(LevelDesc *desc, int lev, uint32_t cap, uint64_t *cnt, const OrdArgs *oa,
+                         uint32_t *hnext, uint32_t hcap, uint32_t *err, cudaStream_t s);
 
 // ord: nullptr (per-CTA slices of ruler ids, sampled ids pi(x)) or
-// launch_order0's arrays: the chase takes its rulers in element order and
-// gives the sampled ones their ids in that order (level 0, no spawning).
+// launch_order's arrays: the chase takes its rulers in element order and
+// gives the sampled ones their ids in that order (no spawning).
 cudaError_t launch_chase(LevelDesc *desc, int lev, void *work, bool rec16, void *next_work,
                          const uint32_t *ns, uint32_t *qctr, int grid, int block, uint32_t *err,
                          int xchg, const uint32_t *tid_cur, uint32_t *tid_next, const SpawnArgs *spawn,
