@@ -428,7 +428,7 @@ def run_ours(args):
         line["batch"] = batch_measure(5, 3, dev)
         torch.cuda.empty_cache()
     if ws == 1 and not args.no_serve:
-        res, info = serve_measure(300, 30, [0.8, 2.0], args.serve_streams, args.serve_capacity, dev)
+        res, info = serve_measure(300, 30, [0.5, 0.8, 0.95, 2.0], args.serve_streams, args.serve_capacity, dev)
         line["serve"] = dict({"loads": res}, **info)
         torch.cuda.empty_cache()
     if rk == 0 and not args.no_cpu:
@@ -647,10 +647,12 @@ def serve_measure(requests, warmup, loads, streams, capacity, dev, fresh_bytes=1
     """Config 5: a Poisson request stream, sizes floor(2^U) with U ~ U[10,26],
     random or locality order with p = 0.5, int64 weights, 40 GB budget;
     continuous batching against plain per-request launches on the same
-    trace, at each offered load (a multiple of a capacity guess in
-    elements/s).  Requests are generated on the device before the trace,
-    every one distinct while their arrays fit `fresh_bytes` (then reused
-    round-robin).  Returns {load: {"batched": ..., "plain": ...}}."""
+    trace, at each offered load: a fraction of the batched capacity in
+    elements/s, measured first by submitting the whole trace at once
+    (capacity <= 0), or of the capacity given.  Requests are generated on
+    the device before the trace, every one distinct while their arrays fit
+    `fresh_bytes` (then reused round-robin).
+    Returns ({load: {"batched": ..., "plain": ...}}, info)."""
     import threading as th
     import numpy as np
     import torch
@@ -675,69 +677,79 @@ def serve_measure(requests, warmup, loads, streams, capacity, dev, fresh_bytes=1
         used += 20 * m
     pool_n = len(pool)
     mean_n = float(np.mean(sizes[:total]))
+
+    def run_trace(mode, gaps):
+        srv = lr.Server(budget_bytes=40_000_000_000, n_streams=streams, max_batch=256,
+                        plain=(mode == "plain"), alone_min_n=alone_min_n)
+        tickets = [None] * total
+        t_start = time.perf_counter()
+
+        def submitter():
+            t = t_start
+            for i in range(total):
+                t += gaps[i]
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                sc, wv, ov = pool[i % pool_n]
+                tickets[i] = srv.submit(sc, wv, out=ov)
+        thr = th.Thread(target=submitter)
+        thr.start()
+        lat, elems, t_first, t_last = [], 0, None, None
+        for i in range(total):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            _, info = srv.wait(tickets[i])
+            if i >= warmup:
+                lat.append(info["t_done_ms"] - info["t_submit_ms"])
+                elems += pool[i % pool_n][0].numel()
+                t_first = info["t_submit_ms"] if t_first is None else min(t_first, info["t_submit_ms"])
+                t_last = info["t_done_ms"] if t_last is None else max(t_last, info["t_done_ms"])
+        thr.join()
+        st = srv.stats()
+        srv.close()
+        lat = np.array(lat)
+        # served results equal the requests ranked alone (a sample)
+        exact = all(bool(torch.equal(ov, lr.rank(sc, wv))) for sc, wv, ov in pool[:min(pool_n, 16)])
+        return {"p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "g_elem_s": round(elems / ((t_last - t_first) * 1e-3) / 1e9, 4),
+                "batches": int(st["batches"]), "ranked_alone": int(st["ranked_alone"]),
+                "exact": exact}
+
+    measured = None
+    if capacity <= 0:
+        # saturation: the whole trace submitted at once, batched
+        measured = run_trace("batched", np.zeros(total))
+        capacity = measured["g_elem_s"] * 1e9
     out = {}
     for load in loads:
-        res = {}
-        for mode in ("batched", "plain"):
-            srv = lr.Server(budget_bytes=40_000_000_000, n_streams=streams, max_batch=256,
-                            plain=(mode == "plain"), alone_min_n=alone_min_n)
-            rate = load * capacity / mean_n
-            gaps = np.random.default_rng(55).exponential(1.0 / rate, size=total)
-            tickets = [None] * total
-            t_start = time.perf_counter()
-
-            def submitter():
-                t = t_start
-                for i in range(total):
-                    t += gaps[i]
-                    d = t - time.perf_counter()
-                    if d > 0:
-                        time.sleep(d)
-                    sc, wv, ov = pool[i % pool_n]
-                    tickets[i] = srv.submit(sc, wv, out=ov)
-            thr = th.Thread(target=submitter)
-            thr.start()
-            lat, elems, t_first, t_last = [], 0, None, None
-            for i in range(total):
-                while tickets[i] is None:
-                    time.sleep(0.0002)
-                _, info = srv.wait(tickets[i])
-                if i >= warmup:
-                    lat.append(info["t_done_ms"] - info["t_submit_ms"])
-                    elems += pool[i % pool_n][0].numel()
-                    t_first = info["t_submit_ms"] if t_first is None else min(t_first, info["t_submit_ms"])
-                    t_last = info["t_done_ms"] if t_last is None else max(t_last, info["t_done_ms"])
-            thr.join()
-            st = srv.stats()
-            srv.close()
-            lat = np.array(lat)
-            # served results equal the requests ranked alone (a sample)
-            exact = all(bool(torch.equal(ov, lr.rank(sc, wv))) for sc, wv, ov in pool[:min(pool_n, 16)])
-            res[mode] = {"p50_ms": round(float(np.percentile(lat, 50)), 3),
-                         "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                         "g_elem_s": round(elems / ((t_last - t_first) * 1e-3) / 1e9, 4),
-                         "batches": int(st["batches"]), "ranked_alone": int(st["ranked_alone"]),
-                         "exact": exact}
-        out[str(load)] = res
-    return out, {"requests": requests, "warmup": warmup, "distinct_requests": pool_n, "mean_request": mean_n,
-                 "capacity_guess_elem_s": capacity, "streams": streams, "size_exp": [lo_exp, hi_exp],
-                 "alone_min_n": alone_min_n}
+        rate = load * capacity / mean_n
+        gaps = np.random.default_rng(55).exponential(1.0 / rate, size=total)
+        out[str(load)] = {mode: run_trace(mode, gaps) for mode in ("batched", "plain")}
+    info = {"requests": requests, "warmup": warmup, "distinct_requests": pool_n, "mean_request": mean_n,
+            "capacity_elem_s": capacity, "capacity_source": "measured" if measured else "given",
+            "streams": streams, "size_exp": [lo_exp, hi_exp], "alone_min_n": alone_min_n}
+    if measured:
+        info["saturation"] = measured
+    return out, info
 
 
 def run_serve(args):
     import torch
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(0)
-    res, info = serve_measure(args.requests, args.serve_warmup, [args.load], args.serve_streams,
+    loads = [float(x) for x in str(args.load).split(",")]
+    res, info = serve_measure(args.requests, args.serve_warmup, loads, args.serve_streams,
                               args.serve_capacity, dev, lo_exp=args.serve_lo, hi_exp=args.serve_hi,
                               alone_min_n=args.serve_alone_min)
-    r = res[str(args.load)]
+    top = res[str(loads[-1])]
     print(json.dumps(dict({
         "workload": "serve", "metric": "served G list elements/s and p50/p99 latency",
-        "value": r["batched"]["g_elem_s"], "unit": UNIT,
-        "batched": r["batched"], "plain": r["plain"], "offered_load": args.load,
-        "config": {"workload": "serving: Poisson arrivals, sizes floor(2^U) U~U[10,26], random/locality "
-                               "orders p=0.5, int64 weights, 40 GB budget, device-resident inputs"}}, **info)),
+        "value": top["batched"]["g_elem_s"], "unit": UNIT, "loads": res,
+        "config": {"workload": "serving: Poisson arrivals, sizes floor(2^U) U~U[%g,%g], random/locality "
+                               "orders p=0.5, int64 weights, 40 GB budget, device-resident inputs"
+                               % (args.serve_lo, args.serve_hi)}}, **info)),
           flush=True)
 
 
@@ -1002,8 +1014,10 @@ def main():
     ap.add_argument("--oracle-reps", type=int, default=3, help="reference sweep: runs at n <= 2^24")
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-streams", type=int, default=4)
-    ap.add_argument("--load", type=float, default=0.8, help="serve: offered load / capacity guess")
-    ap.add_argument("--serve-capacity", type=float, default=12e9, help="serve: capacity guess, elements/s")
+    ap.add_argument("--load", default="0.5,0.8,0.95,2.0",
+                    help="serve: offered loads, as fractions of the capacity (comma-separated)")
+    ap.add_argument("--serve-capacity", type=float, default=0.0,
+                    help="serve: capacity in elements/s (0: measured first, the whole trace at once)")
     ap.add_argument("--serve-lo", type=float, default=10.0, help="serve: request sizes floor(2^U), U >= this")
     ap.add_argument("--serve-hi", type=float, default=26.0, help="serve: request sizes floor(2^U), U <= this")
     ap.add_argument("--serve-alone-min", type=int, default=0,
