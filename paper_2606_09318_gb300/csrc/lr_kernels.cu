@@ -725,15 +725,12 @@ k_ord_mark(const LevelDesc *__restrict__ desc, int lev, uint32_t *__restrict__ b
   }
 }
 
-// Words [w0, w1) of this thread: CTA b takes a contiguous share of the words
-// and each of its threads a contiguous share of the CTA's.
-__device__ __forceinline__ void ord_run(uint32_t words, uint32_t *w0, uint32_t *w1) {
+// Words [c0, c1) of this CTA: a contiguous share, read in tiles of one word
+// per thread (coalesced).
+__device__ __forceinline__ void ord_range(uint32_t words, uint32_t *c0, uint32_t *c1) {
   const uint32_t per_cta = (words + gridDim.x - 1) / gridDim.x;
-  const uint32_t c0 = blockIdx.x * per_cta;
-  const uint32_t c1 = min(words, c0 + per_cta);
-  const uint32_t per_thr = (per_cta + blockDim.x - 1) / blockDim.x;
-  *w0 = min(c1, c0 + threadIdx.x * per_thr);
-  *w1 = min(c1, *w0 + per_thr);
+  *c0 = min(words, blockIdx.x * per_cta);
+  *c1 = min(words, *c0 + per_cta);
 }
 
 __global__ void __launch_bounds__(kHeadThreads)
@@ -742,9 +739,9 @@ k_ord_count(const LevelDesc *__restrict__ desc, int lev, const uint32_t *__restr
   __shared__ uint64_t sm[33];
   const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
-  uint32_t w0, w1, m = 0;
-  ord_run((uint32_t)(((uint64_t)d.n + 31u) / 32u), &w0, &w1);
-  for (uint32_t w = w0; w < w1; ++w) m += __popc(__ldcg(bits + w));
+  uint32_t c0, c1, m = 0;
+  ord_range((uint32_t)(((uint64_t)d.n + 31u) / 32u), &c0, &c1);
+  for (uint32_t w = c0 + threadIdx.x; w < c1; w += blockDim.x) m += __popc(__ldcg(bits + w));
   uint64_t total;
   block_exclusive_scan(m, sm, &total);
   if (threadIdx.x == 0) cnt[blockIdx.x] = total;
@@ -761,25 +758,30 @@ k_ord_scan(const LevelDesc *__restrict__ desc, int lev, uint64_t *__restrict__ c
   if (threadIdx.x == 0 && total != d.r) record_error(err, kErrInternal);   // pi is a bijection
 }
 
+// Tile by tile: each thread one word, the tile's exclusive scan of their
+// counts, then each thread lists its word's marks in ascending order.
 __global__ void __launch_bounds__(kHeadThreads)
 k_ord_write(const LevelDesc *__restrict__ desc, int lev, const uint32_t *__restrict__ bits,
             const uint64_t *__restrict__ cnt, uint32_t *__restrict__ ord, uint32_t *__restrict__ cum) {
   __shared__ uint64_t sm[33];
   const LevelDesc d = desc[lev];
   if (d.mode != kModeSrs) return;
-  uint32_t w0, w1, m = 0;
-  ord_run((uint32_t)(((uint64_t)d.n + 31u) / 32u), &w0, &w1);
-  for (uint32_t w = w0; w < w1; ++w) m += __popc(__ldcg(bits + w));
-  uint64_t pos = cnt[blockIdx.x] + block_exclusive_scan(m, sm, nullptr);
-  for (uint32_t w = w0; w < w1; ++w) {
-    uint32_t b = __ldcg(bits + w);
-    if ((w & 7u) == 0) cum[w >> 3] = (uint32_t)pos;
+  uint32_t c0, c1;
+  ord_range((uint32_t)(((uint64_t)d.n + 31u) / 32u), &c0, &c1);
+  uint64_t base = cnt[blockIdx.x];
+  for (uint32_t t0 = c0; t0 < c1; t0 += blockDim.x) {     // uniform trip count in the CTA
+    const uint32_t w = t0 + threadIdx.x;
+    uint32_t b = w < c1 ? __ldcg(bits + w) : 0u;
+    uint64_t tile;
+    uint64_t pos = base + block_exclusive_scan(__popc(b), sm, &tile);
+    if (w < c1 && (w & 7u) == 0) cum[w >> 3] = (uint32_t)pos;
     while (b) {
       const uint32_t i = __ffs(b) - 1;
       b &= b - 1u;
       if (pos < d.r) ord[pos] = w * 32u + i;
       ++pos;
     }
+    base += tile;
   }
 }
 
