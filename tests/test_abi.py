@@ -58,6 +58,30 @@ def test_host_only_calls(lib):
     assert lr.workspace_size(0) == 0
 
 
+def test_workspace_counts_element_order_arrays(lib, monkeypatch):
+    """A batch chases its levels in element order: its workspace holds the
+    positions of the largest level's sampled rulers (4 B each) and the count
+    before every 256 positions (4 B each), each region 256-byte aligned; a
+    single list, and a batch with LR_TUNING=ord=0, hold neither.  Needs no
+    GPU."""
+    import paper_2606_09318_gb300 as lr
+    n, k = 10_000_000, 100
+    align = lambda x: (x + 255) // 256 * 256
+    monkeypatch.delenv("LR_TUNING", raising=False)
+    on = lr.workspace_size(n, k, weighted=True, max_lists=k)
+    single = lr.workspace_size(n, 0, weighted=True, max_lists=k)
+    monkeypatch.setenv("LR_TUNING", "ord=0")
+    off = lr.workspace_size(n, k, weighted=True, max_lists=k)
+    assert lr.workspace_size(n, 0, weighted=True, max_lists=k) == single
+    # a batch of 10^7 elements keeps ruler spacing 16 at level 0, the largest level
+    assert on - off == align(4 * -(-n // 16)) + align(4 * -(-n // 256))
+    # with extra outputs a batch keeps the slice order (the outputs need the bitmap)
+    monkeypatch.delenv("LR_TUNING", raising=False)
+    a = lr.workspace_size(n, k, weighted=True, max_lists=k, term=True)
+    monkeypatch.setenv("LR_TUNING", "ord=0")
+    assert lr.workspace_size(n, k, weighted=True, max_lists=k, term=True) == a
+
+
 def test_library_has_no_oracle_dependency():
     """The product path never imports, links or calls the oracle."""
     src_dir = os.path.join(ROOT, "paper_2606_09318_gb300")
