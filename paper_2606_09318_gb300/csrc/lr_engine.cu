@@ -689,8 +689,9 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   // bitmap, free once the heads are chosen, holds the ruler marks; level 1's
   // rank array, written only after the chase, holds the order)
   const bool ord0 = use_ord0(u, in.n, log0, spawn0, extras, ptrs || in.offsets != nullptr);
-  // tile-local contraction: forced, or decided from the prep pass's count of
-  // links that stay inside their tile (read with the list count, no extra wait)
+  // tile-local contraction: forced, or decided from the count of links that
+  // stay inside their tile (the log form's first pass counts them and they
+  // are read with the list count; otherwise a sample of the tiles decides)
   const bool contractible = u.contract != LR_CONTRACT_OFF && !in.no_contract && !ptrs &&
                             in.offsets == nullptr && !extras && in.ws == nullptr && in.ctx == nullptr &&
                             !capturing && in.max_lists <= 0 && in.n >= 16384 && in.n <= 0xFFFFFFFEull;
@@ -739,9 +740,27 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   if (!in.ctx) prof.begin(s, (int64_t)in.n);
   unsigned long long *acc = (unsigned long long *)(fixed + p.off_acc);
   LR_TRY(cudaMemsetAsync(fixed + p.off_zero, 0, p.zero_bytes, s));
+  // A first pass that packs records (the exchange form) would pack them in
+  // vain for an input that is then contracted: decide from a sample of the
+  // tiles first.  (The log form's first pass only reads succ, and counts
+  // every tile on the way.)
+  const bool local_exact = count_local && log0;
+  if (count_local && !log0) {
+    LR_TRY(launch_local_sample(in.succ, (uint32_t)in.n, acc + 2, s));
+    LR_TRY(cudaMemcpyAsync(c->host_words + 4, acc + 2, 16, cudaMemcpyDeviceToHost, s));
+    LR_TRY(cudaStreamSynchronize(s));
+    uint64_t smp[2];
+    memcpy(smp, c->host_words + 4, 16);
+    if (smp[0] * 2 >= smp[1]) {                // at least half the sampled links stay in their tile
+      prof.cancel();
+      const lr_status cs = run_contracted(in, tuning, c, false, s);
+      if (cs != LR_ERR_NOT_FOUND) return cs;
+      prof.begin(s, (int64_t)in.n);            // not contracted after all: carry on
+    }
+  }
   LR_TRY(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * ((in.n + 31) / 32), s));
   if (log0)
-    LR_TRY(launch_sum0(in.succ, (uint32_t)in.n, acc, count_local ? acc + 2 : nullptr, err, s));
+    LR_TRY(launch_sum0(in.succ, (uint32_t)in.n, acc, local_exact ? acc + 2 : nullptr, err, s));
   else if (ptrs)
     LR_TRY(launch_prep0_ptrs(in.sptr, in.wptr, in.wtype, (uint32_t)in.n, work0, bitmap, err,
                              in.validate, in.offsets, in.k, s));
@@ -750,8 +769,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
                              reinterpret_cast<unsigned long long *>(bitmap), s));
   else
     LR_TRY(launch_prep0(in.succ, in.weight, in.wtype, (uint32_t)in.n, work0, bitmap, err,
-                        in.validate, in.offsets, in.k, sums0 ? acc : nullptr, count_local ? acc + 2 : nullptr,
-                        s));
+                        in.validate, in.offsets, in.k, sums0 ? acc : nullptr, nullptr, s));
   if (need_count) {
     // count the lists (one wait), then size the recursion for exactly that many:
     // a single-instance pass counts terminals in its reduction, a batch adds
@@ -766,10 +784,10 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
       LR_TRY(launch_count_heads(bitmap, (uint32_t)in.n, hcount, s));
       LR_TRY(cudaMemcpyAsync(c->host_words + 1, hcount, 4, cudaMemcpyDeviceToHost, s));
     }
-    if (count_local)
+    if (local_exact)
       LR_TRY(cudaMemcpyAsync(c->host_words + 2, acc + 2, 8, cudaMemcpyDeviceToHost, s));
     LR_TRY(cudaStreamSynchronize(s));
-    if (count_local) {
+    if (local_exact) {
       uint64_t local_links;
       memcpy(&local_links, c->host_words + 2, 8);
       if (local_links * 2 >= in.n) {           // at least half the links stay in their tile

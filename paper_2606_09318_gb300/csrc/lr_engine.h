@@ -63,7 +63,8 @@ struct Ctx {
   void *contract2 = nullptr;        // and the contracted list
   size_t contract2_bytes = 0;
   uint32_t *host_words = nullptr;   // [0] device error bits, [1] head count, [2..3] tile-local
-                                    // links, [8..9] int64 scratch
+                                    // links, [4..7] sampled tile-local links and elements,
+                                    // [8..9] int64 scratch
   bool pending_status = false;
   const LevelDesc *last_desc = nullptr;   // level descriptors of the last ruling-set call
   int last_nlev = 0;

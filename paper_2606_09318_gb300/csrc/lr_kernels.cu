@@ -220,6 +220,44 @@ cudaError_t launch_prep0(const uint32_t *succ, const void *weight, int wtype, ui
   return cudaGetLastError();
 }
 
+// Links that stay inside their contraction tile, counted over every 16th
+// tile (out[0]: local links, out[1]: elements sampled).  It decides the
+// automatic tile-local contraction before a first pass that would pack
+// records the contraction does not use.
+constexpr uint32_t kLocalSampleEvery = 16;
+
+__global__ void __launch_bounds__(256)
+k_local_sample(const uint32_t *__restrict__ succ, uint32_t n, unsigned long long *__restrict__ out) {
+  constexpr uint32_t kT = 1u << kContractTileShift;
+  const uint64_t tiles = ((uint64_t)n + kT - 1) / kT;
+  const uint64_t items = (tiles + kLocalSampleEvery - 1) / kLocalSampleEvery * kT;
+  unsigned long long loc = 0, cnt = 0;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < items;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = (e / kT) * kLocalSampleEvery * kT + (e % kT);
+    if (i >= n) continue;
+    const uint32_t sx = __ldcs(succ + i);
+    cnt += 1;
+    loc += sx != (uint32_t)i && (sx >> kContractTileShift) == (uint32_t)(i >> kContractTileShift);
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    loc += __shfl_down_sync(0xFFFFFFFFu, loc, d);
+    cnt += __shfl_down_sync(0xFFFFFFFFu, cnt, d);
+  }
+  if ((threadIdx.x & 31) == 0 && cnt) {
+    atomicAdd(out, loc);
+    atomicAdd(out + 1, cnt);
+  }
+}
+
+cudaError_t launch_local_sample(const uint32_t *succ, uint32_t n, unsigned long long *out, cudaStream_t s) {
+  const uint64_t tiles = ((uint64_t)n + (1u << kContractTileShift) - 1) >> kContractTileShift;
+  const uint64_t items = (tiles + kLocalSampleEvery - 1) / kLocalSampleEvery << kContractTileShift;
+  k_local_sample<<<stream_grid(items, 256), 256, 0, s>>>(succ, n, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // Batched prep without per-element atomics.  Each instance j of a batch that
 // is one list has exactly one terminal, and its successors are every local id
 // but the head's, so head_j = n_j (n_j - 1) / 2 - sum of its non-terminal

@@ -61,6 +61,9 @@ cudaError_t launch_finalize_ptrs(LevelDesc *desc, const void *work, bool rec16, 
                                  const int64_t *offsets, int32_t k, uint32_t *err, cudaStream_t s);
 
 cudaError_t launch_count_heads(const uint32_t *bitmap, uint32_t n, uint32_t *out, cudaStream_t s);
+// Tile-local links over a sample of the contraction tiles: out[0] += local
+// links, out[1] += elements sampled.
+cudaError_t launch_local_sample(const uint32_t *succ, uint32_t n, unsigned long long *out, cudaStream_t s);
 
 // Head selection of level `lev` (reads the bitmap at level 0, the head list
 // otherwise), then the exclusive scan and the writes.
