@@ -30,8 +30,9 @@
 // Passes: solve (every tile in shared memory: distances to the local tails,
 // the local-head bitmap), scan (tile prefixes), nodes (the contracted
 // list), the ruling set on the contracted list, tails and fix (the ranks).
-// Whether to contract is decided by the caller from the prep pass's count
-// of links that stay inside their tile.
+// Whether to contract is decided by the caller from the count of links that
+// stay inside their tile: exact from the log form's first pass, or from a
+// sample of the tiles before a first pass that would pack records.
 #include <algorithm>
 #include <cstddef>
 #include <cuda_runtime.h>
