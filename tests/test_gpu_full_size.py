@@ -253,6 +253,37 @@ def test_config4_batch_1024_in_cuda_graph():
     lr.autotune_clear()                                      # leave no tuned entry behind
 
 
+@pytest.mark.parametrize("total", [(1 << 31) - 4, (1 << 31) + 4])
+def test_batch_order_limit_2p31(total):
+    """A batch of four unweighted instances of about 2^29 elements each, just
+    below 2^31 elements in all (levels chased in element order, the largest
+    size that takes it) and just above (per-CTA slices of ruler ids), int64
+    ranks: every element against its instance's closed form.  Each instance
+    is an affine order k -> (a k + b) mod m (gcd(a, m) = 1) of its local ids,
+    so no permutation of 2^29 has to be drawn."""
+    k = 4
+    m = [total // k + (1 if j < total % k else 0) for j in range(k)]
+    offsets = np.zeros(k + 1, dtype=np.int64)
+    np.cumsum(m, out=offsets[1:])
+    a, b = 2654435761, 12345
+    succ = torch.empty(total, dtype=torch.int32, device="cuda")
+    for j in range(k):
+        assert math.gcd(a, m[j]) == 1
+        order = (torch.arange(m[j], device="cuda", dtype=torch.int64) * a + b) % m[j]
+        loc = torch.empty(m[j], dtype=torch.int64, device="cuda")
+        loc[order[:-1]] = order[1:]
+        loc[order[-1]] = order[-1]
+        succ[int(offsets[j]):int(offsets[j + 1])] = loc.to(torch.int32)
+        del order, loc
+    rank = lr.rank_batch(dev(offsets), succ, rank_dtype=torch.int64, max_lists=k)
+    del succ
+    for j in range(k):
+        order = (torch.arange(m[j], device="cuda", dtype=torch.int64) * a + b) % m[j]
+        got = rank[int(offsets[j]):int(offsets[j + 1])][order]
+        assert bool(torch.equal(got, torch.arange(m[j] - 1, -1, -1, device="cuda", dtype=torch.int64))), j
+        del order, got
+
+
 def test_config5_served_requests_full_sizes():
     """Config 5: requests of 2^10 .. 2^26 elements, random or locality order,
     int64 weights, served by continuous batching under a 40 GB budget.  Each
