@@ -95,11 +95,17 @@ struct LcMarks {
   uint32_t pred[kTileWords]; // has-local-predecessor bitmap
   uint32_t tail[kTileWords]; // local-tail bitmap (wide int64 tiles only)
   uint32_t nlinks, nmarked;  // local links; marked elements
+  uint32_t wflags;           // over the tile's local links: kWBig19 | kWNeg | kWBig20
 };
+// A tile whose local-link weights all lie in (-2^19, 2^19), or all in
+// [0, 2^20), has every distance (at most kTile - 1 links) within 32 bits,
+// signed or unsigned: its prefix sums are taken modulo 2^32.
+constexpr uint32_t kWBig19 = 1u, kWNeg = 2u, kWBig20 = 4u;
 struct LcPos {
   union {
     uint32_t pk[2][kTile];   // the doubling's words, double-buffered
     uint64_t P[kTile];       // then the weights by list position, and their prefix sums
+    uint32_t P32[kTile];     // the same modulo 2^32 (a narrow tile)
   };
   int32_t w[kTile];          // each element's link weight (0 for a local tail)
   uint16_t E[kTile];         // list position of each local tail
@@ -165,6 +171,7 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
   const uint32_t tid = threadIdx.x;
   uint32_t x[kLcRuns][4];      // d << 16 | settled | p
   uint32_t links = 0;
+  uint32_t wfl = 0;            // weighted: this thread's kWBig19 | kWNeg | kWBig20
   // int64 weights: does any weight of the tile leave the int32 range?
   bool wide = false;
   if constexpr (WT == 2) {
@@ -216,7 +223,12 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
       const bool local = j < len && s[e] < n && s[e] != i && (s[e] >> kTileShift) == t;
       p[r][e] = local ? s[e] - base : j;
       x[r][e] = (local ? 1u << 16 : kLcSettled) | p[r][e];
-      if constexpr (WT != 0) d[r][e] = local ? w[e] : 0u;   // exact in int32 unless the tile is wide
+      if constexpr (WT != 0) {
+        d[r][e] = local ? w[e] : 0u;   // exact in int32 unless the tile is wide
+        const int64_t wv = (int64_t)d[r][e];
+        wfl |= ((uint64_t)(wv + (1 << 19)) >= (1u << 20) ? kWBig19 : 0u) | (wv < 0 ? kWNeg : 0u) |
+               ((uint64_t)wv >= (1u << 20) ? kWBig20 : 0u);
+      }
       if (local) {
         S.m.mark[s[e] - base] = 1;
         ++links;
@@ -238,6 +250,10 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
   }
   links = __reduce_add_sync(0xFFFFFFFFu, links);
   if ((tid & 31u) == 0 && links) atomicAdd(&S.m.nlinks, links);
+  if constexpr (WT != 0) {
+    wfl = __reduce_or_sync(0xFFFFFFFFu, wfl);
+    if ((tid & 31u) == 0 && wfl) atomicOr(&S.m.wflags, wfl);
+  }
   __syncthreads();
   // marks -> bitmap: eight marks per thread, four threads per word; the
   // marks are cleared for the next tile as they are read
@@ -319,6 +335,9 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
           }
       }
       __syncthreads();                       // E is written; the doubling's buffers are free
+      const uint32_t wf = S.m.wflags;
+      const bool nsig = !(wf & kWBig19), nuns = !(wf & (kWNeg | kWBig20));
+      const bool narrow = nsig || nuns;
       if (fits) {
         // weights by position (a tail's own link does not count); ids past
         // the end of the last tile are lone tails of no sublist
@@ -329,12 +348,26 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
             const uint32_t j = r * kLcRunStride + 4 * tid + e;
             if (j < len && p[r][e] != kEnd16) {
               const uint32_t pos = ((uint32_t)S.q.E[p[r][e]] - (x[r][e] >> 16)) & kLcPtrMask;
-              S.q.P[pos] = (uint64_t)(int64_t)S.q.w[j];
+              if (narrow) S.q.P32[pos] = (uint32_t)S.q.w[j];
+              else S.q.P[pos] = (uint64_t)(int64_t)S.q.w[j];
             }
           }
       }
       __syncthreads();
-      if (fits) {
+      if (fits && narrow) {
+        // inclusive prefix sums modulo 2^32 over the positions, 8 per thread
+        uint32_t v[8];
+        const uint4 *src = reinterpret_cast<const uint4 *>(&S.q.P32[8 * tid]);
+        const uint4 u0 = src[0], u1 = src[1];
+        v[0] = u0.x; v[1] = u0.y; v[2] = u0.z; v[3] = u0.w;
+        v[4] = u1.x; v[5] = u1.y; v[6] = u1.z; v[7] = u1.w;
+#pragma unroll
+        for (int q = 1; q < 8; ++q) v[q] += v[q - 1];
+        const uint32_t off = (uint32_t)block_exclusive_scan((uint64_t)v[7], scan_sm, nullptr);
+        uint4 *dst = reinterpret_cast<uint4 *>(&S.q.P32[8 * tid]);
+        dst[0] = make_uint4(v[0] + off, v[1] + off, v[2] + off, v[3] + off);
+        dst[1] = make_uint4(v[4] + off, v[5] + off, v[6] + off, v[7] + off);
+      } else if (fits) {
         // inclusive prefix sums over the positions, 8 per thread
         uint64_t v[8];
         const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(&S.q.P[8 * tid]);
@@ -363,7 +396,12 @@ __device__ void lc_tile_solve(LcTile<WT> &S, uint32_t t, uint32_t len, const uin
           if (fits && p[r][e] != kEnd16 && r * kLcRunStride + 4 * tid + e < len) {
             const uint32_t last = S.q.E[p[r][e]] & kLcPtrMask;
             const uint32_t pos = (last - (x[r][e] >> 16)) & kLcPtrMask;
-            d[r][e] = S.q.P[last] - (pos ? S.q.P[pos - 1] : 0u);
+            if (narrow) {
+              const uint32_t d32 = S.q.P32[last] - (pos ? S.q.P32[pos - 1] : 0u);
+              d[r][e] = nsig ? (uint64_t)(int64_t)(int32_t)d32 : (uint64_t)d32;
+            } else {
+              d[r][e] = S.q.P[last] - (pos ? S.q.P[pos - 1] : 0u);
+            }
           }
         }
     }
@@ -429,7 +467,7 @@ k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, u
   const uint32_t ntiles = (n + kTile - 1) >> kTileShift;
   for (uint32_t j = threadIdx.x; j < kTile / 4; j += blockDim.x) reinterpret_cast<uint32_t *>(S.m.mark)[j] = 0;
   for (uint32_t w = threadIdx.x; w < kTileWords; w += blockDim.x) S.m.tail[w] = 0;
-  if (threadIdx.x == 0) { S.m.nlinks = 0; S.m.nmarked = 0; }
+  if (threadIdx.x == 0) { S.m.nlinks = 0; S.m.nmarked = 0; S.m.wflags = 0; }
   __syncthreads();
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const uint32_t base = t << kTileShift;
@@ -499,7 +537,7 @@ k_lc_solve(const uint32_t *__restrict__ succ, const void *__restrict__ weight, u
     __syncthreads();
     if constexpr (WT == 2)
       for (uint32_t w = threadIdx.x; w < kTileWords; w += blockDim.x) S.m.tail[w] = 0;
-    if (threadIdx.x == 0) { S.m.nlinks = 0; S.m.nmarked = 0; }
+    if (threadIdx.x == 0) { S.m.nlinks = 0; S.m.nmarked = 0; S.m.wflags = 0; }
     __syncthreads();
   }
 }

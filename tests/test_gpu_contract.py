@@ -114,6 +114,35 @@ def test_weighted_int64_mixed_tiles():
     assert got == "LR_ERR_CYCLE"
 
 
+@pytest.mark.parametrize("wdt", [np.int32, np.int64])
+def test_weighted_narrow_limits(wdt):
+    # A tile whose weights all lie in (-2^19, 2^19), or all in [0, 2^20),
+    # takes its in-tile prefix sums modulo 2^32; identity order makes every
+    # tile one chain of 4095 local links, so its distances reach 4095 times
+    # the weight: just inside 2^31 (signed) and 2^32 (unsigned).  A tile with
+    # one weight past either limit takes 64-bit sums.
+    n = 6 * TILE + 11
+    succ = gen.identity_list(n)
+    w = np.zeros(n, dtype=np.int64)
+    w[0 * TILE:1 * TILE] = (1 << 19) - 1                 # signed limit
+    w[1 * TILE:2 * TILE] = -((1 << 19) - 1)
+    w[2 * TILE:3 * TILE] = (1 << 20) - 1                 # unsigned limit
+    w[3 * TILE:4 * TILE] = (1 << 19) - 1
+    w[3 * TILE + 5] = -(1 << 19)                         # just past the signed limit, negative: 64-bit
+    w[4 * TILE:5 * TILE] = (1 << 20) - 1
+    w[4 * TILE + 9] = 1 << 20                            # just past the unsigned limit: 64-bit
+    rng = np.random.default_rng(514)
+    w[5 * TILE:] = rng.integers(-(1 << 19) + 1, 1 << 19, size=n - 5 * TILE)
+    w = w.astype(wdt)
+    want = oracle.rank(succ, w, np.int64)
+    for t in (None, ON):
+        np.testing.assert_array_equal(rank(succ, w, torch.int64, tuning=t), want)
+    # locality order: many short local sublists per tile, same weights
+    succ = gen.locality_list(n, 515)
+    want = oracle.rank(succ, w, np.int64)
+    np.testing.assert_array_equal(rank(succ, w, torch.int64, tuning=ON), want)
+
+
 def test_euler_tour_forced():
     parent = gen.random_recursive_tree(1 << 16, 508)
     succ, w = gen.euler_tour(parent)
