@@ -159,3 +159,26 @@ def test_request_forest_in_order(monkeypatch):
             np.testing.assert_array_equal(got, oracle.rank(s, w, np.int64))
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("tuning", ["ord=2,f0=8", "ord=0,f0=8"])
+def test_batch_order_with_validation(monkeypatch, tuning):
+    # validation marks predecessors with a bitmap during the first pass (the
+    # element order then reuses that bitmap for its ruler marks)
+    monkeypatch.setenv("LR_TUNING", tuning)
+    lens = _lens(46, 120, 14.0)
+    offsets, succ = _batch(lens, 4700, forest_at=(3,))
+    n = int(offsets[-1])
+    w = gen.weights_i64(n, 4701)
+    for ml in (0, 200):
+        got = lr.rank_batch(dev(offsets), dev(succ), dev(w), validate=True, max_lists=ml).cpu().numpy()
+        np.testing.assert_array_equal(got, oracle.rank_batch(offsets, succ, w, np.int64))
+    j = int(np.argmax(lens))
+    a, m = int(offsets[j]), int(lens[j])
+    bad = succ.copy()
+    tgt = int(bad[a])
+    i = next(i for i in range(m) if bad[a + i] != tgt and bad[a + i] != i)
+    bad[a + i] = tgt                                           # two predecessors
+    with pytest.raises(lr.LRError) as e:
+        lr.rank_batch(dev(offsets), dev(bad), dev(w), validate=True)
+    assert e.value.name == "LR_ERR_NOT_A_LIST"
