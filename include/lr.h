@@ -71,6 +71,14 @@ typedef enum lr_dtype { LR_NONE = 0, LR_I32 = 1, LR_I64 = 2 } lr_dtype;
 /*
  * Tuning knobs of the ruling-set recursion (filled by the autotuner; zero
  * fields take the built-in defaults).  Rulers per level: ceil(n / f_inv).
+ *
+ * LR_TUNING (environment, read at every call that has no explicit
+ * lr_tuning field set) overrides them for measurement, as comma-separated
+ * key=value pairs: f0, f, cutoff, block, ctas (the fields below); xchg=0
+ * (visits by load and store instead of an atomic exchange); log=0 / log=1
+ * (force the level-0 form); algo, contract, spawn; ord (batches: 0 chases
+ * by per-CTA slices of ruler ids, 1 takes level 0's rulers in element
+ * order, 2, the default, every level of 2^20 elements or more).
  */
 typedef struct lr_tuning {
     uint32_t f0_inv;     /* 1/f at level 0 (default by n: 4 below 2^16, 8 below  */
