@@ -72,8 +72,8 @@ typedef enum lr_dtype { LR_NONE = 0, LR_I32 = 1, LR_I64 = 2 } lr_dtype;
  * Tuning knobs of the ruling-set recursion (filled by the autotuner; zero
  * fields take the built-in defaults).  Rulers per level: ceil(n / f_inv).
  *
- * LR_TUNING (environment, read at every call that has no explicit
- * lr_tuning field set) overrides them for measurement, as comma-separated
+ * LR_TUNING (environment, read at every call; a nonzero field of an
+ * explicit lr_tuning takes precedence) overrides them for measurement, as comma-separated
  * key=value pairs: f0, f, cutoff, block, ctas (the fields below); xchg=0
  * (visits by load and store instead of an atomic exchange); log=0 / log=1
  * (force the level-0 form); algo, contract, spawn; ord (batches: 0 chases
