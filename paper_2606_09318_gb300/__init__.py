@@ -21,7 +21,10 @@ __all__ = [
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "_build", "liblr.so")
+# LR_DEBUG_LIB=1: the debug build (build.py, debug=True), whose kernels check
+# the indices they derive and report a failed check instead of faulting
+_LIB_PATH = (os.path.join(_HERE, "_build_debug", "liblr_debug.so") if os.environ.get("LR_DEBUG_LIB") == "1"
+             else os.path.join(_HERE, "_build", "liblr.so"))
 
 STATUS = {
     0: "LR_OK", 1: "LR_ERR_INVALID_ARGUMENT", 2: "LR_ERR_OUT_OF_RANGE", 3: "LR_ERR_CYCLE",

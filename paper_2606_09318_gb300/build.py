@@ -2,6 +2,11 @@
 
 Translation units compile in parallel; the shared library links against the
 static CUDA runtime so it only needs the driver at load time.
+
+build(debug=True) builds _build_debug/liblr_debug.so with -DLR_DEBUG: the
+kernels check the indices they derive before using them and report a failed
+check as LR_ERR_INTERNAL instead of faulting.  The Python binding loads it
+when LR_DEBUG_LIB=1 is set before import.
 """
 import os
 import subprocess
@@ -13,6 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblr.so")
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT_DEBUG, "liblr_debug.so")
 SOURCES = ["lr_kernels.cu", "lr_log.cu", "lr_engine.cu", "lr_server.cu", "lr_noalloc.cu", "lr_probe.cu", "lr_pipeline.cu", "lr_wyllie.cu", "lr_tune.cu", "lr_contract.cu"]
 HEADERS = ["lr_device.cuh", "lr_kernels.h", "lr_engine.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -34,14 +41,17 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    os.makedirs(OUT, exist_ok=True)
+def build(force=False, verbose=False, extra_flags=(), debug=False):
+    out, lib = (OUT_DEBUG, LIB_DEBUG) if debug else (OUT, LIB)
+    if debug:
+        extra_flags = tuple(extra_flags) + ("-DLR_DEBUG",)
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "lr.h")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(OUT, src.replace(".cu", ".o"))
+        o = os.path.join(out, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             jobs.append([nvcc] + ARCH + FLAGS + list(extra_flags) + ["-c", s, "-o", o])
@@ -58,12 +68,12 @@ def build(force=False, verbose=False, extra_flags=()):
         for msg in ex.map(run, jobs):
             if verbose and msg:
                 print(msg, file=sys.stderr)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp.%d" % os.getpid()
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp.%d" % os.getpid()
         run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

@@ -32,7 +32,20 @@ enum : uint32_t {
   kErrNotList = 4u,    // an element with two predecessors
   kErrCapacity = 8u,   // more rulers than the static plan provided for
   kErrInternal = 16u,  // a record or id the pipeline never produces
+  kErrDebug = 32u,     // a debug build's index check failed (LR_DEBUG)
 };
+
+// Debug build (-DLR_DEBUG, build.py's debug=True): the kernels check the
+// indices they derive from their own structures (a ruler's position, a
+// reduced record's id, a queue position) before using them; a failed check
+// records kErrDebug and skips the access instead of faulting, which makes
+// the build a stand-in for a memory checker.  Without LR_DEBUG every check
+// folds away.
+#ifdef LR_DEBUG
+constexpr bool kDebugChecks = true;
+#else
+constexpr bool kDebugChecks = false;
+#endif
 
 // per-level mode, decided on the device by the previous level
 enum : uint32_t { kModeOff = 0, kModeSrs = 1, kModeBase = 2, kModePd = 3 };
@@ -138,6 +151,15 @@ struct __align__(16) Rec16 {
 
 __device__ __forceinline__ void record_error(uint32_t *err, uint32_t bits) {
   atomicOr(err, bits);
+}
+
+// True (after recording kErrDebug) when a debug build's check fails.
+__device__ __forceinline__ bool dbg_fail(bool ok, uint32_t *err) {
+  if (kDebugChecks && !ok) {
+    atomicOr(err, kErrDebug);
+    return true;
+  }
+  return false;
 }
 
 // L2-only loads/stores for data with no reuse in L1.

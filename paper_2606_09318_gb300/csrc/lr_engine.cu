@@ -386,7 +386,17 @@ static bool stream_capturing(cudaStream_t s) {
 }
 
 // Grow-only device buffer.
+// Fault injection on the host (tests): with LR_INJECT_ALLOC_FAIL=1 in the
+// environment every request for library workspace fails as a cudaMalloc
+// that ran out of memory would, whether or not the arena had to grow, and
+// without calling it.
+static bool inject_alloc_failure() {
+  const char *v = getenv("LR_INJECT_ALLOC_FAIL");
+  return v && v[0] == '1';
+}
+
 lr_status ensure_buffer(void **buf, size_t *cur, size_t want, cudaStream_t s) {
+  if (inject_alloc_failure()) return LR_ERR_OUT_OF_MEMORY;
   if (*cur >= want && *buf) return LR_OK;
   if (stream_capturing(s)) return LR_ERR_CAPTURE;
   if (*buf) {
@@ -498,6 +508,7 @@ struct Inputs {
 };
 
 static lr_status map_device_bits(uint32_t bits) {
+  if (bits & kErrDebug) return LR_ERR_INTERNAL;      // a debug build's index check
   if (bits & kErrRange) return LR_ERR_OUT_OF_RANGE;
   if (bits & kErrNotList) return LR_ERR_NOT_A_LIST;
   if (bits & kErrCycle) return LR_ERR_CYCLE;

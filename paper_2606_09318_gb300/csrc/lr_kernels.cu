@@ -961,6 +961,7 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
   auto ord_pos = [&](uint64_t j) -> uint32_t {
     return (j >= d.k && j < R) ? __ldcg(ord + (j - d.k)) : 0u;
   };
+  const uint32_t ncap = desc[lev + 1].cap;             // records of the next level (debug checks)
   uint32_t visited = 0, bad = 0;
   uint32_t myid = kEnd;                                  // SPAWN: reserved, not yet claimed
   const uint32_t slo = (uint32_t)((uint64_t)n * blockIdx.x / gridDim.x);
@@ -984,8 +985,9 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
         c = (uint32_t)(c64 - d.k);
         xo = ord_pos(cnext);
       }
-      v = visit<XCHG>(work + rho, c, 0);
       c64 = cnext;
+      if (dbg_fail(rho < n && c < ncap, err)) continue;
+      v = visit<XCHG>(work + rho, c, 0);
       if constexpr (SPAWN) {
         if (rec_is_claim(v)) {                           // a spawner took this head first
           const uint32_t cs = rec_tag(v);
@@ -1032,6 +1034,7 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
         const uint32_t p = P.fwd(y);
         if (p < r) {                 // reached the next ruler
           nxt = ord ? ord_id(oa.bits, oa.cum, y) : p;
+          if (dbg_fail(nxt < r, err)) nxt = c;
           if (nxt == c) bad |= 2u;   // came back to itself: a cycle
           break;
         }

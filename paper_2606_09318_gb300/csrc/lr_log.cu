@@ -236,6 +236,7 @@ k_chase_log(LevelDesc *__restrict__ desc, const uint32_t *__restrict__ succ, Rec
     const uint64_t cnext = (uint64_t)lo + atomicAdd(q, 1u);
     const uint32_t c = (uint32_t)c64;
     const uint32_t rho = c < r ? P.inv(c) : __ldcg(ns + (c - r));
+    if (dbg_fail(rho < n && c < desc[1].cap, err)) { c64 = cnext; continue; }
     W.put(L, &s_win, kMark | c, kLogEnd, 0);
     uint32_t x = rho, o = 0, nxt = c;
     for (;;) {

@@ -137,3 +137,21 @@ def test_autotune_file_from_environment(tmp_path, lib):
             "assert len(e) == 1 and e[0]['log2n'] == 22 and e[0]['f0_inv'] == 8, e")
     env = dict(os.environ, LR_TUNING_FILE=str(src))
     subprocess.check_call([sys.executable, "-c", code], env=env, cwd=ROOT)
+
+
+def test_debug_build_exports_the_same_symbols():
+    """build(debug=True) cross-compiles here (no GPU needed) into a library
+    of its own that exports exactly the release library's entry points."""
+    import shutil
+    import subprocess as sp
+    if shutil.which("nm") is None:
+        pytest.skip("nm not available")
+    from paper_2606_09318_gb300 import build
+    rel = build.build()
+    dbg = build.build(debug=True)
+    assert dbg != rel and dbg.endswith("liblr_debug.so")
+
+    def exports(path):
+        out = sp.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+        return {ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-1].startswith("lr_")}
+    assert exports(dbg) == exports(rel) and "lr_rank" in exports(rel)
