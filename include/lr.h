@@ -78,7 +78,8 @@ typedef enum lr_dtype { LR_NONE = 0, LR_I32 = 1, LR_I64 = 2 } lr_dtype;
  * (visits by load and store instead of an atomic exchange); log=0 / log=1
  * (force the level-0 form); algo, contract, spawn; ord (batches: 0 chases
  * by per-CTA slices of ruler ids, 1 takes level 0's rulers in element
- * order, 2, the default, every level of 2^20 elements or more).
+ * order, 2, the default, every level of 2^20 elements or more); pf (the
+ * element order's L2 prefetch lead in K elements, 0 off, 4 by default).
  */
 typedef struct lr_tuning {
     uint32_t f0_inv;     /* 1/f at level 0 (default by n: 4 below 2^16, 8 below  */

@@ -79,6 +79,7 @@ Tuning resolve_tuning_builtin(int64_t n, bool weighted, bool batch) {
   u.contract = LR_CONTRACT_AUTO;
   u.spawn = 0;
   u.ord = 2;              // batches: every level of 2^20 or more in element order
+  u.pf = 4;               // ... prefetching its records 4K elements ahead of each draw
   return u;
 }
 
@@ -105,6 +106,7 @@ Tuning resolve_tuning(const lr_tuning *t, int64_t n, bool weighted, bool batch) 
   u.contract = env_u32(env, "contract", u.contract);
   u.spawn = env_u32(env, "spawn", u.spawn);
   u.ord = env_u32(env, "ord", u.ord);
+  u.pf = env_u32(env, "pf", u.pf);
   if (t) {
     if (t->spawn) u.spawn = t->spawn;
     if (t->chase0) u.chase0 = t->chase0;
@@ -908,6 +910,7 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
         oa.ord = (uint32_t *)(var + p.off_ord);
         oa.cum = (uint32_t *)(var + p.off_cum);
         oa.bits = bitmap;        // the has-predecessor bitmap is free once level 0's heads are chosen
+        oa.pf_lead = u.pf << 10;
         LR_TRY(launch_order(desc, l, p.cap[l], bcnt, &oa, hout, p.hcap, err, s));
       }
       LR_TRY(launch_chase(desc, l, work_of(l), r16, work_of(l + 1), ns,

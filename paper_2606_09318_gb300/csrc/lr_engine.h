@@ -11,7 +11,7 @@
 namespace lr {
 
 struct Tuning {
-  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, chase0, algo, contract, spawn, ord;
+  uint32_t f0_inv, f_inv, cutoff, block, ctas, xchg, chase0, algo, contract, spawn, ord, pf;
 };
 
 struct Plan {

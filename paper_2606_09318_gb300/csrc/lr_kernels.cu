@@ -877,11 +877,13 @@ cudaError_t launch_order(LevelDesc *desc, int lev, uint32_t cap, uint64_t *cnt, 
 // take single positions from the global counter.  Nobody waits.
 constexpr uint32_t kOrdChunk = 32;
 
-__device__ __forceinline__ uint64_t ord_take(unsigned long long *s_win, uint32_t *gq, uint64_t total) {
+__device__ __forceinline__ uint64_t ord_take(unsigned long long *s_win, uint32_t *gq, uint64_t total,
+                                             bool *refilled = nullptr) {
   const unsigned long long w = atomicAdd(s_win, 1ull);
   const uint32_t next = (uint32_t)w, end = (uint32_t)(w >> 32);
   if (next < end) return next;
   if (next == end) {
+    if (refilled) *refilled = true;
     // the chunk is this CTA's whatever its length: every position of it
     // must be handed out, up to the end of the sequence
     const uint32_t j = atomicAdd(gq, kOrdChunk);
@@ -932,7 +934,9 @@ __device__ __forceinline__ Rec visit(Rec *p, uint32_t cid, uint64_t off) {
 // heads (ids r .. r+k-1, in head-list order) then ord[0 .. r) (positions of
 // the sampled rulers, ascending), so all CTAs advance one front across the
 // instances together; the sampled ruler ord[i] has id i (ord_id of its
-// position).
+// position).  The thread that draws a CTA's next rulers also asks L2 for
+// the records of the elements its draw covers, pf_lead elements ahead:
+// streamed in order, they are mostly in L2 when the chases reach them.
 template <class Rec, bool XCHG, bool TERM, bool SPAWN>
 __global__ void __launch_bounds__(512)
 k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__restrict__ next,
@@ -955,7 +959,25 @@ k_chase(LevelDesc *__restrict__ desc, int lev, Rec *__restrict__ work, Rec16 *__
   // the next position of this thread's ruler sequence: a ruler id, or (ORD)
   // an index of the ordered sequence
   auto take = [&]() -> uint64_t {
-    if (ord) return ord_take(&s_win, qctr, R);
+    if (ord) {
+      bool refilled = false;
+      const uint64_t j = ord_take(&s_win, qctr, R, &refilled);
+      if (refilled && oa.pf_lead && j >= d.k && j < R) {
+        // the CTA took the rulers from j on: bring the records of the
+        // elements up to its next draw's first ruler, pf_lead elements ahead,
+        // into L2 before the front reaches them
+        const uint64_t a = (uint64_t)__ldcg(ord + (j - d.k)) + oa.pf_lead;
+        const uint64_t jb = j - d.k + kOrdChunk;
+        const uint64_t b = (jb < r ? (uint64_t)__ldcg(ord + jb) : (uint64_t)n) + oa.pf_lead;
+        if (a < n && b > a) {
+          const uintptr_t pa = ((uintptr_t)(work + a) + 15u) & ~(uintptr_t)15u;
+          const uintptr_t pb = (uintptr_t)(work + (b < n ? b : n)) & ~(uintptr_t)15u;
+          if (pb > pa && pb - pa <= (1u << 20))
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(pa), "r"((uint32_t)(pb - pa)) : "memory");
+        }
+      }
+      return j;
+    }
     return (uint64_t)lo + atomicAdd(q, 1u);
   };
   auto ord_pos = [&](uint64_t j) -> uint32_t {

@@ -92,6 +92,7 @@ struct OrdArgs {
   uint32_t *ord;
   uint32_t *cum;
   uint32_t *bits;
+  uint32_t pf_lead;          // prefetch the records this many elements ahead of the front (0: off)
 };
 
 // After a spawning chase at level lev: compact the next level's records
