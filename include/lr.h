@@ -402,7 +402,7 @@ typedef struct lr_server_config {
     int32_t plain;           /* 1: rank every request alone through the single-list  */
                              /* path, as lr_rank_ex does (baseline mode)             */
     int64_t alone_min_n;     /* a request of at least this many elements is ranked   */
-                             /* alone, never batched with others; 0 = default 2^20,  */
+                             /* alone, never batched with others; 0 = default 2^23,  */
                              /* < 0 = batch requests of any size                     */
 } lr_server_config;
 

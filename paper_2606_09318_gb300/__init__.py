@@ -598,7 +598,7 @@ class Server:
     """Continuous-batching ranking server (lr_server_* of the C ABI).
 
     Requests of at least alone_min_n elements (0: the library's default,
-    2^20; negative: never) are ranked on their own through the single-list
+    2^23; negative: never) are ranked on their own through the single-list
     path; smaller ones that wait together are ranked as one forest.  With
     plain=True every request is ranked on its own (the baseline mode)."""
 

@@ -48,7 +48,12 @@ struct Req {
 
 size_t wbytes(lr_dtype t) { return t == LR_I32 ? 4 : (t == LR_I64 ? 8 : 0); }
 
-constexpr int64_t kAloneMinDefault = (int64_t)1 << 20;
+// Requests of at least this many elements are ranked alone (single-list
+// path: contraction, the log form).  Smaller ones that wait together are
+// one batch, chased in element order with its records prefetched into L2,
+// which beats ranking requests of up to a few million elements alone on
+// concurrent streams, where their footprints add up in L2.
+constexpr int64_t kAloneMinDefault = (int64_t)1 << 23;
 
 // Device bytes a request holds while it is resident: its own buffers when
 // the server copies them, plus an estimate of its share of the ranking
