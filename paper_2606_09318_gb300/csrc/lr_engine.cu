@@ -744,10 +744,11 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   // Single instance, no validation: heads from the streaming sums (one list)
   // with the bitmap as the fallback, instead of atomics for every element.
   const bool sums0 = !log0 && !ptrs && in.offsets == nullptr && !in.validate && in.n > u.cutoff;
-  // A batch: per-instance sums (kept at the start of the bitmap's memory,
-  // which must hold 16 bytes per instance) give one head per instance and the
-  // number of lists, with the bitmap as the fallback for the heads.
-  const bool sums0b = !log0 && !ptrs && in.offsets != nullptr && !in.validate && !extras && !spawn0 &&
+  // A batch (contiguous or one pointer per instance): per-instance sums (kept
+  // at the start of the bitmap's memory, which must hold 16 bytes per
+  // instance) give one head per instance and the number of lists, with the
+  // bitmap as the fallback for the heads.
+  const bool sums0b = !log0 && in.offsets != nullptr && !in.validate && !extras && !spawn0 &&
                       in.n > u.cutoff && in.k > 0 && (uint64_t)in.k * 16 <= 4 * ((in.n + 31) / 32);
   Profiler prof;
   if (!in.ctx) prof.begin(s, (int64_t)in.n);
@@ -774,6 +775,9 @@ lr_status run(const Inputs &in, const lr_tuning *tuning, cudaStream_t s) {
   LR_TRY(cudaMemsetAsync(bitmap, 0, sizeof(uint32_t) * ((in.n + 31) / 32), s));
   if (log0)
     LR_TRY(launch_sum0(in.succ, (uint32_t)in.n, acc, local_exact ? acc + 2 : nullptr, err, s));
+  else if (ptrs && sums0b)
+    LR_TRY(launch_prep0_ptrs_sums(in.sptr, in.wptr, in.wtype, (uint32_t)in.n, work0, err, in.offsets, in.k,
+                                  reinterpret_cast<unsigned long long *>(bitmap), s));
   else if (ptrs)
     LR_TRY(launch_prep0_ptrs(in.sptr, in.wptr, in.wtype, (uint32_t)in.n, work0, bitmap, err,
                              in.validate, in.offsets, in.k, s));

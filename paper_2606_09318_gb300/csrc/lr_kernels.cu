@@ -540,6 +540,133 @@ cudaError_t launch_prep0_ptrs(const uint32_t *const *sptr, const void *const *wp
   return cudaGetLastError();
 }
 
+// The instance of element `base` in a table of k nondecreasing offsets with
+// offsets[0] = 0 <= base < offsets[k]: the largest j < k with offsets[j] <=
+// base, found by the whole warp at once (every lane probes one of 32 points
+// spread over the remaining range, the ballot keeps the last probe at or
+// below base), in at most 3 rounds for up to 32768 instances.  Warp-uniform.
+__device__ __forceinline__ int32_t warp_instance(const int64_t *__restrict__ offsets, int32_t k, uint64_t base,
+                                                 uint32_t lane) {
+  int32_t lo = 0, hi = k;
+  while (hi - lo > 1) {
+    const int64_t span = hi - lo;
+    const int32_t q = lo + (int32_t)(((int64_t)(lane + 1) * span) / 33);
+    const uint32_t le = __ballot_sync(0xFFFFFFFFu, (uint64_t)__ldg(offsets + q) <= base);
+    const int t = __popc(le);
+    const int32_t nlo = __shfl_sync(0xFFFFFFFFu, q, t > 0 ? t - 1 : 0);
+    const int32_t nhi = __shfl_sync(0xFFFFFFFFu, q, t < 32 ? t : 31);
+    if (t > 0) lo = max(lo, nlo);
+    if (t < 32) hi = nhi;
+  }
+  return lo;
+}
+
+// Pointer batches without per-element atomics: the per-instance sums of
+// k_prep0_sums (terminals, local successors), read through one pointer per
+// instance.  A warp takes 128 consecutive elements (lane l: l + 32 j, so that
+// loads and record stores are coalesced); lane 0 finds the instance of the
+// first by binary search and every lane walks forward from it.  A warp whose
+// elements all lie in one instance adds its sums with two atomics.
+template <int WT>
+__global__ void __launch_bounds__(256)
+k_prep0_ptrs_sums(const uint32_t *const *__restrict__ sptr, const void *const *__restrict__ wptr,
+                  uint32_t n, void *__restrict__ work, uint32_t *__restrict__ err,
+                  const int64_t *__restrict__ offsets, int32_t k, unsigned long long *__restrict__ isums) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t step = ((uint64_t)gridDim.x * blockDim.x >> 5) * 128u;
+  for (uint64_t base = warp * 128u; base < n; base += step) {
+    const int32_t lo0 = warp_instance(offsets, k, base, lane);
+    // each of the lane's four elements: its instance, then all four loads
+    // in flight together
+    int32_t inst[4];
+    uint64_t ibv[4], iev[4];
+    int32_t lo = lo0;
+    uint64_t ib = (uint64_t)__ldg(offsets + lo), ie = (uint64_t)__ldg(offsets + lo + 1);
+    const bool one = ie >= min(base + 128u, (uint64_t)n);   // warp-uniform
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t i = base + lane + 32u * j;
+      while (i < n && i >= ie && lo + 1 < k) { ++lo; ib = ie; ie = (uint64_t)__ldg(offsets + lo + 1); }
+      inst[j] = lo;
+      ibv[j] = ib;
+      iev[j] = ie;
+    }
+    uint32_t sv[4];
+    uint64_t wv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t i = base + lane + 32u * j;
+      sv[j] = 0u;
+      wv[j] = 1u;
+      if (i < n && i >= ibv[j] && i < iev[j]) {
+        const uint64_t loc = i - ibv[j];
+        sv[j] = __ldcs(sptr[inst[j]] + loc);
+        if constexpr (WT == 1) wv[j] = (uint64_t)(int64_t)__ldcs(reinterpret_cast<const int *>(wptr[inst[j]]) + loc);
+        if constexpr (WT == 2) wv[j] = (uint64_t)__ldcs(reinterpret_cast<const long long *>(wptr[inst[j]]) + loc);
+      }
+    }
+    unsigned long long sT = 0, sS = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t i = base + lane + 32u * j;
+      if (i >= n) continue;
+      uint32_t s = sv[j];
+      uint64_t w = wv[j];
+      const uint64_t ib = ibv[j], ie = iev[j];
+      bool term;
+      if (i < ib || i >= ie) {
+        record_error(err, kErrRange);     // a bad offset table
+        s = (uint32_t)i;
+        term = true;
+      } else if ((uint64_t)s >= ie - ib || ib + s >= n) {
+        record_error(err, kErrRange);     // successor outside its instance
+        s = (uint32_t)i;
+        term = true;
+      } else {
+        term = (uint64_t)s == i - ib;
+        if (!term) {
+          if (one) sS += s;
+          else atomicAdd(isums + 2 * (size_t)inst[j] + 1, (unsigned long long)s);
+        }
+        s = (uint32_t)(ib + s);
+      }
+      if (term) {
+        w = 0u;
+        if (one) sT += 1;
+        else atomicAdd(isums + 2 * (size_t)inst[j], 1ull);
+      }
+      if constexpr (WT == 0) reinterpret_cast<uint2 *>(work)[i] = make_uint2(s, kUnvisited);
+      else __stcs(reinterpret_cast<uint4 *>(work) + i, make_uint4(s, kUnvisited, (uint32_t)w, (uint32_t)(w >> 32)));
+    }
+    if (one) {
+      for (int d = 16; d > 0; d >>= 1) {
+        sT += __shfl_down_sync(0xFFFFFFFFu, sT, d);
+        sS += __shfl_down_sync(0xFFFFFFFFu, sS, d);
+      }
+      if (lane == 0) {
+        if (sT) atomicAdd(isums + 2 * (size_t)lo0, sT);
+        if (sS) atomicAdd(isums + 2 * (size_t)lo0 + 1, sS);
+      }
+    }
+  }
+}
+
+cudaError_t launch_prep0_ptrs_sums(const uint32_t *const *sptr, const void *const *wptr, int wtype, uint32_t n,
+                                   void *work, uint32_t *err, const int64_t *offsets, int32_t k,
+                                   unsigned long long *isums, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int block = 256;
+  const int grid = stream_grid(((uint64_t)n + 3) / 4, block);
+  switch (wtype) {
+    case 0: k_prep0_ptrs_sums<0><<<grid, block, 0, s>>>(sptr, wptr, n, work, err, offsets, k, isums); break;
+    case 1: k_prep0_ptrs_sums<1><<<grid, block, 0, s>>>(sptr, wptr, n, work, err, offsets, k, isums); break;
+    default: k_prep0_ptrs_sums<2><<<grid, block, 0, s>>>(sptr, wptr, n, work, err, offsets, k, isums); break;
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
 // Number of heads (zero bits of the has-predecessor bitmap below n).
 __global__ void k_count_heads(const uint32_t *__restrict__ bitmap, uint32_t n, uint32_t *out) {
   const uint32_t words = (uint32_t)(((uint64_t)n + 31u) / 32u);
@@ -1152,6 +1279,24 @@ __device__ __forceinline__ uint32_t propagate_term(uint32_t c, uint32_t i, uint3
   return kEnd;
 }
 
+// A record's last read (evict-first: the lines it frees in L2 serve the
+// gathers of the next level's ranks).
+template <class Rec>
+__device__ __forceinline__ Rec ld_rec_last(const Rec *p) {
+  Rec r;
+  if constexpr (sizeof(Rec) == 8) {
+    const uint2 a = __ldcs(reinterpret_cast<const uint2 *>(p));
+    r.lo = a.x;
+    r.hi = a.y;
+  } else {
+    const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(p));
+    r.succ = a.x;
+    r.tag = a.y;
+    r.w = ((uint64_t)a.w << 32) | a.z;
+  }
+  return r;
+}
+
 // Ruler propagation: every element gets its ruler's rank minus its offset
 // (TERM: and its ruler's terminal).
 template <class Rec, class RT, bool TERM>
@@ -1176,18 +1321,7 @@ k_finalize(const LevelDesc *__restrict__ desc, int lev, const Rec *__restrict__ 
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const uint64_t i = base + lane + 32u * j;
-      if (i < n) {
-        if constexpr (sizeof(Rec) == 8) {
-          const uint2 a = __ldcs(reinterpret_cast<const uint2 *>(work + i));
-          v[j].lo = a.x;
-          v[j].hi = a.y;
-        } else {
-          const uint4 a = __ldcs(reinterpret_cast<const uint4 *>(work + i));
-          v[j].succ = a.x;
-          v[j].tag = a.y;
-          v[j].w = ((uint64_t)a.w << 32) | a.z;
-        }
-      }
+      if (i < n) v[j] = ld_rec_last(work + i);
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1213,15 +1347,38 @@ k_finalize_ptrs(const LevelDesc *__restrict__ desc, const Rec *__restrict__ work
   const uint32_t n = d.n, nn = desc[1].n;
   uint32_t bad = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0 && d.visited != n) bad |= kErrCycle;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    Rec v = ld_rec(work + i);
-    const RT val = propagate<RT>(done_cid(v), done_off(v), nn, rnext, bad);
-    int32_t lo = 0, hi = k;
-    while (hi - lo > 1) {
-      int32_t mid = (lo + hi) >> 1;
-      if ((uint64_t)__ldg(offsets + mid) <= i) lo = mid; else hi = mid;
+  // each warp takes 128 consecutive elements (lane l: l + 32 j, coalesced
+  // record loads and rank stores); the four records, then the four gathers
+  // of the next level's ranks are in flight together, and the instances are
+  // found meanwhile (the warp's first by a warp-wide search, the others by
+  // walking forward from it).  Element ids and offsets fit 32 bits here.
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t step = ((uint64_t)gridDim.x * blockDim.x >> 5) * 128u;
+  for (uint64_t b64 = warp * 128u; b64 < n; b64 += step) {
+    const uint32_t base = (uint32_t)b64, rem = n - base;
+    Rec v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t t = lane + 32u * j;
+      if (t < rem) v[j] = ld_rec_last(work + base + t);
     }
-    rptr[lo][i - (uint64_t)__ldg(offsets + lo)] = val;
+    RT val[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (lane + 32u * j < rem) val[j] = propagate<RT>(done_cid(v[j]), done_off(v[j]), nn, rnext, bad);
+    }
+    int32_t lo = warp_instance(offsets, k, base, lane);
+    uint32_t ib = (uint32_t)__ldg(offsets + lo), ie = (uint32_t)__ldg(offsets + lo + 1);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t t = lane + 32u * j;
+      if (t < rem) {
+        const uint32_t i = base + t;
+        while (i >= ie && lo + 1 < k) { ++lo; ib = ie; ie = (uint32_t)__ldg(offsets + lo + 1); }
+        __stcs(rptr[lo] + (i - ib), val[j]);
+      }
+    }
   }
   if (bad) record_error(err, bad);
 }
@@ -1230,7 +1387,7 @@ cudaError_t launch_finalize_ptrs(LevelDesc *desc, const void *work, bool rec16, 
                                  void *const *rptr, int rank_bytes, uint32_t cap,
                                  const int64_t *offsets, int32_t k, uint32_t *err, cudaStream_t s) {
   const int block = 256;
-  const int grid = stream_grid(cap, block);
+  const int grid = stream_grid(((uint64_t)cap + 3) / 4, block);
 #define LR_FINP(REC, RT)                                                                          \
   k_finalize_ptrs<REC, RT><<<grid, block, 0, s>>>(desc, reinterpret_cast<const REC *>(work),      \
                                                   reinterpret_cast<const RT *>(rnext),            \

@@ -56,6 +56,11 @@ cudaError_t launch_prep0_ptrs(const uint32_t *const *sptr, const void *const *wp
                               uint32_t n, void *work, uint32_t *bitmap, uint32_t *err, int validate,
                               const int64_t *offsets, int32_t k, cudaStream_t s);
 
+// The same sums for a batch given as one pointer per instance.
+cudaError_t launch_prep0_ptrs_sums(const uint32_t *const *sptr, const void *const *wptr, int wtype, uint32_t n,
+                                   void *work, uint32_t *err, const int64_t *offsets, int32_t k,
+                                   unsigned long long *isums, cudaStream_t s);
+
 cudaError_t launch_finalize_ptrs(LevelDesc *desc, const void *work, bool rec16, const void *rnext,
                                  void *const *rptr, int rank_bytes, uint32_t cap,
                                  const int64_t *offsets, int32_t k, uint32_t *err, cudaStream_t s);

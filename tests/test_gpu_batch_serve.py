@@ -250,3 +250,39 @@ def test_batch_bad_offset_table():
     s2 = np.concatenate(parts).astype(np.uint32)
     got = lr.rank_batch(dev(good), dev(s2), rank_dtype=torch.int32, max_lists=3).cpu().numpy()
     np.testing.assert_array_equal(got, oracle.rank_batch(good, s2, None, np.int32))
+
+
+@pytest.mark.parametrize("wt", [None, "i32", "i64"])
+def test_server_forest_heads_from_sums(wt):
+    # Waiting requests are ranked as one forest of per-request buffers; its
+    # heads come from per-request sums (one head per list request).  Requests
+    # shorter than a warp's 128 elements share warps; requests that are
+    # forests themselves make the heads fall back to the predecessor bitmap;
+    # an invalid request fails alone.
+    rng = np.random.default_rng(77)
+    reqs = []
+    for i in range(60):
+        m = int(rng.choice([1, 2, 5, 37, 130, 700, 4000, 20000]))
+        if i in (11, 40) and m > 8:
+            s = gen.forest(m, 7700 + i, n_long=1, long_len=m // 4, mean_short=4)[0].astype(np.uint32)
+        else:
+            s = gen.random_list(m, 7700 + i).astype(np.uint32)
+        w = None if wt is None else (gen.weights_i32(m, 7800 + i) if wt == "i32" else gen.weights_i64(m, 7800 + i))
+        reqs.append((s, w))
+    bad = gen.random_list(3000, 7999).astype(np.uint32)
+    bad[17] = 3000 + 4                                        # outside its request
+    for with_forest in (False, True):
+        use = [r for i, r in enumerate(reqs) if with_forest or i not in (11, 40)]
+        srv = lr.Server(budget_bytes=1 << 30, n_streams=1, max_batch=64, alone_min_n=1 << 22)
+        try:
+            tickets = [srv.submit(dev(s), None if w is None else dev(w)) for s, w in use]
+            tbad = srv.submit(dev(bad))
+            for t, (s, w) in zip(tickets, use):
+                got, _ = srv.wait(t)
+                np.testing.assert_array_equal(got.cpu().numpy(),
+                                              oracle.rank(s, w, np.int64 if w is not None else np.int32))
+            with pytest.raises(lr.LRError) as e:
+                srv.wait(tbad)
+            assert e.value.name == "LR_ERR_OUT_OF_RANGE"
+        finally:
+            srv.close()
