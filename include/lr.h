@@ -207,6 +207,36 @@ lr_status lr_rank_batch_ex(const int64_t *offsets, const uint32_t *succ, const v
                            void *rank, int32_t k, const lr_opts *opts, lr_stream stream);
 
 /*
+ * Rank k independent instances that live in separate device buffers, as one
+ * forest in one launch sequence (Section 1.1's set of lists; the serving
+ * loop ranks waiting requests this way, where they already are).
+ *   offsets      device int64[k+1], offsets[0] == 0, non-decreasing:
+ *                instance j has offsets[j+1] - offsets[j] elements.
+ *   succ_ptrs    device array of k device pointers, uint32 LOCAL successors
+ *                of instance j ([0, its size); a tail points to itself).
+ *   weight_ptrs  NULL (unweighted) or a device array of k device pointers to
+ *                weights of opts->wtype.
+ *   rank_ptrs    device array of k device pointers to ranks of opts->rtype,
+ *                written by the call.
+ * Every buffer is owned by the caller and must hold its instance's size in
+ * elements (shorter buffers are undefined behaviour); an empty instance's
+ * pointers are never read.  The kernels address the buffers through the
+ * offset table, so the call first reads the table back (one wait on the
+ * stream; not capturable: LR_ERR_CAPTURE) and returns LR_ERR_INVALID_ARGUMENT
+ * unless it starts at 0 and never decreases (and, if opts->n_total > 0,
+ * ends at n_total); the sum of sizes is at most LR_MAX_N.  opts as in
+ * lr_rank_batch_ex (NULL: int64 weights and ranks when weight_ptrs is set,
+ * else int32 ranks): max_lists (> 0) saves counting the lists, validate
+ * checks in-degrees, sync waits and returns the device status.  A caller
+ * workspace is not supported here (LR_ERR_INVALID_ARGUMENT), nor are extra
+ * outputs.  A successor outside its instance is LR_ERR_OUT_OF_RANGE, through
+ * the device status like every data error.
+ */
+lr_status lr_rank_batch_ptrs(const int64_t *offsets, const uint32_t *const *succ_ptrs,
+                             const void *const *weight_ptrs, void *const *rank_ptrs, int32_t k,
+                             const lr_opts *opts, lr_stream stream);
+
+/*
  * Extra outputs of the default algorithm (Section 1.1 defines the result
  * as each element's rank AND the terminal of its list; its in-place form
  * counts the terminal's own weight).  All pointers are device memory owned

@@ -16,7 +16,7 @@ import threading
 
 __all__ = [
     "LRError", "Tuning", "load", "lib_path", "rank", "rank_ex", "rank_batch", "rank_host",
-    "device_status", "workspace_size", "status_string", "version", "profile_enable",
+    "rank_batch_ptrs", "device_status", "workspace_size", "status_string", "version", "profile_enable",
     "profile_read", "kernel_launch_count", "probe_memory", "Server", "STATUS",
 ]
 
@@ -121,6 +121,7 @@ _SIGS = {
     "lr_rank_ex": (ctypes.c_int, [_V, _V, _I64, _V, ctypes.POINTER(_Opts), _V]),
     "lr_rank_batch": (ctypes.c_int, [_V, _V, _V, _V, _I32, _V]),
     "lr_rank_batch_ex": (ctypes.c_int, [_V, _V, _V, _V, _I32, ctypes.POINTER(_Opts), _V]),
+    "lr_rank_batch_ptrs": (ctypes.c_int, [_V, _V, _V, _V, _I32, ctypes.POINTER(_Opts), _V]),
     "lr_rank_host": (ctypes.c_int, [_V, _V, _I64, _V, ctypes.POINTER(_Opts), _V]),
     "lr_rank_host_async": (ctypes.c_int, [_V, _V, _I64, _V, ctypes.POINTER(_Opts), _V]),
     "lr_workspace_size": (_SZ, [_I64, _I32, ctypes.POINTER(_Opts)]),
@@ -304,6 +305,68 @@ def rank_batch(offsets, succ, weight=None, out=None, rank_dtype=None, validate=F
     code = lib.lr_rank_batch_ex(op, sp, wp, rp, k, ctypes.byref(o), _stream_handle(stream))
     _check(code, "lr_rank_batch_ex")
     return out
+
+
+def rank_batch_ptrs(succs, weights=None, outs=None, rank_dtype=None, validate=False,
+                    seed=0x5EED, max_lists=0, tuning=None, sync=True, stream=None):
+    """Rank k lists held in separate CUDA tensors as one forest in one launch
+    sequence (the lr_rank_batch_ptrs entry point).
+
+    succs: CUDA int32/uint32 tensors of local successors, one per instance;
+    weights: None or one int32/int64 tensor per instance (one dtype);
+    outs: None or one rank tensor per instance.  Returns the rank tensors.
+    """
+    torch = _torch()
+    lib = load()
+    succs = list(succs)
+    k = len(succs)
+    if weights is not None:
+        weights = list(weights)
+        if len(weights) != k:
+            raise ValueError("weights and succs differ in count")
+    if outs is not None:
+        outs = list(outs)
+        if len(outs) != k:
+            raise ValueError("outs and succs differ in count")
+    if k == 0:
+        return []
+    device = succs[0].device
+    wdt = None if weights is None else weights[0].dtype
+    rdt = _rank_dtype(None if weights is None else weights[0], rank_dtype)
+    sizes, sp, wp, rp = [], [], [], []
+    if outs is None:
+        outs = [torch.empty(t.numel(), dtype=rdt, device=device) for t in succs]
+    for j, t in enumerate(succs):
+        if t.device != device:
+            raise ValueError("every tensor must be on the same device")
+        sp.append(_dev_ptr(t, "succs[%d]" % j, _succ_dtypes()).value or 0)
+        sizes.append(t.numel())
+        if weights is not None:
+            w = weights[j]
+            if w.dtype != wdt or w.numel() != t.numel():
+                raise ValueError("weights[%d] has another dtype or length" % j)
+            wp.append(_dev_ptr(w, "weights[%d]" % j, (torch.int32, torch.int64)).value or 0)
+        o = outs[j]
+        if o.dtype != outs[0].dtype or o.numel() != t.numel():
+            raise ValueError("outs[%d] has another dtype or length" % j)
+        rp.append(_dev_ptr(o, "outs[%d]" % j, (torch.int32, torch.int64)).value or 0)
+    offsets = torch.zeros(k + 1, dtype=torch.int64)
+    offsets[1:] = torch.cumsum(torch.tensor(sizes, dtype=torch.int64), 0)
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    with torch.cuda.stream(stream):          # the tables are copied on the stream that reads them
+        d_off = offsets.to(device)
+        d_sp = torch.tensor(sp, dtype=torch.int64).to(device)
+        d_rp = torch.tensor(rp, dtype=torch.int64).to(device)
+        d_wp = None if weights is None else torch.tensor(wp, dtype=torch.int64).to(device)
+    wcode = LR_NONE if weights is None else {torch.int32: LR_I32, torch.int64: LR_I64}[wdt]
+    o = _opts(wcode, LR_I32 if outs[0].dtype == torch.int32 else LR_I64, validate, seed,
+              max_lists, tuning, sync, n_total=int(offsets[-1]))
+    code = lib.lr_rank_batch_ptrs(ctypes.c_void_p(d_off.data_ptr()), ctypes.c_void_p(d_sp.data_ptr()),
+                                  None if d_wp is None else ctypes.c_void_p(d_wp.data_ptr()),
+                                  ctypes.c_void_p(d_rp.data_ptr()), k, ctypes.byref(o), _stream_handle(stream))
+    _check(code, "lr_rank_batch_ptrs")
+    return outs
 
 
 def _outputs(succ, rdt, term, prefix, inclusive_tail):

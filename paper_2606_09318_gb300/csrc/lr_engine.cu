@@ -1129,6 +1129,25 @@ lr_status lr_rank(const uint32_t *succ, const void *weight, int64_t n, void *ran
   return lr_rank_ex(succ, weight, n, rank, &o, stream);
 }
 
+// The element total of a batch: n_total when given (> 0), else offsets[k]
+// read back from the device (one wait on the stream).
+static lr_status batch_total(const int64_t *offsets, int32_t k, int64_t n_total, cudaStream_t s, int64_t *n) {
+  if (n_total > 0) {
+    *n = n_total;
+    return LR_OK;
+  }
+  if (stream_capturing(s)) return LR_ERR_CAPTURE;
+  lr_status st;
+  Ctx *c = get_ctx(s, &st);
+  if (!c) return st;
+  int64_t *h = (int64_t *)(c->host_words + 8);
+  cudaError_t e = cudaMemcpyAsync(h, offsets + k, 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  *n = *h;
+  return LR_OK;
+}
+
 static lr_status rank_batch_impl(const int64_t *offsets, const uint32_t *succ, const void *weight,
                                  void *rank, int32_t k, const lr_outputs *outs, const lr_opts *opts,
                                  lr_stream stream) {
@@ -1137,18 +1156,9 @@ static lr_status rank_batch_impl(const int64_t *offsets, const uint32_t *succ, c
   if (k < 0 || (k > 0 && !offsets)) return LR_ERR_INVALID_ARGUMENT;
   if (k == 0) return LR_OK;
   cudaStream_t s = (cudaStream_t)stream;
-  int64_t n = opts->n_total;
-  if (n <= 0) {
-    if (stream_capturing(s)) return LR_ERR_CAPTURE;
-    lr_status st;
-    Ctx *c = get_ctx(s, &st);
-    if (!c) return st;
-    int64_t *h = (int64_t *)(c->host_words + 8);
-    cudaError_t e = cudaMemcpyAsync(h, offsets + k, 8, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return from_cuda(e);
-    n = *h;
-  }
+  int64_t n = 0;
+  const lr_status nst = batch_total(offsets, k, opts->n_total, s, &n);
+  if (nst != LR_OK) return nst;
   if (n < 0 || n > LR_MAX_N) return LR_ERR_INVALID_ARGUMENT;
   if (n > 0 && (!succ || !rank)) return LR_ERR_INVALID_ARGUMENT;
   int wc, rb;
@@ -1192,6 +1202,52 @@ lr_status lr_rank_batch(const int64_t *offsets, const uint32_t *succ, const void
   lr_opts_default(&o);
   if (weight) { o.wtype = LR_I64; o.rtype = LR_I64; }
   return lr_rank_batch_ex(offsets, succ, weight, rank, k, &o, stream);
+}
+
+lr_status lr_rank_batch_ptrs(const int64_t *offsets, const uint32_t *const *succ_ptrs,
+                             const void *const *weight_ptrs, void *const *rank_ptrs, int32_t k,
+                             const lr_opts *opts, lr_stream stream) {
+  lr_opts d;
+  if (!opts) {
+    lr_opts_default(&d);
+    if (weight_ptrs) { d.wtype = LR_I64; d.rtype = LR_I64; }
+    opts = &d;
+  }
+  if (k < 0 || (k > 0 && (!offsets || !succ_ptrs || !rank_ptrs))) return LR_ERR_INVALID_ARGUMENT;
+  if (k == 0) return LR_OK;
+  if (opts->workspace) return LR_ERR_INVALID_ARGUMENT;   // the pointer form keeps its own workspace
+  cudaStream_t s = (cudaStream_t)stream;
+  // the kernels index the caller's buffers through the offset table, so it is
+  // read back and checked here before any of them runs (one wait)
+  if (stream_capturing(s)) return LR_ERR_CAPTURE;
+  std::vector<int64_t> h((size_t)k + 1);
+  cudaError_t e = cudaMemcpyAsync(h.data(), offsets, 8 * ((size_t)k + 1), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (h[0] != 0) return LR_ERR_INVALID_ARGUMENT;
+  for (int32_t j = 0; j < k; ++j)
+    if (h[j + 1] < h[j]) return LR_ERR_INVALID_ARGUMENT;
+  const int64_t n = h[k];
+  if (n > LR_MAX_N || (opts->n_total > 0 && opts->n_total != n)) return LR_ERR_INVALID_ARGUMENT;
+  int wc, rb;
+  lr_status st = check_types(weight_ptrs, opts->wtype, opts->rtype, &wc, &rb);
+  if (st != LR_OK) return st;
+  if (n == 0) return LR_OK;
+  Inputs in;
+  memset(&in, 0, sizeof(in));
+  in.sptr = succ_ptrs;
+  in.wptr = weight_ptrs;
+  in.rptr = rank_ptrs;
+  in.wtype = wc;
+  in.rank_bytes = rb;
+  in.n = (uint64_t)n;
+  in.offsets = offsets;
+  in.k = k;
+  in.validate = opts->validate;
+  in.seed = opts->seed;
+  in.max_lists = opts->max_lists;
+  in.sync = opts->sync;
+  return run(in, opts->tuning, s);
 }
 
 // Enqueue copy-in, ranking and copy-out on `stream` through the stream's own
