@@ -564,9 +564,9 @@ __device__ __forceinline__ int32_t warp_instance(const int64_t *__restrict__ off
 // Pointer batches without per-element atomics: the per-instance sums of
 // k_prep0_sums (terminals, local successors), read through one pointer per
 // instance.  A warp takes 128 consecutive elements (lane l: l + 32 j, so that
-// loads and record stores are coalesced); lane 0 finds the instance of the
-// first by binary search and every lane walks forward from it.  A warp whose
-// elements all lie in one instance adds its sums with two atomics.
+// loads and record stores are coalesced); the warp finds the instance of
+// the first (warp_instance) and every lane walks forward from it.  A warp
+// whose elements all lie in one instance adds its sums with two atomics.
 template <int WT>
 __global__ void __launch_bounds__(256)
 k_prep0_ptrs_sums(const uint32_t *const *__restrict__ sptr, const void *const *__restrict__ wptr,
