@@ -58,6 +58,21 @@ def test_host_only_calls(lib):
     assert lr.workspace_size(0) == 0
 
 
+def test_batch_ptrs_argument_errors_on_host(lib):
+    # lr_rank_batch_ptrs refuses bad arguments before it touches the device
+    import paper_2606_09318_gb300 as lr
+    o = lr._opts(0, 1)
+    fake = ctypes.c_void_p(256)
+    assert lib.lr_rank_batch_ptrs(fake, fake, None, fake, 0, ctypes.byref(o), None) == 0   # no instances
+    assert lib.lr_rank_batch_ptrs(fake, fake, None, fake, -1, ctypes.byref(o), None) == 1
+    assert lib.lr_rank_batch_ptrs(None, fake, None, fake, 2, ctypes.byref(o), None) == 1   # no offsets
+    assert lib.lr_rank_batch_ptrs(fake, None, None, fake, 2, ctypes.byref(o), None) == 1   # no succ table
+    assert lib.lr_rank_batch_ptrs(fake, fake, None, None, 2, ctypes.byref(o), None) == 1   # no rank table
+    o.workspace = fake                                       # a caller workspace is not supported
+    o.ws_bytes = 1 << 20
+    assert lib.lr_rank_batch_ptrs(fake, fake, None, fake, 2, ctypes.byref(o), None) == 1
+
+
 def test_workspace_counts_element_order_arrays(lib, monkeypatch):
     """A batch chases its levels in element order: its workspace holds the
     positions of the largest level's sampled rulers (4 B each) and the count
